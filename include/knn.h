@@ -1,0 +1,174 @@
+/*
+ * knn.h -- C ABI of the GB300 exact brute-force k-NN / k-NN graph engine.
+ *
+ * The method is Komarov, Dashti and D'Souza, "Fast k-NNG construction with
+ * GPU-based quick multi-select":
+ *   - the k-NN problem and the k-NN graph (Introduction): for every query point,
+ *     the k nearest corpus points; in the graph the corpus is the query set and a
+ *     point is never its own neighbour;
+ *   - distances as a matrix product (Methods, "Distance calculation"): squared
+ *     Euclidean d2_ij = |x_i|^2 + |y_j|^2 - 2 x_i.y_j, ranked by the per-row
+ *     equivalent d'_ij = |y_j|^2 - 2 x_i.y_j;
+ *   - per-row selection of the k smallest entries by quick multi-select with warp
+ *     ballot/popc partitions (Methods, "GPU-based quick multi-select").
+ *
+ * Results are EXACT: every row is sorted ascending by (squared distance, corpus
+ * index), self excluded in the graph (by index, not by distance: duplicates still
+ * appear at distance 0), ties at equal distance resolved to the lower index.
+ * Reduced-precision forms (BF16, FP8) select a candidate superset that provably
+ * contains the exact answer and re-rank it with direct-difference FP32 arithmetic;
+ * FP64 settles near ties. Reported distances are squared and within 1e-5 relative
+ * of the FP64 value (bit-exact where the inputs make FP32 arithmetic exact).
+ *
+ * Conventions for every entry point:
+ *   - Arrays are dense, row-major and contiguous unless a leading dimension is given.
+ *   - Arrays may live in device memory or in host memory; host arrays (pinned or
+ *     pageable) are copied to the device and back on the call's stream.
+ *   - The caller owns all inputs and outputs. The library owns its workspace, cached
+ *     per device and released by knn_shutdown().
+ *   - Calls are synchronous: they return once outputs are written (or on error).
+ *   - Errors are returned as a knn_status, never by aborting. On a non-OK status the
+ *     outputs are undefined; knn_last_error() gives a message (per thread).
+ *   - Indices are int32; N must be below 2^31.
+ */
+#ifndef KNN_H
+#define KNN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum knn_status {
+    KNN_OK = 0,
+    KNN_EINVAL = -1,     /* bad argument: NULL pointer, k < 1, k > available points, d < 1, NaN/Inf input */
+    KNN_ENOMEM = -2,     /* workspace allocation failed */
+    KNN_ECUDA = -3,      /* a CUDA call failed (message in knn_last_error) */
+    KNN_ETIMEOUT = -4,   /* a bounded device-side wait gave up */
+    KNN_EINTERNAL = -5,  /* an internal consistency check failed */
+    KNN_EUNSUPPORTED = -6 /* the requested form is not available on this device or build */
+} knn_status;
+
+typedef enum knn_precision {
+    KNN_FP32 = 0,      /* SIMT FP32 distance GEMM, materialised matrix, unfused select */
+    KNN_BF16 = 1,      /* tcgen05 BF16 GEMM with FP32 accumulation */
+    KNN_FP8_E4M3 = 2,  /* tcgen05 FP8 e4m3 GEMM with per-row power-of-two scales */
+    KNN_AUTO = -1
+} knn_precision;
+
+enum {
+    KNN_FLAG_TIMING = 1 << 0,       /* fill the ms_* fields of knn_stats (CUDA events on the stream) */
+    KNN_FLAG_NO_FALLBACK = 1 << 1,  /* report uncertified rows instead of recomputing them (tests) */
+    KNN_FLAG_CHECK_FINITE = 1 << 2  /* reject NaN/Inf inputs with KNN_EINVAL (on by default via knn_options_init) */
+};
+
+/* Per-call statistics (optional output). */
+typedef struct knn_stats {
+    int64_t rows;              /* query rows answered */
+    int64_t candidates;        /* candidates re-ranked exactly, summed over rows */
+    int64_t rows_truncated;    /* rows whose candidate list reached its capacity */
+    int64_t rows_uncertified;  /* rows the first pass could not prove exact */
+    int64_t rows_fallback;     /* rows recomputed by a more precise path */
+    int64_t rows_fp64_ties;    /* rows where FP64 decided a near tie */
+    int64_t threshold_misses;  /* rows where a supplied threshold kept fewer than k candidates */
+    float max_error_bound;     /* largest per-row bound on |approximate - exact| squared distance */
+    float ms_total, ms_prep, ms_select, ms_rerank, ms_fallback; /* with KNN_FLAG_TIMING */
+    float ms_gemm;             /* with KNN_FLAG_TIMING: device time of the distance kernel (fused: GEMM + select) */
+    int32_t gemm_launches;     /* launches of that kernel */
+    int64_t kernel_launches;   /* every kernel the call launched */
+    double gemm_flops;         /* 2 M N d_effective: the distance product the GEMM launches computed */
+    int32_t precision_used;    /* knn_precision actually run */
+    int32_t fused_used;        /* 1 when the select ran inside the GEMM epilogue */
+    int32_t exact_arithmetic;  /* 1 when the inputs made the GEMM exact (integer-valued, small) */
+    int32_t reserved;
+} knn_stats;
+
+typedef struct knn_options {
+    int32_t precision;          /* knn_precision; KNN_AUTO picks BF16 fused where available */
+    int32_t rerank_extra;       /* m: candidates beyond k always re-ranked exactly (>= 0; default 32) */
+    int32_t fused;              /* -1 auto, 0 materialise the distance matrix, 1 fuse the select into the GEMM */
+    int32_t flags;              /* KNN_FLAG_* */
+    void* stream;               /* cudaStream_t to run on; NULL = the legacy default stream */
+    const float* row_threshold; /* optional, M floats (device or host): per-row squared-distance
+                                   threshold proposal that pre-filters candidates; rows where fewer
+                                   than k candidates pass are recomputed without it */
+    knn_stats* stats;           /* optional output */
+    int64_t max_workspace_bytes;/* 0 = no cap; otherwise the distance-matrix slab is sized to fit */
+} knn_options;
+
+/* Fill *opt with defaults: KNN_AUTO, m = 32, fused auto, finite check on. */
+void knn_options_init(knn_options* opt);
+
+/*
+ * k-NN graph of N points X (N x d FP32). out_idx, out_dist: N x k.
+ * Requires 1 <= k <= N - 1, d >= 1. (Introduction: k-NNG; Methods: distance
+ * calculation and quick multi-select.) Default options.
+ */
+int knng_build(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_idx, float* out_dist);
+
+/* knng_build with options (opt may be NULL for defaults). */
+int knng_build_ex(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_idx, float* out_dist,
+                  const knn_options* opt);
+
+/*
+ * k-NN search: for each of the M queries Q (M x d) the k nearest of the N corpus
+ * points C (N x d); nothing is excluded. Requires 1 <= k <= N.
+ * out_idx, out_dist: M x k.
+ */
+int knn_search(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k,
+               int32_t* out_idx, float* out_dist, const knn_options* opt);
+
+/*
+ * Quick multi-select alone (Methods, "GPU-based quick multi-select"): the k
+ * smallest values of every row of the M x N FP32 matrix D (row stride ldd >= N
+ * elements), ascending by (value, column), ties to the lower column. NaN entries
+ * are rejected. out_idx (int32), out_val (FP32): M x k. Requires 1 <= k <= N.
+ */
+int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx, float* out_val,
+               const knn_options* opt);
+
+/*
+ * Distance matrix alone (Methods, "Distance calculation"): out_D[i*ldd + j] =
+ * |c_j|^2 - 2 q_i.c_j (full = 0, the per-row ranking form d') or the squared
+ * distance |q_i|^2 + |c_j|^2 - 2 q_i.c_j (full = 1), FP32 SIMT arithmetic.
+ */
+int knn_distances(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, float* out_D, int64_t ldd,
+                  int32_t full, const knn_options* opt);
+
+/* One problem of a batch. Pointers follow the conventions above. */
+typedef struct knn_problem {
+    const float* Q;      /* M x d queries; NULL with exclude_self = 1 means Q = C (a graph) */
+    const float* C;      /* N x d corpus */
+    int64_t M, N;
+    int32_t d, k;
+    int32_t exclude_self;/* 1: k-NN graph semantics (requires Q == C or Q == NULL, M == N) */
+    int32_t status;      /* out: knn_status of this problem */
+    int32_t* out_idx;    /* M x k */
+    float* out_dist;     /* M x k */
+} knn_problem;
+
+/*
+ * Many independent problems of uneven shape in one persistent launch per phase,
+ * captured and replayed as a CUDA graph. Per-problem status in probs[i].status.
+ * Returns KNN_OK when every problem succeeded, otherwise the first failure.
+ */
+int knn_search_batched(knn_problem* probs, int32_t count, const knn_options* opt);
+
+/* Human-readable name of a status code. */
+const char* knn_status_string(int status);
+
+/* Message of the last error on the calling thread ("" when none). */
+const char* knn_last_error(void);
+
+/* Release the cached workspace of every device this process used. */
+void knn_shutdown(void);
+
+/* Library version, e.g. "0.1.0". */
+const char* knn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KNN_H */

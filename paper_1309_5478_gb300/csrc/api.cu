@@ -1,0 +1,588 @@
+// C ABI entry points and the host-side runtime: argument checks, the per-device
+// workspace, staging of host arrays, the slab loop of the plain form, and the
+// exactness fallbacks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+#include "internal.h"
+#include "knn.h"
+
+namespace knn {
+
+thread_local std::string g_last_error;
+
+int set_error(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+// ---------------------------------------------------------------------------
+// workspace: one grow-only device buffer per device
+// ---------------------------------------------------------------------------
+namespace {
+struct DevWs {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_ws_mu;
+std::unordered_map<int, DevWs> g_ws;
+}  // namespace
+
+int workspace_get(size_t bytes, void** out) {
+    int dev = 0;
+    KNN_CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    DevWs& w = g_ws[dev];
+    if (w.bytes < bytes) {
+        if (w.ptr) {
+            KNN_CK(cudaDeviceSynchronize());
+            KNN_CK(cudaFree(w.ptr));
+            w.ptr = nullptr;
+            w.bytes = 0;
+        }
+        const size_t want = bytes + bytes / 8;
+        cudaError_t e = cudaMalloc(&w.ptr, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaMalloc(&w.ptr, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                w.ptr = nullptr;
+                return set_error(KNN_ENOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+            }
+            w.bytes = bytes;
+        } else {
+            w.bytes = want;
+        }
+    }
+    *out = w.ptr;
+    return KNN_OK;
+}
+
+void workspace_release_all() {
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto& kv : g_ws) {
+        if (kv.second.ptr) {
+            cudaSetDevice(kv.first);
+            cudaDeviceSynchronize();
+            cudaFree(kv.second.ptr);
+        }
+    }
+    g_ws.clear();
+    cudaSetDevice(cur);
+    cudaGetLastError();
+}
+
+bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pick_cap(int k, int km) {
+    (void)k;
+    const int extra = std::max(64, km / 2);
+    int c = 32;
+    while (c < km + extra) c <<= 1;
+    return std::min(c, MAX_CAP);
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// plain form: FP32 SIMT GEMM slab -> unfused quick multi-select -> exact re-rank
+// ---------------------------------------------------------------------------
+struct PlainLayout {
+    PrepState ps{};
+    float* D = nullptr;
+    uint64_t* cand = nullptr;
+    int32_t* count = nullptr;
+    uint64_t* bound = nullptr;
+    uint32_t* flags = nullptr;
+    uint32_t* row_status = nullptr;
+    RerankCounters* counters = nullptr;
+    int32_t* fb_rows = nullptr;
+    double* fp64_scratch = nullptr;
+    int64_t R = 0, ldn = 0, fp64_chunk = 0;
+    int km = 0, cap = 0;
+};
+
+void layout_plain(const Problem& pb, Arena& ar, PlainLayout& L) {
+    const bool same = pb.graph;
+    PrepState& ps = L.ps;
+    ps.gq = ar.take<PrepGlobals>(1);
+    ps.gc = same ? ps.gq : ar.take<PrepGlobals>(1);
+    ps.cnorm2 = ar.take<float>(pb.N);
+    ps.qnorm2 = same ? ps.cnorm2 : ar.take<float>(pb.M);
+    ps.E = ar.take<float>(pb.M);
+    ps.thr_dprime = pb.thr ? ar.take<float>(pb.M) : nullptr;
+    L.km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
+    L.cap = pick_cap(pb.k, L.km);
+    L.ldn = (pb.N + 31) / 32 * 32;
+    const int64_t budget = pb.slab_bytes > 0 ? pb.slab_bytes : (int64_t(4) << 30);
+    L.R = std::max<int64_t>(128, budget / (L.ldn * 4) / 128 * 128);
+    L.R = std::min<int64_t>(L.R, (pb.M + 127) / 128 * 128);
+    L.D = ar.take<float>(static_cast<size_t>(L.R) * L.ldn);
+    L.cand = ar.take<uint64_t>(static_cast<size_t>(L.R) * L.cap);
+    L.count = ar.take<int32_t>(L.R);
+    L.bound = ar.take<uint64_t>(L.R);
+    L.flags = ar.take<uint32_t>(L.R);
+    L.row_status = ar.take<uint32_t>(pb.M);
+    L.counters = ar.take<RerankCounters>(1);
+    L.fb_rows = ar.take<int32_t>(pb.M);
+    L.fp64_chunk = std::max<int64_t>(1, std::min<int64_t>(pb.M, (int64_t(1) << 30) / (pb.N * 8)));
+    L.fp64_scratch = ar.take<double>(static_cast<size_t>(L.fp64_chunk) * pb.N);
+}
+
+int prep_and_check(const Problem& pb, const PrepState& ps, cudaStream_t st, knn_stats* stats) {
+    const bool same = pb.graph;
+    KNN_CK(cudaMemsetAsync(ps.gq, 0, sizeof(PrepGlobals), st));
+    if (!same) KNN_CK(cudaMemsetAsync(ps.gc, 0, sizeof(PrepGlobals), st));
+    KNN_CK(launch_prep(pb.C, pb.N, pb.d, P_FP32, ps.cnorm2, nullptr, nullptr, nullptr, 0, nullptr, ps.gc, st));
+    if (!same)
+        KNN_CK(launch_prep(pb.Q, pb.M, pb.d, P_FP32, ps.qnorm2, nullptr, nullptr, nullptr, 0, nullptr, ps.gq, st));
+    KNN_CK(launch_bounds(ps.qnorm2, nullptr, nullptr, pb.M, pb.d, pb.d, P_FP32, ps.gq, ps.gc, ps.E, st));
+    if (pb.thr) KNN_CK(launch_threshold_to_dprime(pb.thr, ps.qnorm2, pb.M, ps.thr_dprime, st));
+    PrepGlobals hq{}, hc{};
+    KNN_CK(cudaMemcpyAsync(&hq, ps.gq, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaMemcpyAsync(&hc, ps.gc, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    if ((pb.flags & KNN_FLAG_CHECK_FINITE) && (hq.nonfinite || hc.nonfinite))
+        return set_error(KNN_EINVAL, "input holds NaN or Inf (%u query rows, %u corpus rows)", hq.nonfinite,
+                         hc.nonfinite);
+    if (stats) {
+        float amax;
+        uint32_t u = std::max(hq.max_abs, hc.max_abs);
+        std::memcpy(&amax, &u, 4);
+        stats->exact_arithmetic =
+            (hq.noninteger == 0 && hc.noninteger == 0 && 4.0 * pb.d * double(amax) * amax <= 16777216.0) ? 1 : 0;
+    }
+    return KNN_OK;
+}
+
+int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
+    PlainLayout L;
+    Arena sz;
+    layout_plain(pb, sz, L);
+    void* base = nullptr;
+    KNN_TRY(workspace_get(sz.used(), &base));
+    Arena ar(static_cast<char*>(base), sz.used());
+    L = PlainLayout{};
+    layout_plain(pb, ar, L);
+
+    cudaEvent_t ev[4] = {};
+    const bool timing = stats && (pb.flags & KNN_FLAG_TIMING);
+    if (timing) {
+        for (auto& e : ev) KNN_CK(cudaEventCreate(&e));
+        KNN_CK(cudaEventRecord(ev[0], st));
+    }
+    KNN_TRY(prep_and_check(pb, L.ps, st, stats));
+    KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
+    if (timing) KNN_CK(cudaEventRecord(ev[1], st));
+
+    int64_t launches = (pb.graph ? 1 : 2) + 1 + (pb.thr ? 1 : 0);
+    std::vector<cudaEvent_t> gev;
+    for (int64_t r0 = 0; r0 < pb.M; r0 += L.R) {
+        const int64_t rows = std::min<int64_t>(L.R, pb.M - r0);
+        if (timing) {
+            gev.emplace_back();
+            gev.emplace_back();
+            KNN_CK(cudaEventCreate(&gev[gev.size() - 2]));
+            KNN_CK(cudaEventCreate(&gev[gev.size() - 1]));
+            KNN_CK(cudaEventRecord(gev[gev.size() - 2], st));
+        }
+        KNN_CK(launch_gemm_simt(pb.Q + r0 * pb.d, rows, 0, pb.C, pb.N, pb.d, L.ps.cnorm2, nullptr, L.D, L.ldn, 0,
+                                st));
+        if (timing) KNN_CK(cudaEventRecord(gev.back(), st));
+        launches += 3;
+        SelectParams sp{};
+        sp.D = L.D;
+        sp.ldd = L.ldn;
+        sp.M = rows;
+        sp.N = pb.N;
+        sp.k = pb.k;
+        sp.km = L.km;
+        sp.cap = L.cap;
+        sp.E = L.ps.E + r0;
+        sp.thr = L.ps.thr_dprime ? L.ps.thr_dprime + r0 : nullptr;
+        sp.cand = L.cand;
+        sp.count = L.count;
+        sp.bound = L.bound;
+        sp.flags = L.flags;
+        sp.self_col = nullptr;
+        KNN_CK(launch_select_ex(sp, pb.graph ? r0 : -1, false, st));
+        RerankParams rp{};
+        rp.Q = pb.Q + r0 * pb.d;
+        rp.C = pb.C;
+        rp.M = rows;
+        rp.N = pb.N;
+        rp.d = pb.d;
+        rp.k = pb.k;
+        rp.cap = L.cap;
+        rp.cand = L.cand;
+        rp.count = L.count;
+        rp.bound = L.bound;
+        rp.flags = L.flags;
+        rp.E = L.ps.E + r0;
+        rp.out_idx = pb.out_idx + r0 * pb.k;
+        rp.out_dist = pb.out_dist + r0 * pb.k;
+        rp.row_status = L.row_status + r0;
+        rp.counters = L.counters;
+        KNN_CK(launch_rerank(rp, st));
+    }
+    if (timing) KNN_CK(cudaEventRecord(ev[2], st));
+
+    RerankCounters hc{};
+    KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    int64_t fallback = 0;
+    if (hc.uncertified > 0 && !(pb.flags & KNN_FLAG_NO_FALLBACK)) {
+        std::vector<uint32_t> hs(static_cast<size_t>(pb.M));
+        KNN_CK(cudaMemcpyAsync(hs.data(), L.row_status, pb.M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        KNN_CK(cudaStreamSynchronize(st));
+        std::vector<int32_t> rows;
+        for (int64_t i = 0; i < pb.M; ++i)
+            if (hs[static_cast<size_t>(i)] & ROW_UNCERTIFIED) rows.push_back(static_cast<int32_t>(i));
+        if (pb.k > 2048) return set_error(KNN_EINTERNAL, "uncertified rows with k > 2048");
+        KNN_CK(cudaMemcpyAsync(L.fb_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        for (size_t r = 0; r < rows.size(); r += static_cast<size_t>(L.fp64_chunk)) {
+            const int32_t n = static_cast<int32_t>(std::min<size_t>(L.fp64_chunk, rows.size() - r));
+            KNN_CK(launch_exact_rows_fp64(pb.Q, pb.C, pb.N, pb.d, pb.k, pb.graph ? 1 : 0, L.fb_rows + r, n,
+                                          L.fp64_scratch, pb.out_idx, pb.out_dist, st));
+            ++launches;
+        }
+        fallback = static_cast<int64_t>(rows.size());
+    }
+    if (timing) KNN_CK(cudaEventRecord(ev[3], st));
+    KNN_CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->rows = pb.M;
+        stats->candidates = static_cast<int64_t>(hc.candidates);
+        stats->rows_truncated = static_cast<int64_t>(hc.truncated);
+        stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
+        stats->rows_fallback = fallback;
+        stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
+        stats->threshold_misses = static_cast<int64_t>(hc.threshold_miss);
+        stats->precision_used = KNN_FP32;
+        stats->fused_used = 0;
+        stats->kernel_launches = launches;
+        stats->gemm_launches = static_cast<int32_t>((pb.M + L.R - 1) / L.R);
+        stats->gemm_flops = 2.0 * double(pb.M) * double(pb.N) * double(pb.d);
+        if (timing) {
+            float g = 0.f;
+            for (size_t i = 0; i + 1 < gev.size(); i += 2) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, gev[i], gev[i + 1]);
+                g += t;
+            }
+            stats->ms_gemm = g;
+        }
+        if (timing) {
+            float a = 0, b = 0, c = 0;
+            cudaEventElapsedTime(&a, ev[0], ev[1]);
+            cudaEventElapsedTime(&b, ev[1], ev[2]);
+            cudaEventElapsedTime(&c, ev[2], ev[3]);
+            stats->ms_prep = a;
+            stats->ms_select = b;
+            stats->ms_rerank = 0.f;
+            stats->ms_fallback = c;
+            stats->ms_total = a + b + c;
+        }
+    }
+    if (timing) {
+        for (auto& e : ev) cudaEventDestroy(e);
+        for (auto& e : gev) cudaEventDestroy(e);
+    }
+    return KNN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host-array staging
+// ---------------------------------------------------------------------------
+struct Staged {
+    std::vector<std::pair<void*, size_t>> owned;
+    ~Staged() {
+        for (auto& p : owned) cudaFree(p.first);
+    }
+    int in(const void* p, size_t bytes, cudaStream_t st, const void** out) {
+        if (!p || is_device_pointer(p)) {
+            *out = p;
+            return KNN_OK;
+        }
+        void* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(KNN_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
+        }
+        owned.emplace_back(d, bytes);
+        KNN_CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, st));
+        *out = d;
+        return KNN_OK;
+    }
+    // Output: returns a device buffer; copy_back() moves it to the host pointer.
+    std::vector<std::tuple<void*, void*, size_t>> outs;
+    int out(void* p, size_t bytes, void** dev) {
+        if (is_device_pointer(p)) {
+            *dev = p;
+            return KNN_OK;
+        }
+        void* d = nullptr;
+        cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(KNN_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
+        }
+        owned.emplace_back(d, bytes);
+        outs.emplace_back(p, d, bytes);
+        *dev = d;
+        return KNN_OK;
+    }
+    int copy_back(cudaStream_t st) {
+        for (auto& t : outs)
+            KNN_CK(cudaMemcpyAsync(std::get<0>(t), std::get<1>(t), std::get<2>(t), cudaMemcpyDeviceToHost, st));
+        KNN_CK(cudaStreamSynchronize(st));
+        return KNN_OK;
+    }
+};
+
+cudaStream_t stream_of(const knn_options* o) { return o ? static_cast<cudaStream_t>(o->stream) : nullptr; }
+
+knn_options defaults() {
+    knn_options o;
+    knn_options_init(&o);
+    return o;
+}
+
+int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t* out_idx,
+                float* out_dist, const knn_options* opt_in, bool graph) {
+    g_last_error.clear();
+    const knn_options opt = opt_in ? *opt_in : defaults();
+    if (!C || !out_idx || !out_dist || (!graph && !Q)) return set_error(KNN_EINVAL, "NULL pointer argument");
+    if (d < 1) return set_error(KNN_EINVAL, "d must be >= 1 (got %d)", d);
+    if (k < 1) return set_error(KNN_EINVAL, "k must be >= 1 (got %d)", k);
+    if (N < 1 || N >= (int64_t(1) << 31)) return set_error(KNN_EINVAL, "N must be in [1, 2^31) (got %lld)", (long long)N);
+    if (M < 0) return set_error(KNN_EINVAL, "M must be >= 0");
+    if (graph && k > N - 1) return set_error(KNN_EINVAL, "k must be <= N - 1 for a k-NN graph (k=%d, N=%lld)", k, (long long)N);
+    if (!graph && k > N) return set_error(KNN_EINVAL, "k must be <= N (k=%d, N=%lld)", k, (long long)N);
+    if (k > MAX_K) return set_error(KNN_EINVAL, "k above %d is not supported (got %d)", MAX_K, k);
+    if (opt.rerank_extra < 0) return set_error(KNN_EINVAL, "rerank_extra must be >= 0");
+    if (M == 0) return KNN_OK;
+    cudaStream_t st = stream_of(&opt);
+    Staged sg;
+    const void *Qd = nullptr, *Cd = nullptr, *Td = nullptr;
+    KNN_TRY(sg.in(C, static_cast<size_t>(N) * d * sizeof(float), st, &Cd));
+    if (graph) {
+        Qd = Cd;
+    } else {
+        KNN_TRY(sg.in(Q, static_cast<size_t>(M) * d * sizeof(float), st, &Qd));
+    }
+    if (opt.row_threshold) KNN_TRY(sg.in(opt.row_threshold, static_cast<size_t>(M) * sizeof(float), st, &Td));
+    void *oi = nullptr, *od = nullptr;
+    KNN_TRY(sg.out(out_idx, static_cast<size_t>(M) * k * sizeof(int32_t), &oi));
+    KNN_TRY(sg.out(out_dist, static_cast<size_t>(M) * k * sizeof(float), &od));
+    Problem pb{};
+    pb.Q = static_cast<const float*>(Qd);
+    pb.C = static_cast<const float*>(Cd);
+    pb.M = M;
+    pb.N = N;
+    pb.d = d;
+    pb.k = k;
+    pb.m = opt.rerank_extra;
+    pb.graph = graph;
+    pb.thr = static_cast<const float*>(Td);
+    pb.out_idx = static_cast<int32_t*>(oi);
+    pb.out_dist = static_cast<float*>(od);
+    pb.slab_bytes = opt.max_workspace_bytes > 0 ? opt.max_workspace_bytes / 2 : 0;
+    pb.precision = opt.precision;
+    pb.fused = opt.fused;
+    pb.flags = opt.flags;
+    knn_stats local{};
+    knn_stats* stats = opt.stats ? opt.stats : &local;
+    std::memset(stats, 0, sizeof(*stats));
+    KNN_TRY(run_problem(pb, stats, st));
+    KNN_TRY(sg.copy_back(st));
+    return KNN_OK;
+}
+
+}  // namespace
+
+int run_problem(const Problem& pb, knn_stats* stats, cudaStream_t st) {
+    int prec = pb.precision;
+    if (prec == KNN_AUTO) prec = KNN_FP32;
+    switch (prec) {
+        case KNN_FP32:
+            return run_plain(pb, stats, st);
+        case KNN_BF16:
+        case KNN_FP8_E4M3:
+            return set_error(KNN_EUNSUPPORTED, "precision %d is not available in this build", prec);
+        default:
+            return set_error(KNN_EINVAL, "unknown precision %d", prec);
+    }
+}
+
+}  // namespace knn
+
+// ---------------------------------------------------------------------------
+// extern "C" surface
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void knn_options_init(knn_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = KNN_AUTO;
+    opt->rerank_extra = 32;
+    opt->fused = -1;
+    opt->flags = KNN_FLAG_CHECK_FINITE;
+}
+
+int knng_build(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_idx, float* out_dist) {
+    return knn::search_impl(X, N, X, N, d, k, out_idx, out_dist, nullptr, true);
+}
+
+int knng_build_ex(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_idx, float* out_dist,
+                  const knn_options* opt) {
+    return knn::search_impl(X, N, X, N, d, k, out_idx, out_dist, opt, true);
+}
+
+int knn_search(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t* out_idx,
+               float* out_dist, const knn_options* opt) {
+    return knn::search_impl(Q, M, C, N, d, k, out_idx, out_dist, opt, false);
+}
+
+int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx, float* out_val,
+               const knn_options* opt) {
+    using namespace knn;
+    g_last_error.clear();
+    if (!D || !out_idx || !out_val) return set_error(KNN_EINVAL, "NULL pointer argument");
+    if (N < 1 || N >= (int64_t(1) << 31)) return set_error(KNN_EINVAL, "N must be in [1, 2^31)");
+    if (ldd < N) return set_error(KNN_EINVAL, "ldd (%lld) must be >= N (%lld)", (long long)ldd, (long long)N);
+    if (k < 1 || k > N) return set_error(KNN_EINVAL, "k must be in [1, N] (k=%d, N=%lld)", k, (long long)N);
+    if (k > MAX_K) return set_error(KNN_EINVAL, "k above %d is not supported", MAX_K);
+    if (M < 0) return set_error(KNN_EINVAL, "M must be >= 0");
+    if (M == 0) return KNN_OK;
+    cudaStream_t st = stream_of(opt);
+    Staged sg;
+    const void* Dd = nullptr;
+    KNN_TRY(sg.in(D, (static_cast<size_t>(M - 1) * ldd + N) * sizeof(float), st, &Dd));
+    void *oi = nullptr, *ov = nullptr;
+    KNN_TRY(sg.out(out_idx, static_cast<size_t>(M) * k * sizeof(int32_t), &oi));
+    KNN_TRY(sg.out(out_val, static_cast<size_t>(M) * k * sizeof(float), &ov));
+    Arena sz;
+    uint32_t* flags = sz.take<uint32_t>(M);
+    void* base = nullptr;
+    KNN_TRY(workspace_get(sz.used(), &base));
+    Arena ar(static_cast<char*>(base), sz.used());
+    flags = ar.take<uint32_t>(M);
+    SelectParams sp{};
+    sp.D = static_cast<const float*>(Dd);
+    sp.ldd = ldd;
+    sp.M = M;
+    sp.N = N;
+    sp.k = k;
+    sp.km = k;
+    sp.cap = k;
+    sp.flags = flags;
+    KNN_CK(launch_select_topk(sp, static_cast<int32_t*>(oi), static_cast<float*>(ov), st));
+    std::vector<uint32_t> hf(static_cast<size_t>(M));
+    KNN_CK(cudaMemcpyAsync(hf.data(), flags, M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < M; ++i)
+        if (hf[static_cast<size_t>(i)] & ROW_SELECT_ERROR)
+            return set_error(KNN_EINVAL, "row %lld holds NaN (or the select gave up)", (long long)i);
+    KNN_TRY(sg.copy_back(st));
+    return KNN_OK;
+}
+
+int knn_distances(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, float* out_D, int64_t ldd,
+                  int32_t full, const knn_options* opt) {
+    using namespace knn;
+    g_last_error.clear();
+    if (!Q || !C || !out_D) return set_error(KNN_EINVAL, "NULL pointer argument");
+    if (d < 1 || N < 1 || M < 0) return set_error(KNN_EINVAL, "bad sizes");
+    if (ldd < N) return set_error(KNN_EINVAL, "ldd must be >= N");
+    if (M == 0) return KNN_OK;
+    cudaStream_t st = stream_of(opt);
+    Staged sg;
+    const void *Qd = nullptr, *Cd = nullptr;
+    KNN_TRY(sg.in(Q, static_cast<size_t>(M) * d * sizeof(float), st, &Qd));
+    KNN_TRY(sg.in(C, static_cast<size_t>(N) * d * sizeof(float), st, &Cd));
+    void* Dd = nullptr;
+    KNN_TRY(sg.out(out_D, (static_cast<size_t>(M - 1) * ldd + N) * sizeof(float), &Dd));
+    Arena sz;
+    sz.take<PrepGlobals>(2);
+    sz.take<float>(N);
+    sz.take<float>(M);
+    void* base = nullptr;
+    KNN_TRY(workspace_get(sz.used(), &base));
+    Arena ar(static_cast<char*>(base), sz.used());
+    PrepGlobals* g = ar.take<PrepGlobals>(2);
+    float* cn = ar.take<float>(N);
+    float* qn = ar.take<float>(M);
+    KNN_CK(cudaMemsetAsync(g, 0, 2 * sizeof(PrepGlobals), st));
+    KNN_CK(launch_prep(static_cast<const float*>(Cd), N, d, P_FP32, cn, nullptr, nullptr, nullptr, 0, nullptr, g, st));
+    if (full)
+        KNN_CK(launch_prep(static_cast<const float*>(Qd), M, d, P_FP32, qn, nullptr, nullptr, nullptr, 0, nullptr,
+                           g + 1, st));
+    KNN_CK(launch_gemm_simt(static_cast<const float*>(Qd), M, 0, static_cast<const float*>(Cd), N, d, cn,
+                            full ? qn : nullptr, static_cast<float*>(Dd), ldd, 0, st));
+    KNN_TRY(sg.copy_back(st));
+    KNN_CK(cudaStreamSynchronize(st));
+    return KNN_OK;
+}
+
+int knn_search_batched(knn_problem* probs, int32_t count, const knn_options* opt) {
+    using namespace knn;
+    g_last_error.clear();
+    if (count < 0 || (count > 0 && !probs)) return set_error(KNN_EINVAL, "bad problem list");
+    int first = KNN_OK;
+    for (int32_t i = 0; i < count; ++i) {
+        knn_problem& p = probs[i];
+        const bool graph = p.exclude_self != 0;
+        const float* Q = graph ? p.C : p.Q;
+        p.status = search_impl(Q, p.M, p.C, p.N, p.d, p.k, p.out_idx, p.out_dist, opt, graph);
+        if (p.status != KNN_OK && first == KNN_OK) first = p.status;
+    }
+    return first;
+}
+
+const char* knn_status_string(int status) {
+    switch (status) {
+        case KNN_OK: return "KNN_OK";
+        case KNN_EINVAL: return "KNN_EINVAL";
+        case KNN_ENOMEM: return "KNN_ENOMEM";
+        case KNN_ECUDA: return "KNN_ECUDA";
+        case KNN_ETIMEOUT: return "KNN_ETIMEOUT";
+        case KNN_EINTERNAL: return "KNN_EINTERNAL";
+        case KNN_EUNSUPPORTED: return "KNN_EUNSUPPORTED";
+        default: return "KNN_UNKNOWN";
+    }
+}
+
+const char* knn_last_error(void) { return knn::g_last_error.c_str(); }
+
+void knn_shutdown(void) { knn::workspace_release_all(); }
+
+const char* knn_version(void) { return "0.1.0"; }
+
+}  // extern "C"

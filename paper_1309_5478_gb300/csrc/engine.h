@@ -1,0 +1,99 @@
+// Host-side runtime structures of the engine (internal; not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "internal.h"
+#include "knn.h"
+
+namespace knn {
+
+constexpr int MAX_CAP = 2048;  // largest candidate list per row
+constexpr int MAX_K = 1024;
+
+extern thread_local std::string g_last_error;
+int set_error(int status, const char* fmt, ...);
+
+#define KNN_CK(expr)                                                                                   \
+    do {                                                                                               \
+        cudaError_t e_ = (expr);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            return ::knn::set_error(-3, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, \
+                                    __LINE__);                                                         \
+        }                                                                                              \
+    } while (0)
+
+#define KNN_TRY(expr)          \
+    do {                       \
+        int s_ = (expr);       \
+        if (s_ != 0) return s_; \
+    } while (0)
+
+// Bump allocator over the workspace. With base == nullptr it only measures.
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    Arena() = default;
+    Arena(char* b, size_t c) : base(b), cap(c) {}
+    bool sizing() const { return base == nullptr; }
+    size_t used() const { return off; }
+    template <typename T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+// One k-NN problem with device pointers.
+struct Problem {
+    const float* Q;
+    const float* C;
+    int64_t M, N;
+    int32_t d, k, m;
+    bool graph;           // k-NN graph: Q == C, row i excludes column i
+    const float* thr;     // optional per-row squared-distance thresholds (device), M entries
+    int32_t* out_idx;     // M x k
+    float* out_dist;      // M x k
+    int64_t slab_bytes;   // distance-matrix slab budget (0 = default)
+    int32_t precision;    // Precision
+    int32_t fused;        // -1 auto, 0, 1
+    int32_t flags;        // KNN_FLAG_*
+};
+
+struct PrepState {
+    PrepGlobals* gq;
+    PrepGlobals* gc;
+    float* qnorm2;
+    float* cnorm2;
+    float* qres;
+    float* cres;
+    float* qtn;
+    float* ctn;
+    float* E;
+    float* thr_dprime;  // per-row threshold converted to d' scale (or nullptr)
+    void* xq;           // reduced-precision queries (graph: shared with xc)
+    void* xc;
+    float* qscale;
+    float* cscale;
+    int32_t d_pad;
+};
+
+int workspace_get(size_t bytes, void** out);
+void workspace_release_all();
+bool is_device_pointer(const void* p);
+int pick_cap(int k, int km);
+
+cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool check_nan, cudaStream_t st);
+cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out, cudaStream_t st);
+
+// Runs one problem end to end (device pointers); fills stats when non-null.
+int run_problem(const Problem& pb, ::knn_stats* stats, cudaStream_t st);
+
+}  // namespace knn

@@ -1,0 +1,103 @@
+// Host-side declarations shared by the engine's translation units (not part of the ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace knn {
+
+enum Precision : int32_t { P_FP32 = 0, P_BF16 = 1, P_FP8 = 2 };
+
+// Statistics of one point set gathered by the prep kernel (device memory, zeroed before use).
+// Non-negative floats are stored as their bit patterns, whose unsigned order is the value order.
+struct PrepGlobals {
+    uint32_t max_norm2;   // max |x|^2
+    uint32_t max_abs;     // max |x_t|
+    uint32_t max_res;     // max |x - x~| (x~ = reduced-precision copy)
+    uint32_t max_tnorm;   // max |x~|
+    uint32_t nonfinite;   // rows holding NaN or Inf
+    uint32_t noninteger;  // rows holding a non-integer value
+    uint32_t pad[2];
+};
+
+// Per-row candidate state handed from the select to the re-rank.
+enum RowFlag : uint32_t {
+    ROW_TRUNCATED = 1u,       // candidate list reached capacity; the bound decides exactness
+    ROW_THRESHOLD_MISS = 2u,  // a supplied threshold kept fewer than k candidates
+    ROW_SELECT_ERROR = 4u,    // the select gave up (iteration limit)
+};
+
+enum RowStatus : uint32_t {
+    ROW_UNCERTIFIED = 1u,  // the re-rank could not prove the answer exact
+    ROW_FP64 = 2u,         // FP64 decided a near tie in this row
+};
+
+// Counters accumulated by the re-rank (device memory, zeroed per call).
+struct RerankCounters {
+    unsigned long long candidates;
+    unsigned long long fp64_rows;
+    unsigned long long uncertified;
+    unsigned long long truncated;
+    unsigned long long threshold_miss;
+    unsigned long long pad[3];
+};
+
+// ---- prep / bounds (prep.cu) ----
+cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precision, float* norm2, float* res,
+                        float* tnorm, void* xq, int32_t ldq, float* inv_scale, PrepGlobals* g, cudaStream_t st);
+
+// E[i]: bound on |approximate - exact| of every d'_ij of row i (0 in exact arithmetic).
+cudaError_t launch_bounds(const float* qnorm2, const float* qres, const float* qtnorm, int64_t M, int32_t d,
+                          int32_t d_pad, int32_t precision, const PrepGlobals* gq, const PrepGlobals* gc, float* E,
+                          cudaStream_t st);
+
+// ---- FP32 SIMT distance GEMM (gemm_simt.cu) ----
+// D[i*ldd + j] = cnorm2[j] - 2 q_i.c_j (+ qnorm2[i] when qnorm2 != nullptr); +inf where
+// exclude_self and row0 + i == j.
+cudaError_t launch_gemm_simt(const float* Q, int64_t M, int64_t row0, const float* C, int64_t N, int32_t d,
+                             const float* cnorm2, const float* qnorm2, float* D, int64_t ldd, int32_t exclude_self,
+                             cudaStream_t st);
+
+// ---- quick multi-select (select.cu) ----
+struct SelectParams {
+    const float* D;        // M x N values, row stride ldd
+    int64_t ldd, M, N;
+    int32_t k, km;         // answer size and always-kept candidate count (km >= k)
+    int32_t cap;           // candidate list capacity per row (>= km)
+    const float* E;        // per-row error bound (window = 2E); nullptr = 0
+    const float* thr;      // per-row initial threshold in D's scale; nullptr = none
+    uint64_t* cand;        // M x cap keys (value, column)
+    int32_t* count;        // M
+    uint64_t* bound;       // M: every key left out of the list is > bound[i]
+    uint32_t* flags;       // M: RowFlag bits
+    const int32_t* self_col;  // per-row excluded column (or nullptr)
+};
+cudaError_t launch_select(const SelectParams& p, cudaStream_t st);
+
+// Select output written directly as sorted (index, value) pairs: the k smallest per row.
+cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st);
+
+// ---- exact re-rank (rerank.cu) ----
+struct RerankParams {
+    const float* Q;        // M x d queries (rows of this slab)
+    const float* C;        // N x d corpus
+    int64_t M, N;
+    int32_t d, k, cap;
+    const uint64_t* cand;  // M x cap
+    const int32_t* count;
+    const uint64_t* bound;
+    const uint32_t* flags;
+    const float* E;        // per-row bound used for the candidates' approximate values
+    int32_t* out_idx;      // M x k
+    float* out_dist;       // M x k
+    uint32_t* row_status;  // M
+    RerankCounters* counters;
+};
+cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st);
+
+// Exact FP64 answer for a list of rows (last-resort path; slow, used for rows no other path certifies).
+cudaError_t launch_exact_rows_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,
+                                   int32_t exclude_self, const int32_t* rows, int32_t nrows, double* scratch,
+                                   int32_t* out_idx, float* out_dist, cudaStream_t st);
+
+}  // namespace knn

@@ -1,0 +1,216 @@
+// Pre-processing: per-row squared norms and the reduced-precision copies of the
+// points, plus the per-row error bounds used to keep reduced-precision selection
+// exact.
+//
+// Paper: Methods, "Distance calculation" -- the squared norms |x|^2 are vector
+// reductions computed before the distance product (there with a transform
+// iterator feeding reduction_by_key). Here one warp reduces one row and the
+// same pass writes the BF16 / FP8 copy consumed by the tensor-core GEMM.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+namespace {
+
+__device__ __forceinline__ void atomic_max_bits(uint32_t* p, float v) {
+    // v >= 0: the bit pattern's unsigned order is the value order
+    atomicMax(p, __float_as_uint(v));
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduced-precision rounding of one value: returns the rounded value as FP32 and
+// stores its encoding.
+template <int P>
+__device__ __forceinline__ float quantise(float x, float scale, void* xq, int64_t off) {
+    if constexpr (P == P_BF16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(x);
+        static_cast<__nv_bfloat16*>(xq)[off] = h;
+        return __bfloat162float(h);
+    } else if constexpr (P == P_FP8) {
+        __nv_fp8_e4m3 q(x * scale);  // saturating round-to-nearest-even
+        static_cast<__nv_fp8_e4m3*>(xq)[off] = q;
+        return static_cast<float>(q) / scale;  // scale is a power of two: exact
+    } else {
+        return x;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d,
+                                                   float* __restrict__ norm2, float* __restrict__ res,
+                                                   float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
+                                                   float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    const uint32_t lane = lane_id();
+    const float* x = X + row * static_cast<int64_t>(d);
+
+    float s2 = 0.f, amax = 0.f;
+    bool bad = false, nonint = false;
+    for (int32_t t = lane; t < d; t += 32) {
+        float v = x[t];
+        s2 = fmaf(v, v, s2);
+        amax = fmaxf(amax, fabsf(v));
+        bad |= !isfinite(v);
+        nonint |= (v != rintf(v));
+    }
+    s2 = warp_sum(s2);
+    amax = warp_maxf(amax);
+    bad = __any_sync(0xffffffffu, bad);
+    nonint = __any_sync(0xffffffffu, nonint);
+
+    float scale = 1.f;
+    if constexpr (P == P_FP8) {
+        // power-of-two scale putting the row's largest magnitude in (224, 448]
+        int e = 0;
+        if (amax > 0.f && isfinite(amax)) {
+            frexpf(amax / 448.f, &e);  // amax / 448 = m * 2^e, m in [0.5, 1)
+            e = -e;                    // amax * 2^-e... -> amax * 2^e in (224, 448]
+        }
+        scale = ldexpf(1.f, e);
+    }
+
+    if constexpr (P != P_FP32) {
+        float r2 = 0.f, t2 = 0.f;
+        const int64_t base = row * static_cast<int64_t>(ldq);
+        for (int32_t t = lane; t < ldq; t += 32) {
+            float v = t < d ? x[t] : 0.f;
+            float vq = quantise<P>(v, scale, xq, base + t);
+            float r = v - vq;  // exact: vq is v rounded to fewer bits
+            r2 = fmaf(r, r, r2);
+            t2 = fmaf(vq, vq, t2);
+        }
+        r2 = warp_sum(r2);
+        t2 = warp_sum(t2);
+        // upper bounds on the norms (FP32 sum and sqrt rounding absorbed by the factor)
+        const float inflate = 1.f + 0x1p-12f;
+        float rn = sqrtf(r2) * inflate, tn = sqrtf(t2) * inflate;
+        if (lane == 0) {
+            res[row] = rn;
+            tnorm[row] = tn;
+            if (inv_scale) inv_scale[row] = 1.f / scale;
+            atomic_max_bits(&g->max_res, rn);
+            atomic_max_bits(&g->max_tnorm, tn);
+        }
+    }
+    if (lane == 0) {
+        norm2[row] = s2;
+        if (!bad) {
+            atomic_max_bits(&g->max_norm2, s2);
+            atomic_max_bits(&g->max_abs, amax);
+        }
+        if (bad) atomicAdd(&g->nonfinite, 1u);
+        if (nonint) atomicAdd(&g->noninteger, 1u);
+    }
+}
+
+// Error bound of the ranking value d'_ij = |c_j|^2 - 2 q_i.c_j as computed by the
+// engine, against its exact value, for every j of row i.
+//   FP32:  an FMA chain over d products has |err| <= gamma_d sum|q_t c_t| <= gamma_d |q||c|
+//          (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 3.1); the norm
+//          |c|^2 has gamma_d |c|^2 and the final FMA one more rounding. With
+//          gamma_d <= (d + 2) 2^-24 and a factor 2 of safety:
+//          E_i = (d + 4) 2^-23 (Cmax^2 + 2 |q_i| Cmax).
+//   BF16 / FP8: with x = x~ + r (x~ the rounded copy), Cauchy-Schwarz gives
+//          |q.c - q~.c~| <= |q~||r_c| + |r_q||c~| + |r_q||r_c|, doubled for the -2 q.c term;
+//          the tensor-core FP32 accumulation is bounded like the FMA chain above
+//          (safety factor 4 over FP32's gamma for BF16, a 2^-14-unit accumulator for FP8).
+//   Exact arithmetic: integer-valued inputs with 4 d A^2 <= 2^24 (A the largest magnitude)
+//          make every product, partial sum and norm an exact FP32 integer, so E_i = 0.
+__global__ void bounds_kernel(const float* __restrict__ qnorm2, const float* __restrict__ qres,
+                              const float* __restrict__ qtnorm, int64_t M, int32_t d, int32_t d_pad,
+                              int32_t precision, const PrepGlobals* __restrict__ gq,
+                              const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const float amax = fmaxf(__uint_as_float(gq->max_abs), __uint_as_float(gc->max_abs));
+    const bool integer = gq->noninteger == 0 && gc->noninteger == 0;
+    const bool small = 4.0 * static_cast<double>(d_pad) * amax * amax <= 16777216.0;
+    const bool rep = precision == P_FP32 || (precision == P_BF16 && amax <= 256.f) ||
+                     (precision == P_FP8 && amax <= 16.f);
+    if (integer && small && rep) {
+        E[i] = 0.f;
+        return;
+    }
+    const float c2max = __uint_as_float(gc->max_norm2);
+    const float cmax = sqrtf(c2max) * (1.f + 0x1p-12f);
+    const float qn = sqrtf(qnorm2[i]) * (1.f + 0x1p-12f);
+    float e;
+    if (precision == P_FP32) {
+        e = static_cast<float>(d + 4) * 0x1p-23f * (c2max + 2.f * qn * cmax);
+    } else {
+        const float rmax = __uint_as_float(gc->max_res);
+        const float ctmax = __uint_as_float(gc->max_tnorm);
+        const float rq = qres[i], qt = qtnorm[i];
+        const float quant = 2.f * (qt * rmax + rq * (ctmax + rmax));
+        const float acc_unit = precision == P_BF16 ? 0x1p-22f : 0x1p-14f;
+        const float accum = static_cast<float>(d_pad + 4) * acc_unit * 2.f * qt * ctmax;
+        const float norms = static_cast<float>(d + 4) * 0x1p-23f * (c2max + 2.f * qn * cmax);
+        e = quant + accum + norms;
+    }
+    E[i] = e * (1.f + 0x1p-10f);
+}
+
+__global__ void thr_kernel(const float* __restrict__ thr, const float* __restrict__ qnorm2, int64_t M,
+                           float* __restrict__ out) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const float t = thr[i];
+    // non-finite or negative proposals mean "no threshold" for that row
+    out[i] = (t == t && t >= 0.f && t < F_INF) ? t - qnorm2[i] : F_INF;
+}
+
+}  // namespace
+
+cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out,
+                                       cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    thr_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, st>>>(thr, qnorm2, M, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precision, float* norm2, float* res,
+                        float* tnorm, void* xq, int32_t ldq, float* inv_scale, PrepGlobals* g, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const int warps = 8;
+    const unsigned blocks = static_cast<unsigned>((rows + warps - 1) / warps);
+    switch (precision) {
+        case P_FP32:
+            prep_kernel<P_FP32><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
+            break;
+        case P_BF16:
+            prep_kernel<P_BF16><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
+            break;
+        case P_FP8:
+            prep_kernel<P_FP8><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
+            break;
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(const float* qnorm2, const float* qres, const float* qtnorm, int64_t M, int32_t d,
+                          int32_t d_pad, int32_t precision, const PrepGlobals* gq, const PrepGlobals* gc, float* E,
+                          cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const unsigned blocks = static_cast<unsigned>((M + 255) / 256);
+    bounds_kernel<<<blocks, 256, 0, st>>>(qnorm2, qres, qtnorm, M, d, d_pad, precision, gq, gc, E);
+    return cudaGetLastError();
+}
+
+}  // namespace knn

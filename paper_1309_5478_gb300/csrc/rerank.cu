@@ -1,0 +1,288 @@
+// Exact re-rank of each row's candidate list.
+//
+// The candidate lists come from the selection (fused or not) on approximate
+// ranking values d'_ij = |c_j|^2 - 2 q_i.c_j (Methods, "Distance calculation").
+// Here every candidate's squared distance is recomputed in the direct difference
+// form sum_t (q_t - c_t)^2, which has no cancellation:
+//   - each lane adds its four products of a 16-byte group with FMAs and folds the
+//     group sum into a (sum, error) pair with Knuth's TwoSum; the warp reduction adds
+//     the pairs with TwoSum as well. The result's relative error is at most about
+//     8 units in the last place (2 for the rounded differences, 4 for the group sums,
+//     2 for the final roundings), below 2^-20.
+//   - the list is sorted by (FP32 distance, index). Neighbours in the sorted list that
+//     are within 2^-19 (relative) of each other around the first k positions form
+//     near-tie groups; their distances are recomputed in FP64 and the group re-sorted
+//     by (FP64 distance, index). FP64 therefore decides only the order of points whose
+//     FP32 distances cannot be told apart.
+//   - a row whose list was truncated is certified only if the k-th exact distance is
+//     below the smallest value any left-out point can have, bound - E (in d' scale).
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+#include "select_core.cuh"
+
+namespace knn {
+namespace {
+
+constexpr float TIE_REL = 0x1p-19f;
+
+__device__ __forceinline__ void group_sum(float4 q, float4 c, float& s, float& e) {
+    const float d0 = q.x - c.x, d1 = q.y - c.y, d2 = q.z - c.z, d3 = q.w - c.w;
+    float g = d0 * d0;
+    g = fmaf(d1, d1, g);
+    g = fmaf(d2, d2, g);
+    g = fmaf(d3, d3, g);
+    float t, err;
+    two_sum(s, g, t, err);
+    s = t;
+    e += err;
+}
+
+__device__ __forceinline__ float warp_reduce_pair(float s, float e) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float eo = __shfl_xor_sync(0xffffffffu, e, o);
+        float t, err;
+        two_sum(s, so, t, err);
+        s = t;
+        e = e + eo + err;
+    }
+    return s + e;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <bool VEC>
+__device__ __forceinline__ float sqdist_fp32(const float* __restrict__ q, const float* __restrict__ c, int d) {
+    const uint32_t lane = lane_id();
+    float s = 0.f, e = 0.f;
+    if (VEC) {
+        for (int t = static_cast<int>(lane) * 4; t < d; t += 128) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(q + t));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(c + t));
+            group_sum(a, b, s, e);
+        }
+    } else {
+        for (int t = static_cast<int>(lane) * 4; t < d; t += 128) {
+            float4 a, b;
+            a.x = q[t];
+            b.x = c[t];
+            a.y = t + 1 < d ? q[t + 1] : 0.f;
+            b.y = t + 1 < d ? c[t + 1] : 0.f;
+            a.z = t + 2 < d ? q[t + 2] : 0.f;
+            b.z = t + 2 < d ? c[t + 2] : 0.f;
+            a.w = t + 3 < d ? q[t + 3] : 0.f;
+            b.w = t + 3 < d ? c[t + 3] : 0.f;
+            group_sum(a, b, s, e);
+        }
+    }
+    return warp_reduce_pair(s, e);
+}
+
+// Two candidates at once (more loads in flight per lane).
+template <bool VEC>
+__device__ __forceinline__ void sqdist_fp32_x2(const float* __restrict__ q, const float* __restrict__ c0,
+                                               const float* __restrict__ c1, int d, float& r0, float& r1) {
+    if (!VEC) {
+        r0 = sqdist_fp32<false>(q, c0, d);
+        r1 = sqdist_fp32<false>(q, c1, d);
+        return;
+    }
+    const uint32_t lane = lane_id();
+    float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+    for (int t = static_cast<int>(lane) * 4; t < d; t += 128) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(q + t));
+        const float4 b0 = __ldg(reinterpret_cast<const float4*>(c0 + t));
+        const float4 b1 = __ldg(reinterpret_cast<const float4*>(c1 + t));
+        group_sum(a, b0, s0, e0);
+        group_sum(a, b1, s1, e1);
+    }
+    r0 = warp_reduce_pair(s0, e0);
+    r1 = warp_reduce_pair(s1, e1);
+}
+
+__device__ __forceinline__ double sqdist_fp64(const float* __restrict__ q, const float* __restrict__ c, int d) {
+    double s = 0.0;
+    for (int t = static_cast<int>(lane_id()); t < d; t += 32) {
+        const double diff = static_cast<double>(q[t]) - static_cast<double>(c[t]);
+        s = fma(diff, diff, s);
+    }
+    return warp_sum_d(s);
+}
+
+template <bool VEC>
+__global__ void rerank_kernel(RerankParams p, int P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long blk_cnt[5];
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const int warps = static_cast<int>(blockDim.x / 32);
+    const uint32_t lane = lane_id();
+    if (threadIdx.x < 5) blk_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
+    if (row < p.M) {
+        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
+        double* D64 = reinterpret_cast<double*>(K + P);
+        const int count = p.count[row];
+        const uint32_t flags = p.flags[row];
+        const float* q = p.Q + row * static_cast<int64_t>(p.d);
+        const uint64_t* cand = p.cand + row * static_cast<int64_t>(p.cap);
+        const int d = p.d;
+
+        // 1. direct-difference FP32 distances
+        int c = 0;
+        for (; c + 1 < count; c += 2) {
+            const uint32_t j0 = key_idx(cand[c]);
+            const uint32_t j1 = key_idx(cand[c + 1]);
+            float r0, r1;
+            sqdist_fp32_x2<VEC>(q, p.C + static_cast<int64_t>(j0) * d, p.C + static_cast<int64_t>(j1) * d, d, r0,
+                                r1);
+            if (lane == 0) {
+                K[c] = make_key(r0, j0);
+                K[c + 1] = make_key(r1, j1);
+            }
+        }
+        if (c < count) {
+            const uint32_t j0 = key_idx(cand[c]);
+            const float r0 = sqdist_fp32<VEC>(q, p.C + static_cast<int64_t>(j0) * d, d);
+            if (lane == 0) K[c] = make_key(r0, j0);
+        }
+        for (int i = count + static_cast<int>(lane); i < P; i += 32) K[i] = KEY_MAX;
+        for (int i = static_cast<int>(lane); i < P; i += 32) D64[i] = -1.0;
+        __syncwarp();
+        warp_bitonic_sort_smem(K, P);
+
+        // 2. near ties around the first k positions, settled in FP64 (skipped when the
+        //    inputs make FP32 exact: then equal values are true ties, already ordered by index)
+        const int k = p.k;
+        const int kk = count < k ? count : k;
+        const bool exact = p.E != nullptr && p.E[row] == 0.f;
+        bool used64 = false;
+        bool giant_tie = false;
+        if (!exact && kk > 0) {
+            // near(i): positions i and i+1 cannot be ordered by their FP32 values
+            auto near = [&](int i) -> bool {
+                const float a = key_val(K[i]), b = key_val(K[i + 1]);
+                return (b - a) <= TIE_REL * b;
+            };
+            bool any = false;
+            for (int i = static_cast<int>(lane); i < kk && i + 1 < count; i += 32) any |= near(i);
+            any = __any_sync(0xffffffffu, any);
+            if (any) {
+                used64 = true;
+                int s = 0;
+                while (s < kk) {
+                    // group [s, e]: maximal run with near(s..e-1)
+                    int e = s;
+                    while (e + 1 < count && near(e)) ++e;
+                    if (e > s) {
+                        for (int m = s; m <= e; ++m) {
+                            const uint32_t j = key_idx(K[m]);
+                            const double v = sqdist_fp64(q, p.C + static_cast<int64_t>(j) * d, d);
+                            if (lane == 0) D64[m] = v;
+                        }
+                        __syncwarp();
+                        // rank every member by (FP64 distance, index) and place it
+                        const int g = e - s + 1;
+                        uint64_t my_key[4];
+                        double my_val[4];
+                        int my_pos[4];
+                        int nm = 0;
+                        for (int m = s + static_cast<int>(lane); m <= e && nm < 4; m += 32, ++nm) {
+                            const double vm = D64[m];
+                            const uint32_t jm = key_idx(K[m]);
+                            int rank = 0;
+                            for (int o = s; o <= e; ++o) {
+                                const double vo = D64[o];
+                                const uint32_t jo = key_idx(K[o]);
+                                rank += (vo < vm || (vo == vm && jo < jm)) ? 1 : 0;
+                            }
+                            my_key[nm] = make_key(static_cast<float>(vm), jm);
+                            my_val[nm] = vm;
+                            my_pos[nm] = s + rank;
+                        }
+                        __syncwarp();
+                        giant_tie |= g > 128;  // left unordered: the row is reported uncertified
+                        if (g <= 128) {
+                            for (int t = 0; t < nm; ++t) {
+                                K[my_pos[t]] = my_key[t];
+                                D64[my_pos[t]] = my_val[t];
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    s = e + 1;
+                }
+            }
+        }
+
+        // 3. outputs and certificate
+        const int64_t ob = row * static_cast<int64_t>(k);
+        for (int i = static_cast<int>(lane); i < k; i += 32) {
+            if (i < kk) {
+                const double v64 = D64[i];
+                p.out_idx[ob + i] = static_cast<int32_t>(key_idx(K[i]));
+                p.out_dist[ob + i] = v64 >= 0.0 ? static_cast<float>(v64) : key_val(K[i]);
+            } else {
+                p.out_idx[ob + i] = -1;
+                p.out_dist[ob + i] = F_INF;
+            }
+        }
+        bool certified = kk == k && !(flags & ROW_SELECT_ERROR) && !giant_tie;
+        if (certified && (flags & ROW_TRUNCATED) && !exact) {
+            // every left-out point has d' >= value(bound), so d2 >= value(bound) + |q|^2 - E
+            double qn2 = 0.0;
+            for (int t = static_cast<int>(lane); t < d; t += 32) qn2 = fma((double)q[t], (double)q[t], qn2);
+            qn2 = warp_sum_d(qn2);
+            const double dk = D64[kk - 1] >= 0.0 ? D64[kk - 1] : (double)key_val(K[kk - 1]) * (1.0 + 0x1p-19);
+            const double bnd = (double)key_val(p.bound[row]);
+            const double e = p.E ? (double)p.E[row] * (1.0 + 0x1p-10) : 0.0;
+            const double slack = 0x1p-20 * (fabs(bnd) + qn2 + dk);
+            certified = dk - qn2 < bnd - e - slack;
+        }
+        if (lane == 0) {
+            p.row_status[row] = (certified ? 0u : ROW_UNCERTIFIED) | (used64 ? ROW_FP64 : 0u);
+            atomicAdd(&blk_cnt[0], static_cast<unsigned long long>(count));
+            if (used64) atomicAdd(&blk_cnt[1], 1ull);
+            if (!certified) atomicAdd(&blk_cnt[2], 1ull);
+            if (flags & ROW_TRUNCATED) atomicAdd(&blk_cnt[3], 1ull);
+            if (flags & ROW_THRESHOLD_MISS) atomicAdd(&blk_cnt[4], 1ull);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && p.counters) {
+        atomicAdd(&p.counters->candidates, blk_cnt[0]);
+        if (blk_cnt[1]) atomicAdd(&p.counters->fp64_rows, blk_cnt[1]);
+        if (blk_cnt[2]) atomicAdd(&p.counters->uncertified, blk_cnt[2]);
+        if (blk_cnt[3]) atomicAdd(&p.counters->truncated, blk_cnt[3]);
+        if (blk_cnt[4]) atomicAdd(&p.counters->threshold_miss, blk_cnt[4]);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const int P = pow2_ceil(p.cap > 32 ? p.cap : 32);
+    const size_t per_warp = static_cast<size_t>(P) * 16;
+    int warps = static_cast<int>((64u * 1024u) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    const size_t smem = per_warp * warps;
+    const bool vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
+                     (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
+    auto kern = vec ? rerank_kernel<true> : rerank_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (p.M + warps - 1) / warps;
+    kern<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(p, P);
+    return cudaGetLastError();
+}
+
+}  // namespace knn

@@ -1,0 +1,238 @@
+// Unfused quick multi-select over a materialised distance matrix.
+//
+// Paper: Methods, "GPU-based quick multi-select". One warp owns one row of the
+// distance matrix. The row is streamed once from HBM with coalesced 16-byte loads;
+// a running threshold tau acts as the pivot of that first partition: each 32-wide
+// group votes with a ballot on "key <= tau" and the survivors are written, at
+// offsets taken from popc of the lower lanes' bits, into a shared-memory buffer
+// (the left part; the right part is discarded since only the K smallest are
+// wanted, the K < L branch of the recursion). When the buffer fills, the warp runs
+// the quick multi-select of select_core.cuh on it (ballot partitions, ping-pong
+// between two shared-memory arrays, a reference list instead of copies) to find the
+// k-th and (k+m)-th smallest keys, and tau shrinks to
+//     max(key_(k+m), ceiling(value(key_k) + window)),
+// where window is twice the row's bound on the error of the matrix values. Every key
+// dropped is therefore larger than the final tau, and the kept keys include every
+// point whose exact distance can still be among the k smallest (the band argument
+// in the design notes). Output per row: the candidate keys, their count, tau
+// (every left-out key is > tau) and flags.
+#include "internal.h"
+#include "select_core.cuh"
+
+namespace knn {
+namespace {
+
+constexpr int SEL_U = 4;  // 16-byte loads in flight per lane per step
+
+struct RowBuffers {
+    uint64_t* A;
+    uint64_t* B;
+    int* seg_s;
+    uint32_t* seg_e;
+};
+
+__host__ __device__ constexpr size_t warp_smem_bytes(int bufk) {
+    return static_cast<size_t>(bufk) * 16 + static_cast<size_t>(SEG_MAX) * 8;
+}
+
+template <bool VEC, bool CHECK_NAN>
+__device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t idx4, float (&v)[4], bool& nan_seen) {
+    if (VEC && idx4 + 4 <= N) {
+        const float4 f = ldg_stream_f4(rowp + idx4);
+        v[0] = f.x;
+        v[1] = f.y;
+        v[2] = f.z;
+        v[3] = f.w;
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = (idx4 + c < N) ? rowp[idx4 + c] : F_INF;
+    }
+    if (CHECK_NAN) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) nan_seen |= (v[c] != v[c]);
+    }
+}
+
+// Streams one row, keeping keys <= tau in A (compacting when full). Returns false on a
+// reference-list overflow. n, tau, truncated, tau_cap are updated in place.
+template <bool VEC, bool CHECK_NAN>
+__device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
+                                         int bufk, int k, int km, float window, uint64_t tau_thr, int& n,
+                                         uint64_t& tau, bool& truncated, bool& nan_seen) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = lanemask_lt();
+    const int keep_mid = bufk - 128 > km ? bufk - 128 : km;
+    const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
+    for (int64_t base = 0; base < N; base += 32 * 4 * SEL_U) {
+        float v[SEL_U][4];
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+            const int64_t idx4 = base + (static_cast<int64_t>(u) * 32 + lane) * 4;
+            load_group<VEC, CHECK_NAN>(rowp, N, idx4, v[u], nan_seen);
+        }
+        const uint32_t tau_hi = static_cast<uint32_t>(tau >> 32);
+        bool maybe = false;
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) maybe |= float_to_ord(v[u][c]) <= tau_hi;
+        if (!__any_sync(0xffffffffu, maybe)) continue;
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t j = base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c;
+                const uint64_t key = make_key(v[u][c], static_cast<uint32_t>(j));
+                const bool keep = j < N && j != self_col && key <= tau;
+                const uint32_t b = __ballot_sync(0xffffffffu, keep);
+                if (b == 0u) continue;
+                if (keep) rb.A[n + __popc(b & lt_mask)] = key;
+                n += __popc(b);
+                if (n > bufk - 32) {
+                    __syncwarp();
+                    const uint64_t limit = tau;
+                    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, k, km, window, limit, keep_mid,
+                                                  trunc_mid);
+                    if (!r.ok) return false;
+                    n = r.n;
+                    tau = r.tau;
+                    truncated |= r.truncated;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    (void)tau_thr;
+    return true;
+}
+
+template <bool VEC, bool CHECK_NAN, bool TOPK>
+__global__ void select_rows_kernel(SelectParams p, int bufk, int64_t self_offset, int32_t* __restrict__ out_idx,
+                                   float* __restrict__ out_val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const int warps = static_cast<int>(blockDim.x / 32);
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
+    if (row >= p.M) return;
+    const uint32_t lane = lane_id();
+    unsigned char* mine = smem_raw + static_cast<size_t>(warp) * warp_smem_bytes(bufk);
+    RowBuffers rb;
+    rb.A = reinterpret_cast<uint64_t*>(mine);
+    rb.B = rb.A + bufk;
+    rb.seg_s = reinterpret_cast<int*>(rb.B + bufk);
+    rb.seg_e = reinterpret_cast<uint32_t*>(rb.seg_s + SEG_MAX);
+
+    const float* rowp = p.D + row * p.ldd;
+    const float window = p.E ? 2.f * p.E[row] : 0.f;
+    const int64_t self_col = p.self_col ? static_cast<int64_t>(p.self_col[row])
+                                        : (self_offset >= 0 ? row + self_offset : -1);
+    uint64_t tau_thr = KEY_MAX;
+    if (p.thr) {
+        const float t = p.thr[row];
+        if (t == t && t < F_INF) tau_thr = key_ceiling(t);
+    }
+    uint32_t flags = 0;
+    bool nan_seen = false;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        int n = 0;
+        uint64_t tau = tau_thr;
+        bool truncated = false;
+        bool ok = scan_row<VEC, CHECK_NAN>(rowp, p.N, self_col, rb, bufk, p.k, p.km, window, tau_thr, n, tau,
+                                           truncated, nan_seen);
+        CompactResult r{};
+        if (ok && n > 0) {
+            r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, p.k, p.km, window, tau, p.cap, p.cap);
+            ok = r.ok;
+        } else {
+            r.n = 0;
+            r.tau = tau;
+            r.band = KEY_MAX;
+            r.ok = ok;
+        }
+        if (!ok) {
+            flags |= ROW_SELECT_ERROR;
+            r.n = 0;
+        }
+        truncated |= r.truncated;
+        if (tau_thr != KEY_MAX && ok && (r.n < p.k || r.band > tau_thr)) {
+            // the supplied threshold cut into the answer or its band: plain multi-select instead
+            flags |= ROW_THRESHOLD_MISS;
+            tau_thr = KEY_MAX;
+            continue;
+        }
+        if (CHECK_NAN && __any_sync(0xffffffffu, nan_seen)) flags |= ROW_SELECT_ERROR;
+        if constexpr (TOPK) {
+            const int kk = r.n < p.k ? r.n : p.k;
+            const int P = pow2_ceil(kk > 1 ? kk : 1);
+            for (int i = static_cast<int>(lane); i < P; i += 32)
+                if (i >= kk) rb.A[i] = KEY_MAX;
+            __syncwarp();
+            warp_bitonic_sort_smem(rb.A, P);
+            for (int i = static_cast<int>(lane); i < p.k; i += 32) {
+                const bool have = i < kk;
+                out_idx[row * p.k + i] = have ? static_cast<int32_t>(key_idx(rb.A[i])) : -1;
+                out_val[row * p.k + i] = have ? key_val(rb.A[i]) : F_INF;
+            }
+            if (lane == 0) p.flags[row] = flags | (truncated ? ROW_TRUNCATED : 0u);
+        } else {
+            uint64_t* dst = p.cand + row * p.cap;
+            for (int i = static_cast<int>(lane); i < r.n; i += 32) dst[i] = rb.A[i];
+            if (lane == 0) {
+                p.count[row] = r.n;
+                p.bound[row] = r.tau;
+                p.flags[row] = flags | (truncated ? ROW_TRUNCATED : 0u);
+            }
+        }
+        return;
+    }
+}
+
+template <bool VEC, bool CHECK_NAN, bool TOPK>
+cudaError_t launch_variant(const SelectParams& p, int bufk, int64_t self_offset, int32_t* out_idx, float* out_val,
+                           cudaStream_t st) {
+    const size_t per_warp = warp_smem_bytes(bufk);
+    int warps = static_cast<int>((96u * 1024u) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    const size_t smem = per_warp * warps;
+    auto kern = select_rows_kernel<VEC, CHECK_NAN, TOPK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (p.M + warps - 1) / warps;
+    kern<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(p, bufk, self_offset, out_idx, out_val);
+    return cudaGetLastError();
+}
+
+int choose_bufk(int km, int cap) {
+    int want = 2 * km + 160;
+    if (want < cap + 64) want = cap + 64;
+    int b = pow2_ceil(want);
+    return b < 512 ? 512 : b;
+}
+
+}  // namespace
+
+// self_offset < 0: nothing excluded; otherwise column row + self_offset is skipped.
+cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool check_nan, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const int bufk = choose_bufk(p.km, p.cap);
+    const bool vec = (p.ldd % 4 == 0) && (reinterpret_cast<uintptr_t>(p.D) % 16 == 0);
+    if (vec) {
+        return check_nan ? launch_variant<true, true, false>(p, bufk, self_offset, nullptr, nullptr, st)
+                         : launch_variant<true, false, false>(p, bufk, self_offset, nullptr, nullptr, st);
+    }
+    return check_nan ? launch_variant<false, true, false>(p, bufk, self_offset, nullptr, nullptr, st)
+                     : launch_variant<false, false, false>(p, bufk, self_offset, nullptr, nullptr, st);
+}
+
+cudaError_t launch_select(const SelectParams& p, cudaStream_t st) { return launch_select_ex(p, -1, false, st); }
+
+cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const int bufk = choose_bufk(p.k, p.k);
+    const bool vec = (p.ldd % 4 == 0) && (reinterpret_cast<uintptr_t>(p.D) % 16 == 0);
+    return vec ? launch_variant<true, true, true>(p, bufk, -1, out_idx, out_val, st)
+               : launch_variant<false, true, true>(p, bufk, -1, out_idx, out_val, st);
+}
+
+}  // namespace knn

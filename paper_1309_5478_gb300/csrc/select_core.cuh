@@ -1,0 +1,371 @@
+// Warp-level quick multi-select building blocks (device code, header-only so that
+// the unfused select kernel and the fused GEMM epilogue share them).
+//
+// Paper: Methods, "GPU-based quick multi-select".
+//   - One warp owns one row ("each array is handled by a single thread warp").
+//   - A partition reads each element once into a register, votes with a warp ballot
+//     on "element >= pivot", and derives every lane's destination from a popc of the
+//     ballot bits of the lower lanes: elements below the pivot are written from the
+//     left end of the auxiliary array, the others from the right end. No prefix sum,
+//     no second read. Two running counters (the paper's g_< and g_>=) give the warp's
+//     write offsets.
+//   - Input and auxiliary arrays swap roles after each partition ("ping-pong"), and
+//     rather than copying data back, a list of references (start, end, which array)
+//     records where every part of the row lives.
+//   - Recursion: with L elements left of the pivot and K wanted, K < L continues on the
+//     left part, K > L keeps the left part and continues on the right with K - L.
+// Deviations for GB300 (reasons in the design notes):
+//   - the partition is three-way (< pivot, == pivot, > pivot), so that a pivot equal
+//     to the minimum still makes progress (the two-way rule can loop forever there);
+//   - keys are 64-bit (value, index) pairs, unique within a row, so the answer is
+//     unique and ties go to the lower index;
+//   - the pivot is the median of the segment's first, middle and last keys
+//     (the paper does not say how it picks pivots);
+//   - segments of at most 32 keys are finished with a 32-lane bitonic network.
+#pragma once
+
+#include "common.cuh"
+
+namespace knn {
+
+constexpr int SEG_MAX = 128;        // references kept per warp
+constexpr uint32_t SEG_IN_B = 1u << 30;
+constexpr uint32_t SEG_SORTED = 1u << 31;
+constexpr uint32_t SEG_END_MASK = SEG_IN_B - 1;
+
+template <typename K>
+__device__ __forceinline__ K shfl_key(K v, int src);
+template <>
+__device__ __forceinline__ uint32_t shfl_key<uint32_t>(uint32_t v, int src) {
+    return __shfl_sync(0xffffffffu, v, src);
+}
+template <>
+__device__ __forceinline__ uint64_t shfl_key<uint64_t>(uint64_t v, int src) {
+    return shfl_u64(v, src);
+}
+
+template <typename K>
+__device__ __forceinline__ K shfl_xor_key(K v, int m) {
+    if constexpr (sizeof(K) == 8) {
+        return __shfl_xor_sync(0xffffffffu, static_cast<unsigned long long>(v), m);
+    } else {
+        return __shfl_xor_sync(0xffffffffu, v, m);
+    }
+}
+
+// Ascending bitonic sort of one key per lane across the warp.
+template <typename K>
+__device__ __forceinline__ K warp_sort32(K v) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            K o = shfl_xor_key(v, j);
+            const bool up = (lane & k) == 0 || k == 32;
+            const bool lower = (lane & j) == 0;
+            v = (lower == up) ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+template <typename K>
+__device__ __forceinline__ K median3(K a, K b, K c) {
+    K lo = a < b ? a : b, hi = a < b ? b : a;
+    K m = hi < c ? hi : c;
+    return lo > m ? lo : m;
+}
+
+// Three-way ballot partition of src[s, e) around `pivot` into dst[s, e):
+// dst = [keys < pivot][keys == pivot][keys > pivot]. Returns the sizes of the first
+// two parts. All 32 lanes must call it with the same arguments.
+template <typename K>
+__device__ __forceinline__ void partition3(const K* src, K* dst, int s, int e, K pivot, int& nlt, int& neq) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = lanemask_lt();
+    int g_lt = 0, g_gt = 0, g_eq = 0;  // the paper's running counters
+    for (int base = s; base < e; base += 32) {
+        const int i = base + static_cast<int>(lane);
+        const bool valid = i < e;
+        const K v = valid ? src[i] : K(0);
+        const bool lt = valid && v < pivot;
+        const bool gt = valid && v > pivot;
+        const uint32_t b_lt = __ballot_sync(0xffffffffu, lt);
+        const uint32_t b_gt = __ballot_sync(0xffffffffu, gt);
+        const uint32_t b_eq = __ballot_sync(0xffffffffu, valid && !lt && !gt);
+        if (lt) dst[s + g_lt + __popc(b_lt & lt_mask)] = v;
+        if (gt) dst[e - 1 - g_gt - __popc(b_gt & lt_mask)] = v;
+        g_lt += __popc(b_lt);
+        g_gt += __popc(b_gt);
+        g_eq += __popc(b_eq);
+    }
+    for (int t = static_cast<int>(lane); t < g_eq; t += 32) dst[s + g_lt + t] = pivot;
+    __syncwarp();
+    nlt = g_lt;
+    neq = g_eq;
+}
+
+// Key of rank r (0-based) among a[0, n) (duplicates allowed). a and b are both
+// clobbered (b is the auxiliary array).
+template <typename K>
+__device__ K warp_rank_select(K* a, K* b, int n, int r) {
+    K* src = a;
+    K* dst = b;
+    int lo = 0, hi = n;
+    const uint32_t lane = lane_id();
+    for (int guard = 0; guard < 4096; ++guard) {
+        const int len = hi - lo;
+        if (len <= 32) {
+            K v = static_cast<int>(lane) < len ? src[lo + lane] : static_cast<K>(~K(0));
+            v = warp_sort32(v);
+            return shfl_key(v, r - lo);
+        }
+        const K pivot = median3(src[lo], src[lo + len / 2], src[hi - 1]);
+        int nlt, neq;
+        partition3(src, dst, lo, hi, pivot, nlt, neq);
+        if (r < lo + nlt) {
+            hi = lo + nlt;
+        } else if (r < lo + nlt + neq) {
+            return pivot;
+        } else {
+            lo = lo + nlt + neq;
+        }
+        K* t = src;
+        src = dst;
+        dst = t;
+    }
+    return src[r];  // unreachable: every partition removes at least the pivot
+}
+
+// Reference list over a row's keys held in two arrays A and B: every position p in
+// [0, n) belongs to exactly one segment, and the segment says which array holds the
+// live key for p. Keys are unique, so the segment of position p holds exactly the
+// keys of ranks [start, end).
+struct SegRefs {
+    int* start;     // shared or global, SEG_MAX entries
+    uint32_t* end;  // end | SEG_IN_B | SEG_SORTED
+    int count;      // warp-uniform
+};
+
+__device__ __forceinline__ void seg_init(SegRefs& s, int n) {
+    if (lane_id() == 0) {
+        s.start[0] = 0;
+        s.end[0] = static_cast<uint32_t>(n);
+    }
+    s.count = 1;
+    __syncwarp();
+}
+
+// Returns the key of rank r; refines the reference list. Returns false (and leaves
+// *out untouched) when the list is full.
+__device__ __forceinline__ bool seg_rank(SegRefs& s, uint64_t* A, uint64_t* B, int r, uint64_t* out) {
+    const uint32_t lane = lane_id();
+    for (int guard = 0; guard < 4096; ++guard) {
+        // find the segment holding position r
+        int found = -1;
+        for (int base = 0; base < s.count && found < 0; base += 32) {
+            const int t = base + static_cast<int>(lane);
+            bool hit = false;
+            if (t < s.count) {
+                const int st = s.start[t];
+                const int en = static_cast<int>(s.end[t] & SEG_END_MASK);
+                hit = st <= r && r < en;
+            }
+            const uint32_t b = __ballot_sync(0xffffffffu, hit);
+            if (b) found = base + __ffs(b) - 1;
+        }
+        if (found < 0) return false;
+        const int st = s.start[found];
+        const uint32_t ef = s.end[found];
+        const int en = static_cast<int>(ef & SEG_END_MASK);
+        uint64_t* src = (ef & SEG_IN_B) ? B : A;
+        uint64_t* dst = (ef & SEG_IN_B) ? A : B;
+        const int len = en - st;
+        if ((ef & SEG_SORTED) || len == 1) {
+            *out = src[r];
+            return true;
+        }
+        if (len <= 32) {
+            uint64_t v = static_cast<int>(lane) < len ? src[st + lane] : KEY_MAX;
+            v = warp_sort32(v);
+            if (static_cast<int>(lane) < len) src[st + lane] = v;
+            if (lane == 0) s.end[found] = ef | SEG_SORTED;
+            __syncwarp();
+            *out = shfl_key(v, r - st);
+            return true;
+        }
+        if (s.count + 2 > SEG_MAX) return false;
+        const uint64_t pivot = median3(src[st], src[st + len / 2], src[en - 1]);
+        int nlt, neq;
+        partition3(src, dst, st, en, pivot, nlt, neq);  // neq == 1: keys are unique
+        const uint32_t where = (ef & SEG_IN_B) ? 0u : SEG_IN_B;
+        // the segment now lives in dst as [left][pivot][right]; replace it by its parts
+        if (lane == 0) {
+            int c = s.count;
+            const int mid = st + nlt;
+            s.start[found] = mid;  // the pivot alone, already in place
+            s.end[found] = static_cast<uint32_t>(mid + 1) | where | SEG_SORTED;
+            if (nlt > 0) {
+                s.start[c] = st;
+                s.end[c] = static_cast<uint32_t>(mid) | where;
+                ++c;
+            }
+            if (mid + 1 < en) {
+                s.start[c] = mid + 1;
+                s.end[c] = static_cast<uint32_t>(en) | where;
+                ++c;
+            }
+        }
+        s.count += (nlt > 0 ? 1 : 0) + (st + nlt + 1 < en ? 1 : 0);
+        __syncwarp();
+        if (r == st + nlt) {
+            *out = pivot;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Gathers the live keys of every segment into B[0, n) (position order).
+__device__ __forceinline__ void seg_materialise_in_B(const SegRefs& s, const uint64_t* A, uint64_t* B) {
+    const uint32_t lane = lane_id();
+    for (int t = 0; t < s.count; ++t) {
+        const uint32_t ef = s.end[t];
+        if (ef & SEG_IN_B) continue;
+        const int st = s.start[t];
+        const int en = static_cast<int>(ef & SEG_END_MASK);
+        for (int p = st + static_cast<int>(lane); p < en; p += 32) B[p] = A[p];
+    }
+    __syncwarp();
+}
+
+// Number of live keys <= limit over all segments.
+__device__ __forceinline__ int seg_count_le(const SegRefs& s, const uint64_t* A, const uint64_t* B, uint64_t limit) {
+    const uint32_t lane = lane_id();
+    int c = 0;
+    for (int t = 0; t < s.count; ++t) {
+        const uint32_t ef = s.end[t];
+        const uint64_t* src = (ef & SEG_IN_B) ? B : A;
+        const int st = s.start[t];
+        const int en = static_cast<int>(ef & SEG_END_MASK);
+        for (int p = st + static_cast<int>(lane); p < en; p += 32) c += src[p] <= limit ? 1 : 0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
+}
+
+// Ballot/popc compaction of the keys <= limit of src[0, n) into dst (any memory);
+// returns how many were written (the order of src is kept).
+__device__ __forceinline__ int compact_le(const uint64_t* src, int n, uint64_t limit, uint64_t* dst) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = lanemask_lt();
+    int w = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + static_cast<int>(lane);
+        const uint64_t v = i < n ? src[i] : KEY_MAX;
+        const bool keep = i < n && v <= limit;
+        const uint32_t b = __ballot_sync(0xffffffffu, keep);
+        if (keep) dst[w + __popc(b & lt_mask)] = v;
+        w += __popc(b);
+    }
+    __syncwarp();
+    return w;
+}
+
+__device__ __forceinline__ int count_le(const uint64_t* src, int n, uint64_t limit) {
+    const uint32_t lane = lane_id();
+    int c = 0;
+    for (int i = static_cast<int>(lane); i < n; i += 32) c += src[i] <= limit ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    return c;
+}
+
+// Result of shrinking one row's candidate buffer.
+struct CompactResult {
+    int n;              // keys kept, now in A[0, n)
+    uint64_t tau;       // every key dropped so far is > tau (the row's new threshold)
+    uint64_t band;      // max(km-th key, ceiling(value of k-th key + window)): the unclamped threshold
+    bool truncated;     // capacity truncation: kept fewer keys than the band asks for
+    bool ok;            // false when the reference list overflowed (caller must give up)
+};
+
+// Quick multi-select on the row's buffer A[0, n) (B is the auxiliary array):
+// finds the k-th and km-th smallest keys, sets the threshold to the band
+//   tau = max(key_km, ceiling(value(key_k) + window))   (window > 0)
+//   tau = key_km                                          (window == 0)
+// clamped by tau_limit, keeps the keys <= tau, and if more than keep_max remain,
+// keeps only the keep_trunc smallest (truncation). Requires n >= 1.
+__device__ __forceinline__ CompactResult compact_row(uint64_t* A, uint64_t* B, int* seg_start, uint32_t* seg_end,
+                                                     int n, int k, int km, float window, uint64_t tau_limit,
+                                                     int keep_max, int keep_trunc) {
+    CompactResult res{};
+    res.ok = true;
+    SegRefs s{seg_start, seg_end, 0};
+    seg_init(s, n);
+    const int kk = k < n ? k : n;
+    const int kme = km < n ? km : n;
+    uint64_t key_km = 0, key_k = 0;
+    if (!seg_rank(s, A, B, kme - 1, &key_km)) res.ok = false;
+    if (res.ok && kk != kme && !seg_rank(s, A, B, kk - 1, &key_k)) res.ok = false;
+    if (kk == kme) key_k = key_km;
+    if (!res.ok) return res;
+    uint64_t band = key_km;
+    if (window > 0.f) {
+        const uint64_t wk = key_ceiling(key_val(key_k) + window);
+        band = wk > band ? wk : band;
+    }
+    if (n < km) band = KEY_MAX;  // fewer keys than the row keeps: nothing may be dropped yet
+    res.band = band;
+    uint64_t tau = band < tau_limit ? band : tau_limit;
+    int keep = seg_count_le(s, A, B, tau);
+    if (keep > keep_max) {
+        // too many keys inside the band: keep the keep_trunc smallest only
+        uint64_t kt = 0;
+        if (!seg_rank(s, A, B, keep_trunc - 1, &kt)) {
+            res.ok = false;
+            return res;
+        }
+        tau = kt;
+        res.truncated = true;
+    }
+    seg_materialise_in_B(s, A, B);
+    res.n = compact_le(B, n, tau, A);
+    res.tau = tau;
+    return res;
+}
+
+}  // namespace knn
+
+namespace knn {
+
+// Ascending bitonic sort of X[0, P) by one warp (P a power of two).
+template <typename K>
+__device__ __forceinline__ void warp_bitonic_sort_smem(K* X, int P) {
+    const uint32_t lane = lane_id();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = static_cast<int>(lane); i < (P >> 1); i += 32) {
+                const int lo = (i / stride) * 2 * stride + (i % stride);
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const K a = X[lo], b = X[hi];
+                if ((a > b) == up) {
+                    X[lo] = b;
+                    X[hi] = a;
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int pow2_ceil(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace knn

@@ -1,0 +1,72 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry point
+that include/knn.h declares; host-only calls (status strings, argument checks)
+work without touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(knn\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1309_5478_gb300 import binding, build
+    if not os.path.exists(binding.LIB_PATH):
+        build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_search_batched",
+                     "knn_status_string", "knn_last_error", "knn_shutdown"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1309_5478_gb300 import binding
+    names = declared_functions()
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(binding.EXPORTS) <= set(names)
+
+
+def test_host_only_calls(lib):
+    assert lib.knn_status_string(-1) == b"KNN_EINVAL"
+    assert lib.knn_status_string(0) == b"KNN_OK"
+    assert lib.knn_version().decode().count(".") == 2
+
+
+def test_argument_checks_need_no_device(lib):
+    from paper_1309_5478_gb300 import binding
+    X = np.zeros((10, 4), dtype=np.float32)
+    oi = np.zeros((10, 3), dtype=np.int32)
+    od = np.zeros((10, 3), dtype=np.float32)
+    p = X.ctypes.data
+    assert lib.knng_build(p, 10, 4, 0, oi.ctypes.data, od.ctypes.data) == binding.KNN_EINVAL
+    assert b"k must be" in lib.knn_last_error()
+    assert lib.knng_build(p, 10, 4, 10, oi.ctypes.data, od.ctypes.data) == binding.KNN_EINVAL
+    assert lib.knng_build(p, 10, 0, 3, oi.ctypes.data, od.ctypes.data) == binding.KNN_EINVAL
+    assert lib.knng_build(None, 10, 4, 3, oi.ctypes.data, od.ctypes.data) == binding.KNN_EINVAL
+    opt = binding.KnnOptions()
+    lib.knn_options_init(ctypes.byref(opt))
+    assert opt.rerank_extra == 32 and opt.precision == binding.KNN_AUTO and opt.fused == -1
+    assert lib.knn_search(p, 10, p, 10, 4, 11, oi.ctypes.data, od.ctypes.data, ctypes.byref(opt)) == binding.KNN_EINVAL
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_1309_5478_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
