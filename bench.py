@@ -153,14 +153,12 @@ def oracle_sample_rate(X: np.ndarray, k: int, seconds: float, seed: int) -> dict
     import oracle
     from paper_1309_5478_gb300 import inputs
     n = X.shape[0]
-    probe = inputs.sample_rows(n, 4, seed=seed)
+    threads = oracle.threads()
+    probe = inputs.sample_rows(n, threads, seed=seed)  # one row per thread
     t0 = time.perf_counter()
     oracle.knng(X, k, rows=probe)
-    dt = max(time.perf_counter() - t0, 1e-6)
-    threads = oracle.threads()
-    # rows run in parallel across threads: size the sample to fill ~`seconds`
-    per_row = dt / max(1, min(len(probe), threads)) if len(probe) < threads else dt / len(probe)
-    want = int(max(threads, min(4096, seconds / max(per_row, 1e-9) * min(1.0, len(probe) / threads))))
+    rate = len(probe) / max(time.perf_counter() - t0, 1e-6)
+    want = int(min(8192, max(threads, seconds * rate)))
     want = max(threads, (want // threads) * threads)
     rows = inputs.sample_rows(n, want, seed=seed + 1)
     t0 = time.perf_counter()

@@ -15,6 +15,7 @@
 #include "engine.h"
 #include "internal.h"
 #include "knn.h"
+#include "tc_fused.h"
 
 namespace knn {
 
@@ -108,60 +109,206 @@ int pick_cap(int k, int km) {
 
 namespace {
 
+// Events and launch counts of one call (KNN_FLAG_TIMING).
+struct Timing {
+    bool on = false;
+    std::vector<cudaEvent_t> gemm;  // pairs around each distance-kernel launch
+    int64_t launches = 0;
+    int32_t gemm_launches = 0;
+    int record_gemm(cudaStream_t st, bool begin) {
+        if (!on) return KNN_OK;
+        cudaEvent_t e;
+        KNN_CK(cudaEventCreate(&e));
+        gemm.push_back(e);
+        KNN_CK(cudaEventRecord(e, st));
+        (void)begin;
+        return KNN_OK;
+    }
+    float gemm_ms() const {
+        float g = 0.f;
+        for (size_t i = 0; i + 1 < gemm.size(); i += 2) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, gemm[i], gemm[i + 1]);
+            g += t;
+        }
+        return g;
+    }
+    ~Timing() {
+        for (auto& e : gemm) cudaEventDestroy(e);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // plain form: FP32 SIMT GEMM slab -> unfused quick multi-select -> exact re-rank
 // ---------------------------------------------------------------------------
-struct PlainLayout {
-    PrepState ps{};
+struct PlainBuffers {
     float* D = nullptr;
     uint64_t* cand = nullptr;
     int32_t* count = nullptr;
     uint64_t* bound = nullptr;
     uint32_t* flags = nullptr;
-    uint32_t* row_status = nullptr;
-    RerankCounters* counters = nullptr;
-    int32_t* fb_rows = nullptr;
-    double* fp64_scratch = nullptr;
-    int64_t R = 0, ldn = 0, fp64_chunk = 0;
+    int64_t R = 0, ldn = 0;
     int km = 0, cap = 0;
 };
 
-void layout_plain(const Problem& pb, Arena& ar, PlainLayout& L) {
+void layout_plain_buffers(const Problem& pb, int64_t rows, Arena& ar, PlainBuffers& B) {
+    B.km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
+    B.cap = pick_cap(pb.k, B.km);
+    B.ldn = (pb.N + 31) / 32 * 32;
+    const int64_t budget = pb.slab_bytes > 0 ? pb.slab_bytes : (int64_t(4) << 30);
+    B.R = std::max<int64_t>(128, budget / (B.ldn * 4) / 128 * 128);
+    B.R = std::min<int64_t>(B.R, (rows + 127) / 128 * 128);
+    B.D = ar.take<float>(static_cast<size_t>(B.R) * B.ldn);
+    B.cand = ar.take<uint64_t>(static_cast<size_t>(B.R) * B.cap);
+    B.count = ar.take<int32_t>(B.R);
+    B.bound = ar.take<uint64_t>(B.R);
+    B.flags = ar.take<uint32_t>(B.R);
+}
+
+// Rows [0, M) of Q against the whole corpus. Row r excludes column self_col[r] (when
+// self_col != nullptr) or r + self_offset (when self_offset >= 0).
+int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* self_col, int64_t self_offset,
+                   const float* cnorm2, const float* E, const float* thr, int32_t* out_idx, float* out_dist,
+                   uint32_t* row_status, const PlainBuffers& B, RerankCounters* counters, cudaStream_t st,
+                   Timing& tm) {
+    for (int64_t r0 = 0; r0 < M; r0 += B.R) {
+        const int64_t rows = std::min<int64_t>(B.R, M - r0);
+        KNN_TRY(tm.record_gemm(st, true));
+        KNN_CK(launch_gemm_simt(Q + r0 * pb.d, rows, 0, pb.C, pb.N, pb.d, cnorm2, nullptr, B.D, B.ldn, 0, st));
+        KNN_TRY(tm.record_gemm(st, false));
+        SelectParams sp{};
+        sp.D = B.D;
+        sp.ldd = B.ldn;
+        sp.M = rows;
+        sp.N = pb.N;
+        sp.k = pb.k;
+        sp.km = B.km;
+        sp.cap = B.cap;
+        sp.E = E + r0;
+        sp.thr = thr ? thr + r0 : nullptr;
+        sp.cand = B.cand;
+        sp.count = B.count;
+        sp.bound = B.bound;
+        sp.flags = B.flags;
+        sp.self_col = self_col ? self_col + r0 : nullptr;
+        KNN_CK(launch_select_ex(sp, self_offset >= 0 ? self_offset + r0 : -1, false, st));
+        RerankParams rp{};
+        rp.Q = Q + r0 * pb.d;
+        rp.C = pb.C;
+        rp.M = rows;
+        rp.N = pb.N;
+        rp.d = pb.d;
+        rp.k = pb.k;
+        rp.cap = B.cap;
+        rp.cand = B.cand;
+        rp.count = B.count;
+        rp.bound = B.bound;
+        rp.flags = B.flags;
+        rp.E = E + r0;
+        rp.out_idx = out_idx + r0 * pb.k;
+        rp.out_dist = out_dist + r0 * pb.k;
+        rp.row_status = row_status + r0;
+        rp.counters = counters;
+        KNN_CK(launch_rerank(rp, st));
+        tm.launches += 3;
+        tm.gemm_launches += 1;
+    }
+    return KNN_OK;
+}
+
+// Everything one call needs besides the form-specific buffers.
+struct CommonLayout {
+    PrepState ps{};
+    float* E32 = nullptr;        // FP32-form bounds (the fallback's)
+    uint32_t* row_status = nullptr;
+    RerankCounters* counters = nullptr;
+    int* status = nullptr;
+    // fallback of uncertified rows
+    int64_t fb_rows_max = 0, fp64_chunk = 0;
+    int32_t* fb_rows = nullptr;
+    float* fb_Q = nullptr;
+    float* fb_E = nullptr;
+    float* fb_T = nullptr;
+    int32_t* fb_oi = nullptr;
+    float* fb_od = nullptr;
+    uint32_t* fb_status = nullptr;
+    PlainBuffers fb_plain{};
+    double* fp64_scratch = nullptr;
+    int64_t n_pad = 0;
+};
+
+void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena& ar, CommonLayout& L) {
     const bool same = pb.graph;
     PrepState& ps = L.ps;
+    L.n_pad = (pb.N + 255) / 256 * 256;
     ps.gq = ar.take<PrepGlobals>(1);
     ps.gc = same ? ps.gq : ar.take<PrepGlobals>(1);
-    ps.cnorm2 = ar.take<float>(pb.N);
+    ps.cnorm2 = ar.take<float>(L.n_pad);
     ps.qnorm2 = same ? ps.cnorm2 : ar.take<float>(pb.M);
     ps.E = ar.take<float>(pb.M);
     ps.thr_dprime = pb.thr ? ar.take<float>(pb.M) : nullptr;
-    L.km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
-    L.cap = pick_cap(pb.k, L.km);
-    L.ldn = (pb.N + 31) / 32 * 32;
-    const int64_t budget = pb.slab_bytes > 0 ? pb.slab_bytes : (int64_t(4) << 30);
-    L.R = std::max<int64_t>(128, budget / (L.ldn * 4) / 128 * 128);
-    L.R = std::min<int64_t>(L.R, (pb.M + 127) / 128 * 128);
-    L.D = ar.take<float>(static_cast<size_t>(L.R) * L.ldn);
-    L.cand = ar.take<uint64_t>(static_cast<size_t>(L.R) * L.cap);
-    L.count = ar.take<int32_t>(L.R);
-    L.bound = ar.take<uint64_t>(L.R);
-    L.flags = ar.take<uint32_t>(L.R);
+    if (prec != P_FP32) {
+        const int elem = prec == P_BF16 ? 2 : 1;
+        const int per = 128 / elem;
+        ps.d_pad = (pb.d + per - 1) / per * per;
+        const size_t row_bytes = static_cast<size_t>(ps.d_pad) * elem;
+        ps.cres = ar.take<float>(L.n_pad);
+        ps.ctn = ar.take<float>(L.n_pad);
+        ps.qres = same ? ps.cres : ar.take<float>(pb.M);
+        ps.qtn = same ? ps.ctn : ar.take<float>(pb.M);
+        ps.xc = ar.take<char>(row_bytes * pb.N);
+        ps.xq = same ? ps.xc : ar.take<char>(row_bytes * pb.M);
+        if (prec == P_FP8) {
+            ps.cscale = ar.take<float>(L.n_pad);
+            ps.qscale = same ? ps.cscale : ar.take<float>(pb.M);
+        }
+        L.E32 = ar.take<float>(pb.M);
+    } else {
+        ps.d_pad = pb.d;
+        L.E32 = ps.E;
+    }
     L.row_status = ar.take<uint32_t>(pb.M);
     L.counters = ar.take<RerankCounters>(1);
+    L.status = ar.take<int>(1);
     L.fb_rows = ar.take<int32_t>(pb.M);
     L.fp64_chunk = std::max<int64_t>(1, std::min<int64_t>(pb.M, (int64_t(1) << 30) / (pb.N * 8)));
     L.fp64_scratch = ar.take<double>(static_cast<size_t>(L.fp64_chunk) * pb.N);
+    if (with_fallback_plain) {
+        L.fb_rows_max = std::min<int64_t>(pb.M, 16384);
+        L.fb_Q = ar.take<float>(static_cast<size_t>(L.fb_rows_max) * pb.d);
+        L.fb_E = ar.take<float>(L.fb_rows_max);
+        L.fb_T = ar.take<float>(L.fb_rows_max);
+        L.fb_oi = ar.take<int32_t>(static_cast<size_t>(L.fb_rows_max) * pb.k);
+        L.fb_od = ar.take<float>(static_cast<size_t>(L.fb_rows_max) * pb.k);
+        L.fb_status = ar.take<uint32_t>(L.fb_rows_max);
+        layout_plain_buffers(pb, L.fb_rows_max, ar, L.fb_plain);
+    }
 }
 
-int prep_and_check(const Problem& pb, const PrepState& ps, cudaStream_t st, knn_stats* stats) {
+int prep_and_check(const Problem& pb, int prec, const CommonLayout& L, cudaStream_t st, knn_stats* stats,
+                   Timing& tm) {
+    const PrepState& ps = L.ps;
     const bool same = pb.graph;
     KNN_CK(cudaMemsetAsync(ps.gq, 0, sizeof(PrepGlobals), st));
     if (!same) KNN_CK(cudaMemsetAsync(ps.gc, 0, sizeof(PrepGlobals), st));
-    KNN_CK(launch_prep(pb.C, pb.N, pb.d, P_FP32, ps.cnorm2, nullptr, nullptr, nullptr, 0, nullptr, ps.gc, st));
-    if (!same)
-        KNN_CK(launch_prep(pb.Q, pb.M, pb.d, P_FP32, ps.qnorm2, nullptr, nullptr, nullptr, 0, nullptr, ps.gq, st));
-    KNN_CK(launch_bounds(ps.qnorm2, nullptr, nullptr, pb.M, pb.d, pb.d, P_FP32, ps.gq, ps.gc, ps.E, st));
-    if (pb.thr) KNN_CK(launch_threshold_to_dprime(pb.thr, ps.qnorm2, pb.M, ps.thr_dprime, st));
+    if (L.n_pad > pb.N) KNN_CK(cudaMemsetAsync(ps.cnorm2 + pb.N, 0xff, (L.n_pad - pb.N) * sizeof(float), st));
+    const int ldq = prec == P_BF16 ? ps.d_pad : (prec == P_FP8 ? ps.d_pad : 0);
+    KNN_CK(launch_prep(pb.C, pb.N, pb.d, prec, ps.cnorm2, ps.cres, ps.ctn, ps.xc, ldq, ps.cscale, ps.gc, st));
+    ++tm.launches;
+    if (!same) {
+        KNN_CK(launch_prep(pb.Q, pb.M, pb.d, prec, ps.qnorm2, ps.qres, ps.qtn, ps.xq, ldq, ps.qscale, ps.gq, st));
+        ++tm.launches;
+    }
+    KNN_CK(launch_bounds(ps.qnorm2, ps.qres, ps.qtn, pb.M, pb.d, ps.d_pad, prec, ps.gq, ps.gc, ps.E, st));
+    ++tm.launches;
+    if (prec != P_FP32) {
+        KNN_CK(launch_bounds(ps.qnorm2, nullptr, nullptr, pb.M, pb.d, pb.d, P_FP32, ps.gq, ps.gc, L.E32, st));
+        ++tm.launches;
+    }
+    if (pb.thr) {
+        KNN_CK(launch_threshold_to_dprime(pb.thr, ps.qnorm2, pb.M, ps.thr_dprime, st));
+        ++tm.launches;
+    }
     PrepGlobals hq{}, hc{};
     KNN_CK(cudaMemcpyAsync(&hq, ps.gq, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaMemcpyAsync(&hc, ps.gc, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
@@ -174,144 +321,256 @@ int prep_and_check(const Problem& pb, const PrepState& ps, cudaStream_t st, knn_
         uint32_t u = std::max(hq.max_abs, hc.max_abs);
         std::memcpy(&amax, &u, 4);
         stats->exact_arithmetic =
-            (hq.noninteger == 0 && hc.noninteger == 0 && 4.0 * pb.d * double(amax) * amax <= 16777216.0) ? 1 : 0;
+            (hq.noninteger == 0 && hc.noninteger == 0 && 4.0 * ps.d_pad * double(amax) * amax <= 16777216.0) ? 1 : 0;
     }
     return KNN_OK;
 }
 
+// Host list of rows with `bit` set in status[0, M).
+int rows_with(const uint32_t* status_d, int64_t M, uint32_t bit, cudaStream_t st, std::vector<int32_t>& rows) {
+    std::vector<uint32_t> h(static_cast<size_t>(M));
+    KNN_CK(cudaMemcpyAsync(h.data(), status_d, M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    rows.clear();
+    for (int64_t i = 0; i < M; ++i)
+        if (h[static_cast<size_t>(i)] & bit) rows.push_back(static_cast<int32_t>(i));
+    return KNN_OK;
+}
+
+int exact_fp64_rows(const Problem& pb, const CommonLayout& L, const std::vector<int32_t>& rows, cudaStream_t st,
+                    Timing& tm) {
+    if (rows.empty()) return KNN_OK;
+    if (pb.k > 2048) return set_error(KNN_EINTERNAL, "uncertified rows with k > 2048");
+    KNN_CK(cudaMemcpyAsync(L.fb_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    for (size_t r = 0; r < rows.size(); r += static_cast<size_t>(L.fp64_chunk)) {
+        const int32_t n = static_cast<int32_t>(std::min<size_t>(L.fp64_chunk, rows.size() - r));
+        KNN_CK(launch_exact_rows_fp64(pb.Q, pb.C, pb.N, pb.d, pb.k, pb.graph ? 1 : 0, L.fb_rows + r, n,
+                                      L.fp64_scratch, pb.out_idx, pb.out_dist, st));
+        ++tm.launches;
+    }
+    KNN_CK(cudaStreamSynchronize(st));
+    return KNN_OK;
+}
+
+// Plain FP32 recompute of uncertified rows of a reduced-precision pass; rows the
+// plain form cannot certify either go to FP64. Returns the number of FP64 rows.
+int plain_fallback(const Problem& pb, const CommonLayout& L, const std::vector<int32_t>& rows, cudaStream_t st,
+                   Timing& tm, int64_t* n_fp64) {
+    std::vector<int32_t> still;
+    for (size_t r0 = 0; r0 < rows.size(); r0 += static_cast<size_t>(L.fb_rows_max)) {
+        const int32_t n = static_cast<int32_t>(std::min<size_t>(L.fb_rows_max, rows.size() - r0));
+        KNN_CK(cudaMemcpyAsync(L.fb_rows, rows.data() + r0, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        KNN_CK(launch_gather_rows(pb.Q, pb.d, L.fb_rows, n, L.E32, nullptr, L.fb_Q, L.fb_E, nullptr, st));
+        RerankCounters* ctr = L.counters;  // counts of the fallback are not reported separately
+        KNN_TRY(plain_pipeline(pb, L.fb_Q, n, pb.graph ? L.fb_rows : nullptr, -1, L.ps.cnorm2, L.fb_E, nullptr,
+                               L.fb_oi, L.fb_od, L.fb_status, L.fb_plain, ctr, st, tm));
+        KNN_CK(launch_scatter_out(L.fb_rows, n, pb.k, L.fb_oi, L.fb_od, pb.out_idx, pb.out_dist, st));
+        tm.launches += 2;
+        std::vector<int32_t> bad;
+        KNN_TRY(rows_with(L.fb_status, n, ROW_UNCERTIFIED, st, bad));
+        for (int32_t b : bad) still.push_back(rows[r0 + static_cast<size_t>(b)]);
+    }
+    *n_fp64 = static_cast<int64_t>(still.size());
+    return exact_fp64_rows(pb, L, still, st, tm);
+}
+
+void fill_stats(knn_stats* stats, const Problem& pb, const RerankCounters& hc, int64_t fallback, int prec, int fused,
+                const Timing& tm, cudaEvent_t* ev) {
+    if (!stats) return;
+    stats->rows = pb.M;
+    stats->candidates = static_cast<int64_t>(hc.candidates);
+    stats->rows_truncated = static_cast<int64_t>(hc.truncated);
+    stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
+    stats->rows_fallback = fallback;
+    stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
+    stats->threshold_misses = static_cast<int64_t>(hc.threshold_miss);
+    stats->precision_used = prec;
+    stats->fused_used = fused;
+    stats->kernel_launches = tm.launches;
+    stats->gemm_launches = tm.gemm_launches;
+    stats->gemm_flops = 2.0 * double(pb.M) * double(pb.N) * double(pb.d);
+    if (tm.on) {
+        float a = 0, b = 0, c = 0, d = 0;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        cudaEventElapsedTime(&c, ev[2], ev[3]);
+        cudaEventElapsedTime(&d, ev[3], ev[4]);
+        stats->ms_prep = a;
+        stats->ms_select = b;
+        stats->ms_rerank = c;
+        stats->ms_fallback = d;
+        stats->ms_total = a + b + c + d;
+        stats->ms_gemm = tm.gemm_ms();
+    }
+}
+
+struct Events {
+    cudaEvent_t ev[5] = {};
+    bool on = false;
+    int init(bool t) {
+        on = t;
+        if (on)
+            for (auto& e : ev) KNN_CK(cudaEventCreate(&e));
+        return KNN_OK;
+    }
+    int rec(int i, cudaStream_t st) {
+        if (on) KNN_CK(cudaEventRecord(ev[i], st));
+        return KNN_OK;
+    }
+    ~Events() {
+        if (on)
+            for (auto& e : ev) cudaEventDestroy(e);
+    }
+};
+
 int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
-    PlainLayout L;
-    Arena sz;
-    layout_plain(pb, sz, L);
-    void* base = nullptr;
-    KNN_TRY(workspace_get(sz.used(), &base));
-    Arena ar(static_cast<char*>(base), sz.used());
-    L = PlainLayout{};
-    layout_plain(pb, ar, L);
-
-    cudaEvent_t ev[4] = {};
-    const bool timing = stats && (pb.flags & KNN_FLAG_TIMING);
-    if (timing) {
-        for (auto& e : ev) KNN_CK(cudaEventCreate(&e));
-        KNN_CK(cudaEventRecord(ev[0], st));
+    CommonLayout L;
+    PlainBuffers B;
+    {
+        Arena sz;
+        layout_common(pb, P_FP32, false, sz, L);
+        layout_plain_buffers(pb, pb.M, sz, B);
+        void* base = nullptr;
+        KNN_TRY(workspace_get(sz.used(), &base));
+        Arena ar(static_cast<char*>(base), sz.used());
+        L = CommonLayout{};
+        B = PlainBuffers{};
+        layout_common(pb, P_FP32, false, ar, L);
+        layout_plain_buffers(pb, pb.M, ar, B);
     }
-    KNN_TRY(prep_and_check(pb, L.ps, st, stats));
+    Timing tm;
+    tm.on = stats && (pb.flags & KNN_FLAG_TIMING);
+    Events ev;
+    KNN_TRY(ev.init(tm.on));
+    KNN_TRY(ev.rec(0, st));
+    KNN_TRY(prep_and_check(pb, P_FP32, L, st, stats, tm));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
-    if (timing) KNN_CK(cudaEventRecord(ev[1], st));
-
-    int64_t launches = (pb.graph ? 1 : 2) + 1 + (pb.thr ? 1 : 0);
-    std::vector<cudaEvent_t> gev;
-    for (int64_t r0 = 0; r0 < pb.M; r0 += L.R) {
-        const int64_t rows = std::min<int64_t>(L.R, pb.M - r0);
-        if (timing) {
-            gev.emplace_back();
-            gev.emplace_back();
-            KNN_CK(cudaEventCreate(&gev[gev.size() - 2]));
-            KNN_CK(cudaEventCreate(&gev[gev.size() - 1]));
-            KNN_CK(cudaEventRecord(gev[gev.size() - 2], st));
-        }
-        KNN_CK(launch_gemm_simt(pb.Q + r0 * pb.d, rows, 0, pb.C, pb.N, pb.d, L.ps.cnorm2, nullptr, L.D, L.ldn, 0,
-                                st));
-        if (timing) KNN_CK(cudaEventRecord(gev.back(), st));
-        launches += 3;
-        SelectParams sp{};
-        sp.D = L.D;
-        sp.ldd = L.ldn;
-        sp.M = rows;
-        sp.N = pb.N;
-        sp.k = pb.k;
-        sp.km = L.km;
-        sp.cap = L.cap;
-        sp.E = L.ps.E + r0;
-        sp.thr = L.ps.thr_dprime ? L.ps.thr_dprime + r0 : nullptr;
-        sp.cand = L.cand;
-        sp.count = L.count;
-        sp.bound = L.bound;
-        sp.flags = L.flags;
-        sp.self_col = nullptr;
-        KNN_CK(launch_select_ex(sp, pb.graph ? r0 : -1, false, st));
-        RerankParams rp{};
-        rp.Q = pb.Q + r0 * pb.d;
-        rp.C = pb.C;
-        rp.M = rows;
-        rp.N = pb.N;
-        rp.d = pb.d;
-        rp.k = pb.k;
-        rp.cap = L.cap;
-        rp.cand = L.cand;
-        rp.count = L.count;
-        rp.bound = L.bound;
-        rp.flags = L.flags;
-        rp.E = L.ps.E + r0;
-        rp.out_idx = pb.out_idx + r0 * pb.k;
-        rp.out_dist = pb.out_dist + r0 * pb.k;
-        rp.row_status = L.row_status + r0;
-        rp.counters = L.counters;
-        KNN_CK(launch_rerank(rp, st));
-    }
-    if (timing) KNN_CK(cudaEventRecord(ev[2], st));
-
+    KNN_TRY(ev.rec(1, st));
+    KNN_TRY(plain_pipeline(pb, pb.Q, pb.M, nullptr, pb.graph ? 0 : -1, L.ps.cnorm2, L.ps.E, L.ps.thr_dprime,
+                           pb.out_idx, pb.out_dist, L.row_status, B, L.counters, st, tm));
+    KNN_TRY(ev.rec(2, st));
+    KNN_TRY(ev.rec(3, st));
     RerankCounters hc{};
     KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
     int64_t fallback = 0;
     if (hc.uncertified > 0 && !(pb.flags & KNN_FLAG_NO_FALLBACK)) {
-        std::vector<uint32_t> hs(static_cast<size_t>(pb.M));
-        KNN_CK(cudaMemcpyAsync(hs.data(), L.row_status, pb.M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        KNN_CK(cudaStreamSynchronize(st));
         std::vector<int32_t> rows;
-        for (int64_t i = 0; i < pb.M; ++i)
-            if (hs[static_cast<size_t>(i)] & ROW_UNCERTIFIED) rows.push_back(static_cast<int32_t>(i));
-        if (pb.k > 2048) return set_error(KNN_EINTERNAL, "uncertified rows with k > 2048");
-        KNN_CK(cudaMemcpyAsync(L.fb_rows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        for (size_t r = 0; r < rows.size(); r += static_cast<size_t>(L.fp64_chunk)) {
-            const int32_t n = static_cast<int32_t>(std::min<size_t>(L.fp64_chunk, rows.size() - r));
-            KNN_CK(launch_exact_rows_fp64(pb.Q, pb.C, pb.N, pb.d, pb.k, pb.graph ? 1 : 0, L.fb_rows + r, n,
-                                          L.fp64_scratch, pb.out_idx, pb.out_dist, st));
-            ++launches;
-        }
+        KNN_TRY(rows_with(L.row_status, pb.M, ROW_UNCERTIFIED, st, rows));
+        KNN_TRY(exact_fp64_rows(pb, L, rows, st, tm));
         fallback = static_cast<int64_t>(rows.size());
     }
-    if (timing) KNN_CK(cudaEventRecord(ev[3], st));
+    KNN_TRY(ev.rec(4, st));
     KNN_CK(cudaStreamSynchronize(st));
-    if (stats) {
-        stats->rows = pb.M;
-        stats->candidates = static_cast<int64_t>(hc.candidates);
-        stats->rows_truncated = static_cast<int64_t>(hc.truncated);
-        stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
-        stats->rows_fallback = fallback;
-        stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
-        stats->threshold_misses = static_cast<int64_t>(hc.threshold_miss);
-        stats->precision_used = KNN_FP32;
-        stats->fused_used = 0;
-        stats->kernel_launches = launches;
-        stats->gemm_launches = static_cast<int32_t>((pb.M + L.R - 1) / L.R);
-        stats->gemm_flops = 2.0 * double(pb.M) * double(pb.N) * double(pb.d);
-        if (timing) {
-            float g = 0.f;
-            for (size_t i = 0; i + 1 < gev.size(); i += 2) {
-                float t = 0.f;
-                cudaEventElapsedTime(&t, gev[i], gev[i + 1]);
-                g += t;
-            }
-            stats->ms_gemm = g;
-        }
-        if (timing) {
-            float a = 0, b = 0, c = 0;
-            cudaEventElapsedTime(&a, ev[0], ev[1]);
-            cudaEventElapsedTime(&b, ev[1], ev[2]);
-            cudaEventElapsedTime(&c, ev[2], ev[3]);
-            stats->ms_prep = a;
-            stats->ms_select = b;
-            stats->ms_rerank = 0.f;
-            stats->ms_fallback = c;
-            stats->ms_total = a + b + c;
-        }
+    fill_stats(stats, pb, hc, fallback, KNN_FP32, 0, tm, ev.ev);
+    return KNN_OK;
+}
+
+int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
+    CommonLayout L;
+    uint64_t* cand = nullptr;
+    int32_t* count = nullptr;
+    uint64_t* bound = nullptr;
+    uint32_t* flags = nullptr;
+    const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
+    const int cap = pick_cap(pb.k, km);
+    auto layout = [&](Arena& ar) {
+        layout_common(pb, prec, true, ar, L);
+        cand = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap);
+        count = ar.take<int32_t>(pb.M);
+        bound = ar.take<uint64_t>(pb.M);
+        flags = ar.take<uint32_t>(pb.M);
+    };
+    {
+        Arena sz;
+        layout(sz);
+        void* base = nullptr;
+        KNN_TRY(workspace_get(sz.used(), &base));
+        Arena ar(static_cast<char*>(base), sz.used());
+        L = CommonLayout{};
+        layout(ar);
     }
-    if (timing) {
-        for (auto& e : ev) cudaEventDestroy(e);
-        for (auto& e : gev) cudaEventDestroy(e);
+    Timing tm;
+    tm.on = stats && (pb.flags & KNN_FLAG_TIMING);
+    Events ev;
+    KNN_TRY(ev.init(tm.on));
+    KNN_TRY(ev.rec(0, st));
+    KNN_TRY(prep_and_check(pb, prec, L, st, stats, tm));
+    KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
+    KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
+    KNN_TRY(ev.rec(1, st));
+
+    FusedParams fp{};
+    fp.xq = L.ps.xq;
+    fp.xc = L.ps.xc;
+    fp.M = pb.M;
+    fp.N = pb.N;
+    fp.k_bytes = L.ps.d_pad * (prec == P_BF16 ? 2 : 1);
+    fp.k = pb.k;
+    fp.km = km;
+    fp.cap = cap;
+    fp.cnorm2 = L.ps.cnorm2;
+    fp.E = L.ps.E;
+    fp.thr = L.ps.thr_dprime;
+    fp.q_inv_scale = L.ps.qscale;
+    fp.c_inv_scale = L.ps.cscale;
+    fp.self_offset = pb.graph ? 0 : -1;
+    fp.cand = cand;
+    fp.count = count;
+    fp.bound = bound;
+    fp.flags = flags;
+    fp.status = L.status;
+    int dev = 0, sms = 0;
+    KNN_CK(cudaGetDevice(&dev));
+    KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nrb = (pb.M + 127) / 128;
+    const int grid = static_cast<int>(std::min<int64_t>(sms, nrb));
+    KNN_TRY(tm.record_gemm(st, true));
+    KNN_CK(launch_fused(fp, prec, grid, st));
+    KNN_TRY(tm.record_gemm(st, false));
+    ++tm.launches;
+    ++tm.gemm_launches;
+    KNN_TRY(ev.rec(2, st));
+    int hstatus = 0;
+    KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the fused kernel stopped: a device-side wait timed out");
+
+    RerankParams rp{};
+    rp.Q = pb.Q;
+    rp.C = pb.C;
+    rp.M = pb.M;
+    rp.N = pb.N;
+    rp.d = pb.d;
+    rp.k = pb.k;
+    rp.cap = cap;
+    rp.cand = cand;
+    rp.count = count;
+    rp.bound = bound;
+    rp.flags = flags;
+    rp.E = L.ps.E;
+    rp.out_idx = pb.out_idx;
+    rp.out_dist = pb.out_dist;
+    rp.row_status = L.row_status;
+    rp.counters = L.counters;
+    KNN_CK(launch_rerank(rp, st));
+    ++tm.launches;
+    KNN_TRY(ev.rec(3, st));
+    RerankCounters hc{};
+    KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    int64_t fallback = 0;
+    if (hc.uncertified > 0 && !(pb.flags & KNN_FLAG_NO_FALLBACK)) {
+        std::vector<int32_t> rows;
+        KNN_TRY(rows_with(L.row_status, pb.M, ROW_UNCERTIFIED, st, rows));
+        int64_t n64 = 0;
+        KNN_TRY(plain_fallback(pb, L, rows, st, tm, &n64));
+        fallback = static_cast<int64_t>(rows.size());
     }
+    KNN_TRY(ev.rec(4, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    // the fallback's re-rank adds to the counters after they were read: report the first pass
+    fill_stats(stats, pb, hc, fallback, prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3, 1, tm, ev.ev);
     return KNN_OK;
 }
 
@@ -428,13 +687,21 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
 
 int run_problem(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     int prec = pb.precision;
-    if (prec == KNN_AUTO) prec = KNN_FP32;
+    const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
+    const int cap = pick_cap(pb.k, km);
+    const bool fused_ok = fused_available() && cap <= 256 && pb.fused != 0;
+    if (prec == KNN_AUTO) prec = fused_ok ? KNN_BF16 : KNN_FP32;
     switch (prec) {
         case KNN_FP32:
+            if (pb.fused == 1) return set_error(KNN_EUNSUPPORTED, "the FP32 form is not fused");
             return run_plain(pb, stats, st);
         case KNN_BF16:
         case KNN_FP8_E4M3:
-            return set_error(KNN_EUNSUPPORTED, "precision %d is not available in this build", prec);
+            if (!fused_ok)
+                return set_error(KNN_EUNSUPPORTED,
+                                 "the tensor-core form needs an sm_103 device and a candidate list of at most "
+                                 "256 (k + m <= 170); got k=%d m=%d", pb.k, pb.m);
+            return run_fused(pb, prec == KNN_BF16 ? P_BF16 : P_FP8, stats, st);
         default:
             return set_error(KNN_EINVAL, "unknown precision %d", prec);
     }

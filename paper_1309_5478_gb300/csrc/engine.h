@@ -92,6 +92,10 @@ int pick_cap(int k, int km);
 
 cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool check_nan, cudaStream_t st);
 cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out, cudaStream_t st);
+cudaError_t launch_gather_rows(const float* Q, int32_t d, const int32_t* rows, int32_t n, const float* E,
+                               const float* thr, float* Qs, float* Es, float* Ts, cudaStream_t st);
+cudaError_t launch_scatter_out(const int32_t* rows, int32_t n, int32_t k, const int32_t* oi_s, const float* od_s,
+                               int32_t* oi, float* od, cudaStream_t st);
 
 // Runs one problem end to end (device pointers); fills stats when non-null.
 int run_problem(const Problem& pb, ::knn_stats* stats, cudaStream_t st);

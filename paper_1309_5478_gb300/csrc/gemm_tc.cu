@@ -1,0 +1,521 @@
+// Fused tensor-core distance GEMM + quick multi-select (the chosen form).
+//
+// Paper: Methods, "Distance calculation" (distances from the product X^T Y and the
+// norms, ranked by d'_ij = |y_j|^2 - 2 x_i.y_j) and "GPU-based quick multi-select"
+// (per-row selection with warp ballot/popc partitions). The paper materialises the
+// M x N matrix in global memory between the two; here the selection runs in the
+// GEMM's epilogue, so the matrix never leaves the chip.
+//
+// Structure (one persistent CTA per SM, 6 warps):
+//   warp 0     TMA producer: 128 x 64 query tiles (A) and 256 x 64 corpus tiles (B),
+//              128-byte swizzle, into a 4-stage shared-memory ring (mbarrier full/empty)
+//   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues
+//              tcgen05.mma (BF16 kind::f16, or FP8 e4m3 kind::f8f6f4) from one thread;
+//              tcgen05.commit releases smem stages and publishes finished accumulators
+//   warps 2-5  epilogue: thread t owns query row t of the 128-row block (its TMEM lane);
+//              tcgen05.ld 32 columns at a time, v = |c_j|^2 - 2 acc (FP8: acc scaled back),
+//              keep v when it passes the row's running threshold, appending the key
+//              (v, j) to the row's candidate list in global memory (L2-resident).
+//              When any list of the warp nears its capacity the warp shrinks it with the
+//              quick multi-select (select_core.cuh) in shared memory: the threshold becomes
+//              max(key_(k+m), ceiling(value(key_k) + 2E_i)), so the list always holds every
+//              point whose exact distance can still be among the row's k smallest.
+// Work: row blocks of 128 queries; each CTA sweeps all corpus tiles of a row block
+// (the candidate state of a row lives in one CTA), then takes the next row block.
+// Every mbarrier wait is bounded; on expiry the kernel records KNN_ETIMEOUT in a status
+// word, stops issuing work, waits (bounded) for its own copies and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "engine.h"
+#include "internal.h"
+#include "select_core.cuh"
+#include "tc_fused.h"
+
+namespace knn {
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_BK_BYTES = 128;  // one 128-byte swizzle row per stage: 64 BF16 or 128 FP8 values
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 192;
+constexpr int A_BYTES = TC_BM * TC_BK_BYTES;  // 16 KB
+constexpr int B_BYTES = TC_BN * TC_BK_BYTES;  // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr long long WAIT_LIMIT = 1ll << 26;  // try_wait polls before a wait is declared stuck
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false when the limit expired or another warp already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 255) == 255 && *abort_flag) return false;
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((addr & 0x3ffffu) >> 4);
+    d |= static_cast<uint64_t>(1) << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride byte offset: 8 rows x 128 B
+    d |= static_cast<uint64_t>(1) << 46;            // descriptor version
+    d |= static_cast<uint64_t>(2) << 61;            // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256.
+template <int P>
+__host__ __device__ constexpr uint32_t idesc() {
+    // bits 4-5 D format (1 = F32); 7-9 A format, 10-12 B format (kind::f16: 1 = BF16;
+    // kind::f8f6f4: 0 = E4M3); 15/16 A/B major (0 = K); 17-22 N >> 3; 24-28 M >> 4.
+    return (1u << 4) | ((P == P_BF16 ? 1u : 0u) << 7) | ((P == P_BF16 ? 1u : 0u) << 10) |
+           (static_cast<uint32_t>(TC_BN >> 3) << 17) | (static_cast<uint32_t>(TC_BM >> 4) << 24);
+}
+
+template <int P>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    if constexpr (P == P_BF16) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc<P>()), "r"(accumulate));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc<P>()), "r"(accumulate));
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Largest value a key <= tau can carry (+inf for the open threshold).
+__device__ __forceinline__ float tau_value(uint64_t tau) {
+    return (tau >> 32) == 0xffffffffull ? F_INF : key_val(tau);
+}
+
+struct EpiSmem {
+    uint64_t* A;
+    uint64_t* B;
+    int* seg_s;
+    uint32_t* seg_e;
+};
+
+__host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
+    return static_cast<size_t>(cap) * 16 + static_cast<size_t>(SEG_MAX) * 8;
+}
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int cap) {
+    return 1024 /* alignment slack */ + static_cast<size_t>(TC_STAGES) * STAGE_BYTES + 4 * epi_warp_bytes(cap) + 256;
+}
+
+// Warp-cooperative shrink of the candidate list of the row owned by `owner_lane`.
+// Returns the new count; tau (64-bit key) and truncated are updated for the owner.
+__device__ __forceinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, int owner_lane, int64_t grow,
+                                           int& cnt, uint64_t& tau, bool& truncated, float window, int keep_max,
+                                           int keep_trunc, uint64_t* band_out) {
+    const uint32_t lane = lane_id();
+    const int n = __shfl_sync(0xffffffffu, cnt, owner_lane);
+    const uint64_t t = shfl_u64(tau, owner_lane);
+    const float w = __shfl_sync(0xffffffffu, window, owner_lane);
+    const int64_t r = static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(grow), owner_lane));
+    uint64_t* gbuf = p.cand + r * p.cap;
+    __syncwarp();
+    for (int i = static_cast<int>(lane); i < n; i += 32) es.A[i] = gbuf[i];
+    __syncwarp();
+    CompactResult res = compact_row(es.A, es.B, es.seg_s, es.seg_e, n, p.k, p.km, w, t, keep_max, keep_trunc);
+    int nn = n;
+    uint64_t nt = t;
+    bool tr = false;
+    uint64_t band = KEY_MAX;
+    if (res.ok) {
+        for (int i = static_cast<int>(lane); i < res.n; i += 32) gbuf[i] = es.A[i];
+        nn = res.n;
+        nt = res.tau;
+        tr = res.truncated;
+        band = res.band;
+    }
+    __syncwarp();
+    if (static_cast<int>(lane) == owner_lane) {
+        cnt = nn;
+        tau = nt;
+        truncated |= tr || !res.ok;
+        if (band_out) *band_out = band;
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    fused_gemm_select_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                             const FusedParams p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    unsigned char* stage_base = smem;
+    unsigned char* epi_base = smem + TC_STAGES * STAGE_BYTES;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + 4 * epi_warp_bytes(p.cap));
+    uint64_t* full = bars;                     // [TC_STAGES]
+    uint64_t* empty = bars + TC_STAGES;        // [TC_STAGES]
+    uint64_t* acc_full = bars + 2 * TC_STAGES; // [2]
+    uint64_t* acc_empty = acc_full + 2;        // [2]
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const uint32_t lane = lane_id();
+    const int nrb = static_cast<int>((p.M + TC_BM - 1) / TC_BM);
+    const int nct = static_cast<int>((p.N + TC_BN - 1) / TC_BN);
+    const int nk = p.k_bytes / TC_BK_BYTES;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------------ TMA producer ------------------------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            bool ok = true;
+            for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+                for (int ct = 0; ct < nct && ok; ++ct) {
+                    for (int ks = 0; ks < nk; ++ks) {
+                        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        unsigned char* a = stage_base + s * STAGE_BYTES;
+                        mbar_expect_tx(&full[s], STAGE_BYTES);
+                        tma_load_2d(a, &tmA, &full[s], ks * (TC_BK_BYTES / (P == P_BF16 ? 2 : 1)), rb * TC_BM);
+                        tma_load_2d(a + A_BYTES, &tmB, &full[s], ks * (TC_BK_BYTES / (P == P_BF16 ? 2 : 1)),
+                                    ct * TC_BN);
+                        if (++s == TC_STAGES) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                }
+            }
+            // drain: wait until the MMA warp has consumed every stage we filled
+            if (ok) {
+                for (int i = 0; i < TC_STAGES; ++i) {
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+                    if (++s == TC_STAGES) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+            } else {
+                // gave up: still let the copies already issued land before the CTA exits
+                for (int i = 0; i < TC_STAGES; ++i) {
+                    if (--s < 0) {
+                        s = TC_STAGES - 1;
+                        ph ^= 1u;
+                    }
+                    for (int spin = 0; spin < (1 << 20); ++spin)
+                        if (mbar_try_wait(&full[s], ph)) break;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ------------------------------ MMA issuer --------------------------------
+        if (lane == 0) {
+            int s = 0;
+            uint32_t ph = 0;
+            int tile = 0;
+            bool ok = true;
+            const int k_per_mma = 32;  // bytes of K per instruction: 16 BF16 or 32 FP8 values
+            for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+                    const int acc = tile & 1;
+                    const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
+                    if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
+                    for (int ks = 0; ks < nk; ++ks) {
+                        if (!mbar_wait(&full[s], ph, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a_addr = smem_u32(stage_base + s * STAGE_BYTES);
+                        const uint32_t b_addr = a_addr + A_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK_BYTES / k_per_mma; ++kk) {
+                            umma<P>(d_tmem, sdesc(a_addr + kk * k_per_mma), sdesc(b_addr + kk * k_per_mma),
+                                    (ks | kk) != 0 ? 1u : 0u);
+                        }
+                        umma_commit(&empty[s]);
+                        if (++s == TC_STAGES) {
+                            s = 0;
+                            ph ^= 1u;
+                        }
+                    }
+                    if (ok) umma_commit(&acc_full[acc]);
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------ epilogue ----------------------------------
+        const int ew = warp - 2;                  // epilogue warp 0..3
+        const int quarter = warp & 3;             // TMEM lane quarter this warp may read
+        const int row_in_block = quarter * 32 + static_cast<int>(lane);
+        EpiSmem es;
+        unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap);
+        es.A = reinterpret_cast<uint64_t*>(mine);
+        es.B = es.A + p.cap;
+        es.seg_s = reinterpret_cast<int*>(es.B + p.cap);
+        es.seg_e = reinterpret_cast<uint32_t*>(es.seg_s + SEG_MAX);
+        const int keep_mid = p.cap - 64 > p.km ? p.cap - 64 : p.km;
+        const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
+        int tile = 0;
+        bool ok = true;
+        for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+            const int64_t grow = static_cast<int64_t>(rb) * TC_BM + row_in_block;
+            const bool valid = grow < p.M;
+            const int64_t self = valid && p.self_offset >= 0 ? grow + p.self_offset : -1;
+            float window = valid && p.E ? 2.f * p.E[grow] : 0.f;
+            uint64_t tau = KEY_MAX;
+            uint64_t tau_thr = KEY_MAX;
+            if (valid && p.thr) {
+                const float t = p.thr[grow];
+                if (t == t && t < F_INF) tau_thr = key_ceiling(t);
+            }
+            tau = tau_thr;
+            if (!valid) tau = 0;  // nothing passes
+            float tau_v = valid ? tau_value(tau) : -F_INF;
+            const float qscale = (P == P_FP8 && valid) ? p.q_inv_scale[grow] : 1.f;
+            int cnt = 0;
+            bool truncated = false;
+            uint64_t* gbuf = valid ? p.cand + grow * p.cap : nullptr;
+
+            for (int ct = 0; ct < nct; ++ct, ++tile) {
+                const int acc = tile & 1;
+                const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
+                if (!mbar_wait(&acc_full[acc], acc_ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                       static_cast<uint32_t>(acc * TC_BN);
+#pragma unroll 1
+                for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                    uint32_t r[32];
+                    tmem_ld32(taddr + ch * 32, r);
+                    if (ch == TC_BN / 32 - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                    }
+                    const int64_t j0 = static_cast<int64_t>(ct) * TC_BN + ch * 32;
+                    const float4* cn4 = reinterpret_cast<const float4*>(p.cnorm2 + j0);
+                    const float4* cs4 = reinterpret_cast<const float4*>(P == P_FP8 ? p.c_inv_scale + j0 : p.cnorm2);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 c = __ldg(cn4 + q);
+                        float s4[4] = {1.f, 1.f, 1.f, 1.f};
+                        if constexpr (P == P_FP8) {
+                            const float4 sc = __ldg(cs4 + q);
+                            s4[0] = sc.x * qscale;
+                            s4[1] = sc.y * qscale;
+                            s4[2] = sc.z * qscale;
+                            s4[3] = sc.w * qscale;
+                        }
+                        const float cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int t = q * 4 + e;
+                            float a = __uint_as_float(r[t]);
+                            if constexpr (P == P_FP8) a *= s4[e];
+                            const float v = fmaf(-2.f, a, cv[e]);
+                            if (v <= tau_v) {
+                                const int64_t j = j0 + t;
+                                const uint64_t key = make_key(v, static_cast<uint32_t>(j));
+                                if (j != self && key <= tau) gbuf[cnt++] = key;
+                            }
+                        }
+                    }
+                    // keep room for the next 32 columns of every row of the warp
+                    uint32_t need = __ballot_sync(0xffffffffu, cnt > p.cap - 32);
+                    while (need) {
+                        const int owner = __ffs(need) - 1;
+                        need &= need - 1;
+                        shrink_row(p, es, owner, grow, cnt, tau, truncated, window, keep_mid, trunc_mid, nullptr);
+                        if (static_cast<int>(lane) == owner) tau_v = tau_value(tau);
+                    }
+                }
+            }
+            if (!ok) break;
+            // final shrink of every row of the warp to at most cap candidates
+            for (int owner = 0; owner < 32; ++owner) {
+                const int n = __shfl_sync(0xffffffffu, cnt, owner);
+                const bool v = __shfl_sync(0xffffffffu, valid ? 1 : 0, owner) != 0;
+                if (!v) continue;
+                uint64_t band = KEY_MAX;
+                if (n > 0) shrink_row(p, es, owner, grow, cnt, tau, truncated, window, p.cap, p.cap, &band);
+                if (static_cast<int>(lane) == owner) {
+                    uint32_t fl = truncated ? ROW_TRUNCATED : 0u;
+                    if (tau_thr != KEY_MAX && (cnt < p.k || band > tau_thr)) fl |= ROW_THRESHOLD_MISS | ROW_TRUNCATED;
+                    p.count[grow] = cnt;
+                    p.bound[grow] = tau;
+                    p.flags[grow] = fl;
+                }
+            }
+        }
+        if (!ok && lane == 0) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+    }
+    if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t row_bytes, int box_rows, int elem_bytes) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const CUtensorMapDataType dt = elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const cuuint64_t dims[2] = {static_cast<cuuint64_t>(row_bytes / elem_bytes), static_cast<cuuint64_t>(rows)};
+    const cuuint64_t strides[1] = {static_cast<cuuint64_t>(row_bytes)};
+    const cuuint32_t box[2] = {static_cast<cuuint32_t>(TC_BK_BYTES / elem_bytes), static_cast<cuuint32_t>(box_rows)};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool fused_available() {
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaGetLastError();
+    return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+size_t fused_smem_bytes(int cap) { return tc_smem_bytes(cap); }
+
+cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const int elem = precision == P_BF16 ? 2 : 1;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, p.xq, p.M, p.k_bytes, TC_BM, elem)) return cudaErrorInvalidValue;
+    if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
+    const size_t smem = tc_smem_bytes(p.cap);
+    if (precision == P_BF16) {
+        auto kern = fused_gemm_select_kernel<P_BF16>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
+    } else {
+        auto kern = fused_gemm_select_kernel<P_FP8>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace knn

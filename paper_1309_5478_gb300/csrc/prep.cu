@@ -174,7 +174,46 @@ __global__ void thr_kernel(const float* __restrict__ thr, const float* __restric
     out[i] = (t == t && t >= 0.f && t < F_INF) ? t - qnorm2[i] : F_INF;
 }
 
+__global__ void gather_rows_kernel(const float* __restrict__ Q, int32_t d, const int32_t* __restrict__ rows,
+                                   int32_t n, const float* __restrict__ E, const float* __restrict__ thr,
+                                   float* __restrict__ Qs, float* __restrict__ Es, float* __restrict__ Ts) {
+    const int32_t i = blockIdx.x;
+    if (i >= n) return;
+    const int64_t r = rows[i];
+    for (int32_t t = threadIdx.x; t < d; t += blockDim.x) Qs[static_cast<int64_t>(i) * d + t] = Q[r * d + t];
+    if (threadIdx.x == 0) {
+        Es[i] = E[r];
+        if (thr) Ts[i] = thr[r];
+    }
+}
+
+__global__ void scatter_out_kernel(const int32_t* __restrict__ rows, int32_t n, int32_t k,
+                                   const int32_t* __restrict__ oi_s, const float* __restrict__ od_s,
+                                   int32_t* __restrict__ oi, float* __restrict__ od) {
+    const int32_t i = blockIdx.x;
+    if (i >= n) return;
+    const int64_t r = rows[i];
+    for (int32_t t = threadIdx.x; t < k; t += blockDim.x) {
+        oi[r * k + t] = oi_s[static_cast<int64_t>(i) * k + t];
+        od[r * k + t] = od_s[static_cast<int64_t>(i) * k + t];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_gather_rows(const float* Q, int32_t d, const int32_t* rows, int32_t n, const float* E,
+                               const float* thr, float* Qs, float* Es, float* Ts, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    gather_rows_kernel<<<n, 128, 0, st>>>(Q, d, rows, n, E, thr, Qs, Es, Ts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_out(const int32_t* rows, int32_t n, int32_t k, const int32_t* oi_s, const float* od_s,
+                               int32_t* oi, float* od, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    scatter_out_kernel<<<n, 128, 0, st>>>(rows, n, k, oi_s, od_s, oi, od);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out,
                                        cudaStream_t st) {

@@ -1,0 +1,91 @@
+"""GPU parity of the tensor-core forms (BF16 / FP8 tcgen05 GEMM with the quick
+multi-select fused into its epilogue, exact re-rank, fallbacks) against the FP64
+oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from acceptance import check_exact, check_float
+from paper_1309_5478_gb300 import binding as kb
+from paper_1309_5478_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def graph(X, k, precision="bf16", **kw):
+    out = kb.knng_build(dev(X), k, precision=precision, fused=1, return_stats=True, **kw)
+    torch.cuda.synchronize()
+    return out[0].cpu().numpy(), out[1].cpu().numpy(), out[2]
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_integer_lattice_bit_exact(precision):
+    X = inputs.integer_lattice(n=4096, d=128)
+    idx, dist, st = graph(X, 16, precision)
+    assert st["fused_used"] == 1
+    check_exact(idx, dist, *oracle.knng(X, 16))
+
+
+@pytest.mark.parametrize("n,d,k", [(1000, 37, 7), (300, 200, 64), (257, 64, 1), (5000, 130, 100)])
+def test_integer_ragged_bit_exact(n, d, k):
+    X = inputs.integer_lattice(n=n, d=d, lo=-6, hi=6, seed=200 + n)
+    idx, dist, _ = graph(X, k)
+    check_exact(idx, dist, *oracle.knng(X, k))
+
+
+def test_gaussian_mixture_float():
+    X = inputs.gaussian_mixture(n=6000, d=256, components=16)
+    idx, dist, st = graph(X, 32)
+    rows = inputs.sample_rows(len(X), 200, seed=1)
+    ref_idx, ref_dist = oracle.knng(X, 32, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_unit_directions_with_duplicates():
+    X, t, s = inputs.unit_directions_with_duplicates(n=20000, d=1024, seed=3)
+    idx, dist, st = graph(X, 64)
+    assert np.all(dist[t, 0] == 0.0) and np.array_equal(idx[t, 0], s)
+    rows = np.concatenate([t[:10], inputs.sample_rows(len(X), 40, seed=5)])
+    ref_idx, ref_dist = oracle.knng(X, 64, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_search_separate_sets():
+    C = inputs.gaussian_mixture(n=7000, d=96, components=8, seed=5)
+    Q = inputs.gaussian_mixture(n=333, d=96, components=8, seed=6)
+    idx, dist, st = kb.knn_search(dev(Q), dev(C), 20, precision="bf16", fused=1, return_stats=True)
+    ref_idx, ref_dist = oracle.knn(Q, C, 20)
+    check_float(Q, C, np.arange(len(Q)), idx.cpu().numpy(), dist.cpu().numpy(), ref_idx, ref_dist, False)
+
+
+def test_fused_matches_plain_exactly_on_float_data():
+    X = inputs.anisotropic_mixture(n=5000, d=192, components=16, seed=8)
+    a = graph(X, 24, "bf16")
+    b = kb.knng_build(dev(X), 24, precision="fp32")
+    # both forms are exact: identical answers (distances may differ only where FP64 decided)
+    assert np.array_equal(a[0], b[0].cpu().numpy())
+    assert np.allclose(a[1], b[1].cpu().numpy(), rtol=1e-6, atol=0)
+
+
+def test_tight_threshold_goes_through_the_fallback():
+    X = inputs.gaussian_mixture(n=4000, d=64, components=8, seed=13)
+    base_i, base_d, _ = graph(X, 16)
+    thr = (base_d[:, -1] * 0.5).astype(np.float32)  # too tight: every row misses
+    i2, d2, st = graph(X, 16, row_threshold=dev(thr))
+    assert st["threshold_misses"] > 0 and st["rows_fallback"] > 0
+    assert np.array_equal(i2, base_i) and np.array_equal(d2, base_d)
+    thr = (base_d[:, -1] * 1.2 + 1.0).astype(np.float32)  # loose: nothing lost
+    i3, d3, st3 = graph(X, 16, row_threshold=dev(thr))
+    assert np.array_equal(i3, base_i) and np.array_equal(d3, base_d)
+
+
+def test_fp8_on_float_data_is_still_exact():
+    X = inputs.gaussian_mixture(n=3000, d=128, components=8, seed=21)
+    idx, dist, st = graph(X, 10, "fp8")
+    ref_idx, ref_dist = oracle.knng(X, 10, rows=np.arange(100))
+    check_float(X, X, np.arange(100), idx[:100], dist[:100], ref_idx, ref_dist, exclude_self=True)
