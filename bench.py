@@ -51,7 +51,48 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--mode", choices=["knng", "select"], default="knng",
+                    help="select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments)")
+    ap.add_argument("--q", type=int, default=16384, help="select mode: rows")
+    ap.add_argument("--cols", type=int, default=65536, help="select mode: row length n")
     return ap.parse_args()
+
+
+def run_select_only(args):
+    """Quick multi-select alone: k smallest of every row of a Q x n uniform random FP32 matrix."""
+    import torch
+    from paper_1309_5478_gb300 import binding as kb
+    P = peaks()
+    g = torch.Generator(device="cuda").manual_seed(20130906)
+    D = torch.rand((args.q, args.cols), device="cuda", generator=g, dtype=torch.float32)
+    k = args.k
+    oi = torch.empty((args.q, k), dtype=torch.int32, device="cuda")
+    ov = torch.empty((args.q, k), dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        kb.knn_select(D, k, out_idx=oi, out_val=ov)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        kb.knn_select(D, k, out_idx=oi, out_val=ov)
+    ev1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    bytes_alg = args.q * args.cols * 4 + args.q * k * 8
+    gbs = bytes_alg / (ms / 1000.0) / 1e9
+    line = {"metric": "quick multi-select rows/s (selection only, uniform random values)", "value": args.q / (ms / 1000),
+            "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"select k={k} smallest of {args.q} rows x {args.cols} uniform FP32 values",
+                       "Q": args.q, "n": args.cols, "k": k, "l2": "matrix > L2: no flush needed"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": P["hbm_gbs"], "unit": "GB/s",
+                         "frac": gbs / P["hbm_gbs"], "traffic": None, "kernel": "select_rows_kernel",
+                         "peak_source": P["source"]},
+            "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
 
 
 def peaks():
@@ -208,6 +249,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.mode == "select":
+        import torch
+        torch.cuda.set_device(local)
+        run_select_only(args)
         return
 
     import torch

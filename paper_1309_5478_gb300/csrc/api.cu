@@ -473,13 +473,21 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     uint64_t* bound = nullptr;
     uint32_t* flags = nullptr;
     const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
-    const int cap = pick_cap(pb.k, km);
+    const int cap = fused_cap(pb.k, km);
+    const int stages = fused_stages(cap, prec);
+    int dev = 0, sms = 0;
+    KNN_CK(cudaGetDevice(&dev));
+    KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t nrb = (pb.M + 127) / 128;
+    const int grid = static_cast<int>(std::min<int64_t>(sms, nrb));
+    uint64_t* scratch = nullptr;
     auto layout = [&](Arena& ar) {
         layout_common(pb, prec, true, ar, L);
         cand = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap);
         count = ar.take<int32_t>(pb.M);
         bound = ar.take<uint64_t>(pb.M);
         flags = ar.take<uint32_t>(pb.M);
+        scratch = ar.take<uint64_t>(fused_scratch_words(cap, grid));
     };
     {
         Arena sz;
@@ -520,11 +528,8 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.bound = bound;
     fp.flags = flags;
     fp.status = L.status;
-    int dev = 0, sms = 0;
-    KNN_CK(cudaGetDevice(&dev));
-    KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t nrb = (pb.M + 127) / 128;
-    const int grid = static_cast<int>(std::min<int64_t>(sms, nrb));
+    fp.scratch = scratch;
+    fp.stages = stages;
     KNN_TRY(tm.record_gemm(st, true));
     KNN_CK(launch_fused(fp, prec, grid, st));
     KNN_TRY(tm.record_gemm(st, false));
@@ -688,8 +693,8 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
 int run_problem(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     int prec = pb.precision;
     const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
-    const int cap = pick_cap(pb.k, km);
-    const bool fused_ok = fused_available() && cap <= 256 && pb.fused != 0;
+    const int want = prec == KNN_FP8_E4M3 ? P_FP8 : P_BF16;
+    const bool fused_ok = fused_available() && fused_stages(fused_cap(pb.k, km), want) > 0 && pb.fused != 0;
     if (prec == KNN_AUTO) prec = fused_ok ? KNN_BF16 : KNN_FP32;
     switch (prec) {
         case KNN_FP32:
@@ -699,8 +704,8 @@ int run_problem(const Problem& pb, knn_stats* stats, cudaStream_t st) {
         case KNN_FP8_E4M3:
             if (!fused_ok)
                 return set_error(KNN_EUNSUPPORTED,
-                                 "the tensor-core form needs an sm_103 device and a candidate list of at most "
-                                 "256 (k + m <= 170); got k=%d m=%d", pb.k, pb.m);
+                                 "the tensor-core form needs an sm_103 device and k + m small enough for its "
+                                 "shared-memory candidate buffers; got k=%d m=%d", pb.k, pb.m);
             return run_fused(pb, prec == KNN_BF16 ? P_BF16 : P_FP8, stats, st);
         default:
             return set_error(KNN_EINVAL, "unknown precision %d", prec);

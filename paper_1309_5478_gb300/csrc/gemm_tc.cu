@@ -133,7 +133,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Issues a 32-column TMEM load; the registers are valid only after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -141,8 +144,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
           "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    tmem_ld32_issue(taddr, r);
+    tmem_ld_wait();
 }
 
 // Largest value a key <= tau can carry (+inf for the open threshold).
@@ -150,54 +158,185 @@ __device__ __forceinline__ float tau_value(uint64_t tau) {
     return (tau >> 32) == 0xffffffffull ? F_INF : key_val(tau);
 }
 
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+constexpr int MAX_STAGES = 4;
+
+// Per-epilogue-warp shared memory: the row's keys (C), two 32-bit value arrays (A, B)
+// and a histogram for the quick multi-select.
 struct EpiSmem {
-    uint64_t* A;
-    uint64_t* B;
-    int* seg_s;
-    uint32_t* seg_e;
+    uint64_t* C;
+    uint32_t* A;
+    uint32_t* B;
+    uint32_t* hist;
+    uint64_t* scratch;  // global: exact 64-bit path (2 cap keys + reference list)
 };
 
-__host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
-    return static_cast<size_t>(cap) * 16 + static_cast<size_t>(SEG_MAX) * 8;
+__host__ __device__ constexpr size_t epi_warp_bytes(int cap) { return static_cast<size_t>(cap) * 16 + 256; }
+
+__host__ __device__ constexpr size_t cn_bytes(int precision) { return (precision == P_FP8 ? 2 : 1) * 2 * TC_BN * 4; }
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision) {
+    return 1024 /* alignment slack */ + static_cast<size_t>(stages) * STAGE_BYTES + 4 * epi_warp_bytes(cap) +
+           cn_bytes(precision) + 256;
 }
 
-__host__ __device__ constexpr size_t tc_smem_bytes(int cap) {
-    return 1024 /* alignment slack */ + static_cast<size_t>(TC_STAGES) * STAGE_BYTES + 4 * epi_warp_bytes(cap) + 256;
+__host__ __device__ constexpr size_t scratch_words_per_warp(int cap) {
+    return 2 * static_cast<size_t>(cap) + SEG_MAX;
 }
 
-// Warp-cooperative shrink of the candidate list of the row owned by `owner_lane`.
-// Returns the new count; tau (64-bit key) and truncated are updated for the owner.
-__device__ __forceinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, int owner_lane, int64_t grow,
-                                           int& cnt, uint64_t& tau, bool& truncated, float window, int keep_max,
-                                           int keep_trunc, uint64_t* band_out) {
+// Copies the row's n keys from its global list into shared memory (keys in C, their
+// values in A), issuing 8 independent loads per lane before using any of them so that
+// the L2 latency is paid once per 256 keys rather than once per 32.
+__device__ __forceinline__ void stage_list(const uint64_t* gbuf, int n, const EpiSmem& es) {
+    const int lane = static_cast<int>(lane_id());
+    for (int base = 0; base < n; base += 256) {
+        uint64_t v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = base + q * 32 + lane;
+            v[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + i) : 0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int i = base + q * 32 + lane;
+            if (i < n) {
+                es.C[i] = v[q];
+                es.A[i] = static_cast<uint32_t>(v[q] >> 32);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Warp-cooperative shrink of the candidate list of the row owned by `owner`: the
+// quick multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest
+// values; the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))).
+// When more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc
+// smallest keys instead.
+__device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, int owner, int64_t grow, int& cnt,
+                                        uint64_t& tau, bool& truncated, float window, int keep_max, int keep_trunc,
+                                        uint64_t* band_out) {
     const uint32_t lane = lane_id();
-    const int n = __shfl_sync(0xffffffffu, cnt, owner_lane);
-    const uint64_t t = shfl_u64(tau, owner_lane);
-    const float w = __shfl_sync(0xffffffffu, window, owner_lane);
-    const int64_t r = static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(grow), owner_lane));
+    const uint32_t lt_mask = lanemask_lt();
+    const int n = __shfl_sync(0xffffffffu, cnt, owner);
+    const uint64_t t = shfl_u64(tau, owner);
+    const float w = __shfl_sync(0xffffffffu, window, owner);
+    const int64_t r = static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(grow), owner));
     uint64_t* gbuf = p.cand + r * p.cap;
     __syncwarp();
-    for (int i = static_cast<int>(lane); i < n; i += 32) es.A[i] = gbuf[i];
-    __syncwarp();
-    CompactResult res = compact_row(es.A, es.B, es.seg_s, es.seg_e, n, p.k, p.km, w, t, keep_max, keep_trunc);
-    int nn = n;
-    uint64_t nt = t;
-    bool tr = false;
+    stage_list(gbuf, n, es);
+    const int kk = p.k < n ? p.k : n;
+    const int kme = p.km < n ? p.km : n;
     uint64_t band = KEY_MAX;
-    if (res.ok) {
-        for (int i = static_cast<int>(lane); i < res.n; i += 32) gbuf[i] = es.A[i];
-        nn = res.n;
-        nt = res.tau;
-        tr = res.truncated;
-        band = res.band;
+    if (n >= p.km) {
+        uint32_t o_k = 0, o_km = 0;
+        two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k, o_km);
+        float bv = ord_to_float(o_km);
+        if (w > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + w);
+        band = key_ceiling(bv);
+    }
+    uint64_t nt = band < t ? band : t;
+    const int keep = count_le(es.C, n, nt);
+    int nn;
+    bool tr = false;
+    if (keep <= keep_max) {
+        nn = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + static_cast<int>(lane);
+            const uint64_t v = i < n ? es.C[i] : KEY_MAX;
+            const bool kp = i < n && v <= nt;
+            const uint32_t b = __ballot_sync(0xffffffffu, kp);
+            if (kp) gbuf[nn + __popc(b & lt_mask)] = v;
+            nn += __popc(b);
+        }
+    } else {
+        // exact path on 64-bit keys in global scratch (ties at the threshold value)
+        uint64_t* sA = es.scratch;
+        uint64_t* sB = sA + p.cap;
+        int* seg_s = reinterpret_cast<int*>(sB + p.cap);
+        uint32_t* seg_e = reinterpret_cast<uint32_t*>(seg_s + SEG_MAX);
+        for (int i = static_cast<int>(lane); i < n; i += 32) sA[i] = es.C[i];
+        __syncwarp();
+        CompactResult res = compact_row(sA, sB, seg_s, seg_e, n, p.k, p.km, w, t, keep_max, keep_trunc);
+        if (res.ok) {
+            for (int i = static_cast<int>(lane); i < res.n; i += 32) gbuf[i] = sA[i];
+            nn = res.n;
+            nt = res.tau;
+            tr = res.truncated;
+            band = res.band;
+        } else {
+            nn = n;  // leave the list as it was; the row is reported truncated
+            nt = t;
+            tr = true;
+        }
     }
     __syncwarp();
-    if (static_cast<int>(lane) == owner_lane) {
+    if (static_cast<int>(lane) == owner) {
         cnt = nn;
         tau = nt;
-        truncated |= tr || !res.ok;
+        truncated |= tr;
         if (band_out) *band_out = band;
     }
+}
+
+// Filters one 32-column chunk of the accumulator into the row's candidate list. Every
+// ranking value v = |c_j|^2 - 2 acc is compared with the row's threshold tau_f, a float
+// such that v <= tau_f exactly when key(v, j) <= tau: the columns of this chunk come
+// after every column the threshold key was built from, so a value tied with a
+// non-ceiling threshold is above it (tau_f is then the float just below tau's value).
+// Survivors get consecutive slots from a popc of the lower survivor bits and are
+// written with predicated stores: no per-column branches.
+template <int P>
+__device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
+                                             int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt) {
+    float v[32];
+    uint32_t mask = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 c = reinterpret_cast<const float4*>(cn)[q];
+        const float cv[4] = {c.x, c.y, c.z, c.w};
+        float sv[4] = {1.f, 1.f, 1.f, 1.f};
+        if constexpr (P == P_FP8) {
+            const float4 sc = reinterpret_cast<const float4*>(cs)[q];
+            sv[0] = sc.x * qscale;
+            sv[1] = sc.y * qscale;
+            sv[2] = sc.z * qscale;
+            sv[3] = sc.w * qscale;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int t = q * 4 + e;
+            float a = __uint_as_float(r[t]);
+            if constexpr (P == P_FP8) a *= sv[e];
+            v[t] = fmaf(-2.f, a, cv[e]);
+            mask |= (v[t] <= tau_f) ? (1u << t) : 0u;
+        }
+    }
+    const uint64_t ds = static_cast<uint64_t>(self - j0);
+    if (ds < 32u) mask &= ~(1u << ds);
+    if (__reduce_or_sync(0xffffffffu, mask) == 0u) return;
+    if (mask) {
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const int pos = cnt + __popc(mask & ((1u << t) - 1u));
+            const uint64_t key = make_key(v[t], static_cast<uint32_t>(j0 + t));
+            if (mask & (1u << t)) gbuf[pos] = key;
+        }
+        cnt += __popc(mask);
+    }
+}
+
+// Float threshold for filter_chunk (see there).
+__device__ __forceinline__ float tau_filter(uint64_t tau) {
+    if ((tau >> 32) == 0xffffffffull) return F_INF;
+    const float v = key_val(tau);
+    return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
 }
 
 template <int P>
@@ -207,13 +346,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
+    const int nst = p.stages;
     unsigned char* stage_base = smem;
-    unsigned char* epi_base = smem + TC_STAGES * STAGE_BYTES;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(epi_base + 4 * epi_warp_bytes(p.cap));
-    uint64_t* full = bars;                     // [TC_STAGES]
-    uint64_t* empty = bars + TC_STAGES;        // [TC_STAGES]
-    uint64_t* acc_full = bars + 2 * TC_STAGES; // [2]
-    uint64_t* acc_empty = acc_full + 2;        // [2]
+    unsigned char* epi_base = smem + nst * STAGE_BYTES;
+    float* cn_smem = reinterpret_cast<float*>(epi_base + 4 * epi_warp_bytes(p.cap));  // [2][TC_BN] (+ scales)
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P));
+    uint64_t* full = bars;                        // [MAX_STAGES]
+    uint64_t* empty = bars + MAX_STAGES;          // [MAX_STAGES]
+    uint64_t* acc_full = bars + 2 * MAX_STAGES;   // [2]
+    uint64_t* acc_empty = acc_full + 2;           // [2]
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
@@ -222,14 +363,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nrb = static_cast<int>((p.M + TC_BM - 1) / TC_BM);
     const int nct = static_cast<int>((p.N + TC_BN - 1) / TC_BN);
     const int nk = p.k_bytes / TC_BK_BYTES;
+    constexpr uint32_t CN_TX = static_cast<uint32_t>(cn_bytes(P) / 2);  // bytes staged per tile
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_full[a], 2);  // the norms' copy (arrive + bytes) and the MMA commit
             mbar_init(&acc_empty[a], 4);
         }
         *abort_flag = 0;
@@ -252,6 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int s = 0;
             uint32_t ph = 0;
             bool ok = true;
+            const int kx = TC_BK_BYTES / (P == P_BF16 ? 2 : 1);
             for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
                 for (int ct = 0; ct < nct && ok; ++ct) {
                     for (int ks = 0; ks < nk; ++ks) {
@@ -261,30 +404,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
                         unsigned char* a = stage_base + s * STAGE_BYTES;
                         mbar_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(a, &tmA, &full[s], ks * (TC_BK_BYTES / (P == P_BF16 ? 2 : 1)), rb * TC_BM);
-                        tma_load_2d(a + A_BYTES, &tmB, &full[s], ks * (TC_BK_BYTES / (P == P_BF16 ? 2 : 1)),
-                                    ct * TC_BN);
-                        if (++s == TC_STAGES) {
+                        tma_load_2d(a, &tmA, &full[s], ks * kx, rb * TC_BM);
+                        tma_load_2d(a + A_BYTES, &tmB, &full[s], ks * kx, ct * TC_BN);
+                        if (++s == nst) {
                             s = 0;
                             ph ^= 1u;
                         }
                     }
                 }
             }
-            // drain: wait until the MMA warp has consumed every stage we filled
             if (ok) {
-                for (int i = 0; i < TC_STAGES; ++i) {
+                // drain: every stage filled has been consumed
+                for (int i = 0; i < nst; ++i) {
                     if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
-                    if (++s == TC_STAGES) {
+                    if (++s == nst) {
                         s = 0;
                         ph ^= 1u;
                     }
                 }
             } else {
                 // gave up: still let the copies already issued land before the CTA exits
-                for (int i = 0; i < TC_STAGES; ++i) {
+                for (int i = 0; i < nst; ++i) {
                     if (--s < 0) {
-                        s = TC_STAGES - 1;
+                        s = nst - 1;
                         ph ^= 1u;
                     }
                     for (int spin = 0; spin < (1 << 20); ++spin)
@@ -310,6 +452,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
+                    // stage this tile's corpus norms (and FP8 scales) for the epilogue
+                    mbar_expect_tx(&acc_full[acc], CN_TX);
+                    bulk_copy_g2s(cn_smem + acc * TC_BN, p.cnorm2 + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4,
+                                  &acc_full[acc]);
+                    if constexpr (P == P_FP8)
+                        bulk_copy_g2s(cn_smem + 2 * TC_BN + acc * TC_BN,
+                                      p.c_inv_scale + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4, &acc_full[acc]);
                     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
                     for (int ks = 0; ks < nk; ++ks) {
                         if (!mbar_wait(&full[s], ph, abort_flag)) {
@@ -325,7 +474,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                     (ks | kk) != 0 ? 1u : 0u);
                         }
                         umma_commit(&empty[s]);
-                        if (++s == TC_STAGES) {
+                        if (++s == nst) {
                             s = 0;
                             ph ^= 1u;
                         }
@@ -342,11 +491,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int row_in_block = quarter * 32 + static_cast<int>(lane);
         EpiSmem es;
         unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap);
-        es.A = reinterpret_cast<uint64_t*>(mine);
+        es.C = reinterpret_cast<uint64_t*>(mine);
+        es.A = reinterpret_cast<uint32_t*>(es.C + p.cap);
         es.B = es.A + p.cap;
-        es.seg_s = reinterpret_cast<int*>(es.B + p.cap);
-        es.seg_e = reinterpret_cast<uint32_t*>(es.seg_s + SEG_MAX);
-        const int keep_mid = p.cap - 64 > p.km ? p.cap - 64 : p.km;
+        es.hist = es.B + p.cap;
+        es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * 4 + ew) * scratch_words_per_warp(p.cap);
+        const int keep_mid = p.cap - 96 > p.km ? p.cap - 96 : p.km;
         const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
         int tile = 0;
         bool ok = true;
@@ -354,16 +504,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t grow = static_cast<int64_t>(rb) * TC_BM + row_in_block;
             const bool valid = grow < p.M;
             const int64_t self = valid && p.self_offset >= 0 ? grow + p.self_offset : -1;
-            float window = valid && p.E ? 2.f * p.E[grow] : 0.f;
-            uint64_t tau = KEY_MAX;
+            const float window = valid && p.E ? 2.f * p.E[grow] : 0.f;
             uint64_t tau_thr = KEY_MAX;
             if (valid && p.thr) {
                 const float t = p.thr[grow];
                 if (t == t && t < F_INF) tau_thr = key_ceiling(t);
             }
-            tau = tau_thr;
-            if (!valid) tau = 0;  // nothing passes
-            float tau_v = valid ? tau_value(tau) : -F_INF;
+            uint64_t tau = valid ? tau_thr : 0ull;
+            float tau_v = valid ? tau_filter(tau) : -F_INF;
             const float qscale = (P == P_FP8 && valid) ? p.q_inv_scale[grow] : 1.f;
             int cnt = 0;
             bool truncated = false;
@@ -379,55 +527,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                        static_cast<uint32_t>(acc * TC_BN);
+                const float* cn = cn_smem + acc * TC_BN;
+                const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN;
+                uint32_t ra[32], rb2[32];
+                tmem_ld32(taddr, ra);
 #pragma unroll 1
-                for (int ch = 0; ch < TC_BN / 32; ++ch) {
-                    uint32_t r[32];
-                    tmem_ld32(taddr + ch * 32, r);
-                    if (ch == TC_BN / 32 - 1) {
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&acc_empty[acc]);
-                    }
-                    const int64_t j0 = static_cast<int64_t>(ct) * TC_BN + ch * 32;
-                    const float4* cn4 = reinterpret_cast<const float4*>(p.cnorm2 + j0);
-                    const float4* cs4 = reinterpret_cast<const float4*>(P == P_FP8 ? p.c_inv_scale + j0 : p.cnorm2);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 c = __ldg(cn4 + q);
-                        float s4[4] = {1.f, 1.f, 1.f, 1.f};
-                        if constexpr (P == P_FP8) {
-                            const float4 sc = __ldg(cs4 + q);
-                            s4[0] = sc.x * qscale;
-                            s4[1] = sc.y * qscale;
-                            s4[2] = sc.z * qscale;
-                            s4[3] = sc.w * qscale;
-                        }
-                        const float cv[4] = {c.x, c.y, c.z, c.w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int t = q * 4 + e;
-                            float a = __uint_as_float(r[t]);
-                            if constexpr (P == P_FP8) a *= s4[e];
-                            const float v = fmaf(-2.f, a, cv[e]);
-                            if (v <= tau_v) {
-                                const int64_t j = j0 + t;
-                                const uint64_t key = make_key(v, static_cast<uint32_t>(j));
-                                if (j != self && key <= tau) gbuf[cnt++] = key;
-                            }
-                        }
-                    }
-                    // keep room for the next 32 columns of every row of the warp
-                    uint32_t need = __ballot_sync(0xffffffffu, cnt > p.cap - 32);
+                for (int ch = 0; ch < TC_BN / 32; ch += 2) {
+                    // chunk ch in ra; fetch chunk ch+1 into rb2 while filtering ch
+                    tmem_ld32_issue(taddr + (ch + 1) * 32, rb2);
+                    filter_chunk<P>(ra, cn + ch * 32, cs + ch * 32, qscale, static_cast<int64_t>(ct) * TC_BN + ch * 32,
+                                    self, tau_v, gbuf, cnt);
+                    tmem_ld_wait();
+                    if (ch + 2 < TC_BN / 32) tmem_ld32_issue(taddr + (ch + 2) * 32, ra);
+                    filter_chunk<P>(rb2, cn + (ch + 1) * 32, cs + (ch + 1) * 32, qscale,
+                                    static_cast<int64_t>(ct) * TC_BN + (ch + 1) * 32, self, tau_v, gbuf, cnt);
+                    if (ch + 2 < TC_BN / 32) tmem_ld_wait();
+                    // keep room for the next 64 columns of every row of the warp
+                    uint32_t need = __ballot_sync(0xffffffffu, cnt > p.cap - 64);
                     while (need) {
                         const int owner = __ffs(need) - 1;
                         need &= need - 1;
                         shrink_row(p, es, owner, grow, cnt, tau, truncated, window, keep_mid, trunc_mid, nullptr);
-                        if (static_cast<int>(lane) == owner) tau_v = tau_value(tau);
+                        if (static_cast<int>(lane) == owner) tau_v = tau_filter(tau);
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_empty[acc]);
             }
             if (!ok) break;
-            // final shrink of every row of the warp to at most cap candidates
+            // final shrink of every row of the warp
             for (int owner = 0; owner < 32; ++owner) {
                 const int n = __shfl_sync(0xffffffffu, cnt, owner);
                 const bool v = __shfl_sync(0xffffffffu, valid ? 1 : 0, owner) != 0;
@@ -495,7 +624,20 @@ bool fused_available() {
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-size_t fused_smem_bytes(int cap) { return tc_smem_bytes(cap); }
+int fused_cap(int k, int km) {
+    (void)k;
+    int c = 2 * km + 160;
+    c = (c + 31) / 32 * 32;
+    return c < 448 ? 448 : c;
+}
+
+int fused_stages(int cap, int precision) {
+    for (int st = MAX_STAGES; st >= 2; --st)
+        if (tc_smem_bytes(cap, st, precision) <= 232448) return st;
+    return 0;
+}
+
+size_t fused_scratch_words(int cap, int grid) { return scratch_words_per_warp(cap) * 4 * static_cast<size_t>(grid); }
 
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
@@ -503,7 +645,7 @@ cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStre
     CUtensorMap ta, tb;
     if (!make_map(&ta, p.xq, p.M, p.k_bytes, TC_BM, elem)) return cudaErrorInvalidValue;
     if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
-    const size_t smem = tc_smem_bytes(p.cap);
+    const size_t smem = tc_smem_bytes(p.cap, p.stages, precision);
     if (precision == P_BF16) {
         auto kern = fused_gemm_select_kernel<P_BF16>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));

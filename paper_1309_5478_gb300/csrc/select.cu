@@ -22,7 +22,7 @@
 namespace knn {
 namespace {
 
-constexpr int SEL_U = 4;  // 16-byte loads in flight per lane per step
+constexpr int SEL_U = 4;  // 16-byte loads per lane per step
 
 struct RowBuffers {
     uint64_t* A;
@@ -35,8 +35,8 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int bufk) {
     return static_cast<size_t>(bufk) * 16 + static_cast<size_t>(SEG_MAX) * 8;
 }
 
-template <bool VEC, bool CHECK_NAN>
-__device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t idx4, float (&v)[4], bool& nan_seen) {
+template <bool VEC>
+__device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t idx4, float (&v)[4]) {
     if (VEC && idx4 + 4 <= N) {
         const float4 f = ldg_stream_f4(rowp + idx4);
         v[0] = f.x;
@@ -44,70 +44,141 @@ __device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t
         v[2] = f.z;
         v[3] = f.w;
     } else {
+        // past the row end: NaN never passes a threshold compare
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = (idx4 + c < N) ? rowp[idx4 + c] : F_INF;
-    }
-    if (CHECK_NAN) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) nan_seen |= (v[c] != v[c]);
+        for (int c = 0; c < 4; ++c) v[c] = (idx4 + c < N) ? rowp[idx4 + c] : __int_as_float(0x7fffffff);
     }
 }
 
-// Streams one row, keeping keys <= tau in A (compacting when full). Returns false on a
-// reference-list overflow. n, tau, truncated, tau_cap are updated in place.
-template <bool VEC, bool CHECK_NAN>
-__device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
-                                         int bufk, int k, int km, float window, uint64_t tau_thr, int& n,
-                                         uint64_t& tau, bool& truncated, bool& nan_seen) {
-    const uint32_t lane = lane_id();
-    const uint32_t lt_mask = lanemask_lt();
-    const int keep_mid = bufk - 128 > km ? bufk - 128 : km;
-    const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
-    for (int64_t base = 0; base < N; base += 32 * 4 * SEL_U) {
-        float v[SEL_U][4];
+// Largest value a key <= tau can carry (+inf for the open threshold).
+__device__ __forceinline__ float tau_value(uint64_t tau) {
+    return (tau >> 32) == 0xffffffffull ? F_INF : key_val(tau);
+}
+
+// Survivor bits (4 per float4 group, SEL_U groups) of one lane: value <= tau_v.
+// NaN (including the padding past the row end) never passes.
+__device__ __forceinline__ uint32_t value_bits(const float (&v)[SEL_U][4], float tau_v) {
+    uint32_t m = 0;
 #pragma unroll
-        for (int u = 0; u < SEL_U; ++u) {
-            const int64_t idx4 = base + (static_cast<int64_t>(u) * 32 + lane) * 4;
-            load_group<VEC, CHECK_NAN>(rowp, N, idx4, v[u], nan_seen);
-        }
-        const uint32_t tau_hi = static_cast<uint32_t>(tau >> 32);
-        bool maybe = false;
+    for (int u = 0; u < SEL_U; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) m |= (v[u][c] <= tau_v) ? (1u << (u * 4 + c)) : 0u;
+    return m;
+}
+
+// Removes from m the entries whose key is above tau (only entries tied with tau's value
+// can be, and only when tau is an exact key rather than a value ceiling) and the
+// excluded self column.
+__device__ __forceinline__ uint32_t refine_bits(uint32_t m, const float (&v)[SEL_U][4], int64_t base, int64_t self_col,
+                                               float tau_v, uint64_t tau, bool tau_ceil) {
+    const uint32_t lane = lane_id();
+    if (self_col >= base && self_col < base + 32 * 4 * SEL_U) {
+        const int64_t off = self_col - base;
+        const int64_t q = off >> 2;
+        if ((q & 31) == lane) m &= ~(1u << ((q >> 5) * 4 + (off & 3)));
+    }
+    if (!tau_ceil && m) {
 #pragma unroll
         for (int u = 0; u < SEL_U; ++u)
 #pragma unroll
-            for (int c = 0; c < 4; ++c) maybe |= float_to_ord(v[u][c]) <= tau_hi;
-        if (!__any_sync(0xffffffffu, maybe)) continue;
-#pragma unroll
-        for (int u = 0; u < SEL_U; ++u) {
-#pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const int64_t j = base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c;
-                const uint64_t key = make_key(v[u][c], static_cast<uint32_t>(j));
-                const bool keep = j < N && j != self_col && key <= tau;
-                const uint32_t b = __ballot_sync(0xffffffffu, keep);
-                if (b == 0u) continue;
-                if (keep) rb.A[n + __popc(b & lt_mask)] = key;
-                n += __popc(b);
-                if (n > bufk - 32) {
+                const uint32_t bit = 1u << (u * 4 + c);
+                if ((m & bit) && v[u][c] == tau_v) {
+                    const int64_t j = base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c;
+                    if (make_key(v[u][c], static_cast<uint32_t>(j)) > tau) m &= ~bit;
+                }
+            }
+    }
+    return m;
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (static_cast<int>(lane) >= o) x += y;
+    }
+    return x;
+}
+
+template <bool VEC>
+__device__ __forceinline__ void load_step(const float* rowp, int64_t N, int64_t base, float (&v)[SEL_U][4]) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int u = 0; u < SEL_U; ++u) load_group<VEC>(rowp, N, base + (static_cast<int64_t>(u) * 32 + lane) * 4, v[u]);
+}
+
+// Streams one row, keeping keys <= tau in A (compacting when full). The next step's
+// loads are issued before the current step is filtered. Returns false on a
+// reference-list overflow. n, tau, truncated are updated in place.
+template <bool VEC, bool CHECK_NAN>
+__device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
+                                         int bufk, int k, int km, float window, int& n, uint64_t& tau,
+                                         bool& truncated, bool& nan_seen) {
+    const uint32_t lane = lane_id();
+    const int keep_mid = bufk - 160 > km ? bufk - 160 : km;
+    const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
+    constexpr int STEP = 32 * 4 * SEL_U;
+    float tau_v = tau_value(tau);
+    bool tau_ceil = static_cast<uint32_t>(tau) == 0xffffffffu;
+    float cur[SEL_U][4], nxt[SEL_U][4];
+    load_step<VEC>(rowp, N, 0, cur);
+    for (int64_t base = 0; base < N; base += STEP) {
+        if (base + STEP < N) load_step<VEC>(rowp, N, base + STEP, nxt);
+        if (CHECK_NAN) {
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    nan_seen |= (cur[u][c] != cur[u][c]) &&
+                                (base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c < N);
+        }
+        uint32_t m = value_bits(cur, tau_v);
+        if (__any_sync(0xffffffffu, m != 0)) {
+            m = refine_bits(m, cur, base, self_col, tau_v, tau, tau_ceil);
+#pragma unroll
+            for (int u = 0; u < SEL_U; ++u) {
+                uint32_t mu = (m >> (u * 4)) & 0xfu;
+                if (!__any_sync(0xffffffffu, mu != 0)) continue;
+                int c = __popc(mu);
+                int incl = warp_incl_scan(c);
+                int total = __shfl_sync(0xffffffffu, incl, 31);
+                if (n + total > bufk) {
                     __syncwarp();
-                    const uint64_t limit = tau;
-                    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, k, km, window, limit, keep_mid,
+                    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, k, km, window, tau, keep_mid,
                                                   trunc_mid);
                     if (!r.ok) return false;
                     n = r.n;
                     tau = r.tau;
                     truncated |= r.truncated;
+                    tau_v = tau_value(tau);
+                    tau_ceil = static_cast<uint32_t>(tau) == 0xffffffffu;
+                    m = refine_bits(value_bits(cur, tau_v), cur, base, self_col, tau_v, tau, tau_ceil);
+                    mu = (m >> (u * 4)) & 0xfu;
+                    c = __popc(mu);
+                    incl = warp_incl_scan(c);
+                    total = __shfl_sync(0xffffffffu, incl, 31);
                 }
+                int pos = n + incl - c;
+                const int64_t idx4 = base + (static_cast<int64_t>(u) * 32 + lane) * 4;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (mu & (1u << e)) rb.A[pos++] = make_key(cur[u][e], static_cast<uint32_t>(idx4 + e));
+                n += total;
             }
         }
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cur[u][c] = nxt[u][c];
     }
     __syncwarp();
-    (void)tau_thr;
     return true;
 }
 
 template <bool VEC, bool CHECK_NAN, bool TOPK>
-__global__ void select_rows_kernel(SelectParams p, int bufk, int64_t self_offset, int32_t* __restrict__ out_idx,
+__global__ void __launch_bounds__(256, 3) select_rows_kernel(SelectParams p, int bufk, int64_t self_offset, int32_t* __restrict__ out_idx,
                                    float* __restrict__ out_val) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = static_cast<int>(threadIdx.x / 32);
@@ -137,8 +208,8 @@ __global__ void select_rows_kernel(SelectParams p, int bufk, int64_t self_offset
         int n = 0;
         uint64_t tau = tau_thr;
         bool truncated = false;
-        bool ok = scan_row<VEC, CHECK_NAN>(rowp, p.N, self_col, rb, bufk, p.k, p.km, window, tau_thr, n, tau,
-                                           truncated, nan_seen);
+        bool ok = scan_row<VEC, CHECK_NAN>(rowp, p.N, self_col, rb, bufk, p.k, p.km, window, n, tau, truncated,
+                                           nan_seen);
         CompactResult r{};
         if (ok && n > 0) {
             r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, p.k, p.km, window, tau, p.cap, p.cap);
@@ -204,7 +275,7 @@ cudaError_t launch_variant(const SelectParams& p, int bufk, int64_t self_offset,
 }
 
 int choose_bufk(int km, int cap) {
-    int want = 2 * km + 160;
+    int want = 2 * km + 288;
     if (want < cap + 64) want = cap + 64;
     int b = pow2_ceil(want);
     return b < 512 ? 512 : b;

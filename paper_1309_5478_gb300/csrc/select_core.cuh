@@ -369,3 +369,95 @@ __host__ __device__ __forceinline__ int pow2_ceil(int x) {
 }
 
 }  // namespace knn
+
+namespace knn {
+
+// Values of ranks r1 <= r2 (0-based) among a[0, n) (32-bit, duplicates allowed), by a
+// two-level sample select: 32 evenly spaced keys, sorted across the lanes, split the
+// values into 33 buckets; a shared-memory histogram of the buckets locates the bucket
+// of each rank, whose members are gathered into b and finished with a 32-lane sort
+// (or the quick multi-select when a bucket holds more than 32). a is preserved; b and
+// hist (at least 64 words) are scratch. Returns false only if the fallback overflows.
+__device__ __forceinline__ void two_ranks_sampled(const uint32_t* a, uint32_t* b, uint32_t* tmp, uint32_t* hist,
+                                                  int n, int r1, int r2, uint32_t& v1, uint32_t& v2) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = lanemask_lt();
+    // 1. pivots
+    uint32_t piv = a[(static_cast<int64_t>(lane) * n) >> 5];
+    piv = warp_sort32(piv);
+    for (int i = static_cast<int>(lane); i < 64; i += 32) hist[i] = 0u;
+    __syncwarp();
+    // 2. bucket histogram: bucket(x) = number of pivots <= x (0..32)
+    const uint32_t p31 = __shfl_sync(0xffffffffu, piv, 31);
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + static_cast<int>(lane);
+        const uint32_t x = i < n ? a[i] : 0u;
+        int lo = 0;  // number of pivots <= x, by binary search over the sorted lanes
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t pv = __shfl_sync(0xffffffffu, piv, lo + step - 1);
+            if (pv <= x) lo += step;
+        }
+        if (lo == 31 && p31 <= x) lo = 32;
+        if (i < n) atomicAdd(&hist[lo], 1u);
+    }
+    __syncwarp();
+    // 3. exclusive prefix over the 33 buckets (lane j holds buckets j; lane 0 also bucket 32)
+    const uint32_t h = hist[lane];
+    uint32_t incl = h;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (static_cast<int>(lane) >= o) incl += y;
+    }
+    const uint32_t excl = incl - h;
+    const uint32_t h32 = hist[32];
+    const uint32_t total31 = __shfl_sync(0xffffffffu, incl, 31);
+    // 4. each rank: its bucket, the bucket's members, then an exact small select
+    uint32_t out[2];
+    const int rr[2] = {r1, r2};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int r = rr[q];
+        int bkt;
+        uint32_t base_cnt, cnt;
+        if (static_cast<uint32_t>(r) >= total31) {
+            bkt = 32;
+            base_cnt = total31;
+            cnt = h32;
+        } else {
+            const uint32_t hit = __ballot_sync(0xffffffffu, excl <= static_cast<uint32_t>(r) &&
+                                                                 static_cast<uint32_t>(r) < incl);
+            bkt = __ffs(hit) - 1;
+            base_cnt = __shfl_sync(0xffffffffu, excl, bkt);
+            cnt = __shfl_sync(0xffffffffu, h, bkt);
+        }
+        // bucket bounds: [pivot bkt-1, pivot bkt)
+        const uint32_t lo_v = bkt > 0 ? __shfl_sync(0xffffffffu, piv, bkt - 1) : 0u;
+        const uint32_t hi_v = bkt < 32 ? __shfl_sync(0xffffffffu, piv, bkt < 32 ? bkt : 31) : 0xffffffffu;
+        int w = 0;
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + static_cast<int>(lane);
+            const uint32_t x = i < n ? a[i] : 0u;
+            const bool in = i < n && (bkt == 0 || x >= lo_v) && (bkt == 32 ? true : x < hi_v);
+            const uint32_t bb = __ballot_sync(0xffffffffu, in);
+            if (in) b[w + __popc(bb & lt_mask)] = x;
+            w += __popc(bb);
+        }
+        __syncwarp();
+        const int rel = r - static_cast<int>(base_cnt);
+        if (w <= 32) {
+            uint32_t v = static_cast<int>(lane) < w ? b[lane] : 0xffffffffu;
+            v = warp_sort32(v);
+            out[q] = __shfl_sync(0xffffffffu, v, rel);
+        } else {
+            out[q] = warp_rank_select<uint32_t>(b, tmp, w, rel);
+        }
+        (void)cnt;
+        __syncwarp();
+    }
+    v1 = out[0];
+    v2 = out[1];
+}
+
+}  // namespace knn
