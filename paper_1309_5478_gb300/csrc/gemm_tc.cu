@@ -41,7 +41,7 @@ constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK_BYTES = 128;  // one 128-byte swizzle row per stage: 64 BF16 or 128 FP8 values
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 192;
+constexpr int TC_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
 constexpr int A_BYTES = TC_BM * TC_BK_BYTES;  // 16 KB
 constexpr int B_BYTES = TC_BN * TC_BK_BYTES;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -167,70 +167,79 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 
 constexpr int MAX_STAGES = 4;
 
-// Per-epilogue-warp shared memory: the row's keys (C), two 32-bit value arrays (A, B)
-// and a histogram for the quick multi-select.
+constexpr int EPI_WARPS = 8;   // two per TMEM lane quarter; each takes half of every tile's columns
+constexpr int HIST_WORDS = 36; // histogram of the sampled select (33 buckets used)
+
+// Per-epilogue-warp shared memory: two 32-bit value arrays (A, B) and a histogram for
+// the quick multi-select of one row's list (the keys stay in the global list).
 struct EpiSmem {
-    uint64_t* C;
     uint32_t* A;
     uint32_t* B;
     uint32_t* hist;
     uint64_t* scratch;  // global: exact 64-bit path (2 cap keys + reference list)
 };
 
-__host__ __device__ constexpr size_t epi_warp_bytes(int cap) { return static_cast<size_t>(cap) * 16 + 256; }
+// Shared candidate-list state of the 128 rows of the current row block; both warps of a
+// lane quarter insert into the same lists (slots from a shared-memory atomic).
+struct RowState {
+    int* cnt;         // [128] list length
+    uint64_t* tau;    // [128] threshold key: every key left out is > tau
+    float* tauf;      // [128] float form of tau for the column filter (tau_filter)
+    uint32_t* trunc;  // [128] 1 when the list was truncated
+};
+
+__host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
+    return static_cast<size_t>(cap) * 8 + HIST_WORDS * 4;
+}
+constexpr size_t ROWSTATE_BYTES = 128 * (4 + 8 + 4 + 4);
 
 __host__ __device__ constexpr size_t cn_bytes(int precision) { return (precision == P_FP8 ? 2 : 1) * 2 * TC_BN * 4; }
 
 __host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision) {
-    return 1024 /* alignment slack */ + static_cast<size_t>(stages) * STAGE_BYTES + 4 * epi_warp_bytes(cap) +
-           cn_bytes(precision) + 256;
+    return 1024 /* alignment slack */ + static_cast<size_t>(stages) * STAGE_BYTES + EPI_WARPS * epi_warp_bytes(cap) +
+           cn_bytes(precision) + ROWSTATE_BYTES + 128;
 }
 
 __host__ __device__ constexpr size_t scratch_words_per_warp(int cap) {
     return 2 * static_cast<size_t>(cap) + SEG_MAX;
 }
 
-// Copies the row's n keys from its global list into shared memory (keys in C, their
-// values in A), issuing 8 independent loads per lane before using any of them so that
-// the L2 latency is paid once per 256 keys rather than once per 32.
-__device__ __forceinline__ void stage_list(const uint64_t* gbuf, int n, const EpiSmem& es) {
-    const int lane = static_cast<int>(lane_id());
-    for (int base = 0; base < n; base += 256) {
-        uint64_t v[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int i = base + q * 32 + lane;
-            v[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + i) : 0ull;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int i = base + q * 32 + lane;
-            if (i < n) {
-                es.C[i] = v[q];
-                es.A[i] = static_cast<uint32_t>(v[q] >> 32);
-            }
-        }
-    }
-    __syncwarp();
+// Float threshold for the column filter: v <= tau_filter(tau) exactly when
+// key(v, j) <= tau, for every column j after the ones tau was built from (the filter
+// visits columns in increasing order; a value tied with a non-ceiling threshold key is
+// then above it, so the float just below tau's value is used).
+__device__ __forceinline__ float tau_filter(uint64_t tau) {
+    if ((tau >> 32) == 0xffffffffull) return F_INF;
+    const float v = key_val(tau);
+    return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
 }
 
-// Warp-cooperative shrink of the candidate list of the row owned by `owner`: the
-// quick multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest
-// values; the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))).
-// When more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc
-// smallest keys instead.
-__device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, int owner, int64_t grow, int& cnt,
-                                        uint64_t& tau, bool& truncated, float window, int keep_max, int keep_trunc,
+// Warp-cooperative shrink of the candidate list of row r (of the block): the quick
+// multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest values;
+// the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))). When
+// more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
+__device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, const RowState& rs, int r,
+                                        int64_t grow, float window, int keep_max, int keep_trunc,
                                         uint64_t* band_out) {
-    const uint32_t lane = lane_id();
+    const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
-    const int n = __shfl_sync(0xffffffffu, cnt, owner);
-    const uint64_t t = shfl_u64(tau, owner);
-    const float w = __shfl_sync(0xffffffffu, window, owner);
-    const int64_t r = static_cast<int64_t>(__shfl_sync(0xffffffffu, static_cast<int>(grow), owner));
-    uint64_t* gbuf = p.cand + r * p.cap;
+    const int n = rs.cnt[r];
+    const uint64_t t = rs.tau[r];
+    uint64_t* gbuf = p.cand + grow * p.cap;
+    // stage the values in A; keep the keys in registers (cap <= 32 * KEYS_PER_LANE)
+    constexpr int KPL = 16;
+    uint64_t key[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const int i = q * 32 + lane;
+        key[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + i) : KEY_MAX;
+    }
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const int i = q * 32 + lane;
+        if (i < n) es.A[i] = static_cast<uint32_t>(key[q] >> 32);
+    }
     __syncwarp();
-    stage_list(gbuf, n, es);
     const int kk = p.k < n ? p.k : n;
     const int kme = p.km < n ? p.km : n;
     uint64_t band = KEY_MAX;
@@ -238,21 +247,24 @@ __device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es,
         uint32_t o_k = 0, o_km = 0;
         two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k, o_km);
         float bv = ord_to_float(o_km);
-        if (w > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + w);
+        if (window > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + window);
         band = key_ceiling(bv);
     }
     uint64_t nt = band < t ? band : t;
-    const int keep = count_le(es.C, n, nt);
+    int keep = 0;
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
     int nn;
     bool tr = false;
     if (keep <= keep_max) {
         nn = 0;
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + static_cast<int>(lane);
-            const uint64_t v = i < n ? es.C[i] : KEY_MAX;
-            const bool kp = i < n && v <= nt;
+#pragma unroll
+        for (int q = 0; q < KPL; ++q) {
+            const bool kp = q * 32 + lane < n && key[q] <= nt;
             const uint32_t b = __ballot_sync(0xffffffffu, kp);
-            if (kp) gbuf[nn + __popc(b & lt_mask)] = v;
+            if (kp) gbuf[nn + __popc(b & lt_mask)] = key[q];
             nn += __popc(b);
         }
     } else {
@@ -261,42 +273,45 @@ __device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es,
         uint64_t* sB = sA + p.cap;
         int* seg_s = reinterpret_cast<int*>(sB + p.cap);
         uint32_t* seg_e = reinterpret_cast<uint32_t*>(seg_s + SEG_MAX);
-        for (int i = static_cast<int>(lane); i < n; i += 32) sA[i] = es.C[i];
+#pragma unroll
+        for (int q = 0; q < KPL; ++q)
+            if (q * 32 + lane < n) sA[q * 32 + lane] = key[q];
         __syncwarp();
-        CompactResult res = compact_row(sA, sB, seg_s, seg_e, n, p.k, p.km, w, t, keep_max, keep_trunc);
+        CompactResult res = compact_row(sA, sB, seg_s, seg_e, n, p.k, p.km, window, t, keep_max, keep_trunc);
         if (res.ok) {
-            for (int i = static_cast<int>(lane); i < res.n; i += 32) gbuf[i] = sA[i];
+            for (int i = lane; i < res.n; i += 32) gbuf[i] = sA[i];
             nn = res.n;
             nt = res.tau;
             tr = res.truncated;
             band = res.band;
         } else {
-            nn = n;  // leave the list as it was; the row is reported truncated
-            nt = t;
+            // reference list overflow: keep a prefix and give up the bound, so the row
+            // cannot be certified and goes to the exact fallback
+            nn = n < keep_trunc ? n : keep_trunc;
+            nt = 0ull;
             tr = true;
         }
     }
     __syncwarp();
-    if (static_cast<int>(lane) == owner) {
-        cnt = nn;
-        tau = nt;
-        truncated |= tr;
-        if (band_out) *band_out = band;
+    if (lane == 0) {
+        rs.cnt[r] = nn;
+        rs.tau[r] = nt;
+        rs.tauf[r] = tau_filter(nt);
+        if (tr) rs.trunc[r] = 1u;
     }
+    if (band_out) *band_out = band;
+    __syncwarp();
 }
 
-// Filters one 32-column chunk of the accumulator into the row's candidate list. Every
-// ranking value v = |c_j|^2 - 2 acc is compared with the row's threshold tau_f, a float
-// such that v <= tau_f exactly when key(v, j) <= tau: the columns of this chunk come
-// after every column the threshold key was built from, so a value tied with a
-// non-ceiling threshold is above it (tau_f is then the float just below tau's value).
-// Survivors get consecutive slots from a popc of the lower survivor bits and are
-// written with predicated stores: no per-column branches.
+// Filters one 32-column chunk of the accumulator into the row's candidate list: every
+// ranking value v = |c_j|^2 - 2 acc is compared with the row's float threshold; the
+// survivors of a lane get consecutive slots of the row's list (one shared-memory atomic
+// per lane) and are written with predicated stores, without per-column branches.
 template <int P>
 __device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
-                                             int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt) {
+                                             int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int* cnt_slot) {
     float v[32];
-    uint32_t mask = 0;
+    uint32_t m8[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 c = reinterpret_cast<const float4*>(cn)[q];
@@ -309,34 +324,36 @@ __device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const floa
             sv[2] = sc.z * qscale;
             sv[3] = sc.w * qscale;
         }
+        uint32_t mq = 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int t = q * 4 + e;
             float a = __uint_as_float(r[t]);
             if constexpr (P == P_FP8) a *= sv[e];
             v[t] = fmaf(-2.f, a, cv[e]);
-            mask |= (v[t] <= tau_f) ? (1u << t) : 0u;
+            mq |= (v[t] <= tau_f) ? (1u << e) : 0u;
         }
+        m8[q] = mq << (4 * q);
     }
+    uint32_t mask = ((m8[0] | m8[1]) | (m8[2] | m8[3])) | ((m8[4] | m8[5]) | (m8[6] | m8[7]));
     const uint64_t ds = static_cast<uint64_t>(self - j0);
     if (ds < 32u) mask &= ~(1u << ds);
     if (__reduce_or_sync(0xffffffffu, mask) == 0u) return;
     if (mask) {
+        const int base = atomicAdd(cnt_slot, __popc(mask));
+        const uint32_t jlo = static_cast<uint32_t>(j0);
 #pragma unroll
         for (int t = 0; t < 32; ++t) {
-            const int pos = cnt + __popc(mask & ((1u << t) - 1u));
-            const uint64_t key = make_key(v[t], static_cast<uint32_t>(j0 + t));
+            const int pos = base + __popc(mask & ((1u << t) - 1u));
+            const uint64_t key = make_key(v[t], jlo + static_cast<uint32_t>(t));
             if (mask & (1u << t)) gbuf[pos] = key;
         }
-        cnt += __popc(mask);
     }
 }
 
-// Float threshold for filter_chunk (see there).
-__device__ __forceinline__ float tau_filter(uint64_t tau) {
-    if ((tau >> 32) == 0xffffffffull) return F_INF;
-    const float v = key_val(tau);
-    return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
+__device__ __forceinline__ void pair_barrier(int quarter) {
+    // named barrier 1 + quarter, shared by the two epilogue warps of that lane quarter
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + quarter) : "memory");
 }
 
 template <int P>
@@ -349,8 +366,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int nst = p.stages;
     unsigned char* stage_base = smem;
     unsigned char* epi_base = smem + nst * STAGE_BYTES;
-    float* cn_smem = reinterpret_cast<float*>(epi_base + 4 * epi_warp_bytes(p.cap));  // [2][TC_BN] (+ scales)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P));
+    float* cn_smem = reinterpret_cast<float*>(epi_base + EPI_WARPS * epi_warp_bytes(p.cap));  // [2][TC_BN] (+ scales)
+    unsigned char* rs_base = reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P);
+    RowState rs;
+    rs.tau = reinterpret_cast<uint64_t*>(rs_base);
+    rs.cnt = reinterpret_cast<int*>(rs.tau + 128);
+    rs.tauf = reinterpret_cast<float*>(rs.cnt + 128);
+    rs.trunc = reinterpret_cast<uint32_t*>(rs.tauf + 128);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(rs_base + ROWSTATE_BYTES);
     uint64_t* full = bars;                        // [MAX_STAGES]
     uint64_t* empty = bars + MAX_STAGES;          // [MAX_STAGES]
     uint64_t* acc_full = bars + 2 * MAX_STAGES;   // [2]
@@ -372,7 +395,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 2);  // the norms' copy (arrive + bytes) and the MMA commit
-            mbar_init(&acc_empty[a], 4);
+            mbar_init(&acc_empty[a], EPI_WARPS);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -486,17 +509,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------ epilogue ----------------------------------
-        const int ew = warp - 2;                  // epilogue warp 0..3
+        const int ew = warp - 2;                  // epilogue warp 0..7
         const int quarter = warp & 3;             // TMEM lane quarter this warp may read
+        const int half = ew >> 2;                 // which half of every tile's columns
+        const int partner_bit = half;             // rows of the quarter this warp compacts: parity == half
         const int row_in_block = quarter * 32 + static_cast<int>(lane);
         EpiSmem es;
         unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap);
-        es.C = reinterpret_cast<uint64_t*>(mine);
-        es.A = reinterpret_cast<uint32_t*>(es.C + p.cap);
+        es.A = reinterpret_cast<uint32_t*>(mine);
         es.B = es.A + p.cap;
         es.hist = es.B + p.cap;
-        es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * 4 + ew) * scratch_words_per_warp(p.cap);
-        const int keep_mid = p.cap - 96 > p.km ? p.cap - 96 : p.km;
+        es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * EPI_WARPS + ew) * scratch_words_per_warp(p.cap);
+        // room for one half-tile of insertions from both warps: 2 x 64 per row
+        const int trigger = p.cap - 128;
+        const int keep_mid = p.cap - 160 > p.km ? p.cap - 160 : p.km;
         const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
         int tile = 0;
         bool ok = true;
@@ -504,18 +530,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int64_t grow = static_cast<int64_t>(rb) * TC_BM + row_in_block;
             const bool valid = grow < p.M;
             const int64_t self = valid && p.self_offset >= 0 ? grow + p.self_offset : -1;
-            const float window = valid && p.E ? 2.f * p.E[grow] : 0.f;
             uint64_t tau_thr = KEY_MAX;
             if (valid && p.thr) {
                 const float t = p.thr[grow];
                 if (t == t && t < F_INF) tau_thr = key_ceiling(t);
             }
-            uint64_t tau = valid ? tau_thr : 0ull;
-            float tau_v = valid ? tau_filter(tau) : -F_INF;
+            if (half == 0) {
+                rs.cnt[row_in_block] = 0;
+                rs.tau[row_in_block] = valid ? tau_thr : 0ull;
+                rs.tauf[row_in_block] = valid ? tau_filter(tau_thr) : -F_INF;
+                rs.trunc[row_in_block] = 0u;
+            }
+            pair_barrier(quarter);
+            float tau_f = rs.tauf[row_in_block];
             const float qscale = (P == P_FP8 && valid) ? p.q_inv_scale[grow] : 1.f;
-            int cnt = 0;
-            bool truncated = false;
             uint64_t* gbuf = valid ? p.cand + grow * p.cap : nullptr;
+            int* cnt_slot = rs.cnt + row_in_block;
 
             for (int ct = 0; ct < nct; ++ct, ++tile) {
                 const int acc = tile & 1;
@@ -525,52 +555,69 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
+                const int c0 = half * (TC_BN / 2);  // first column of this warp's half
                 const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                       static_cast<uint32_t>(acc * TC_BN);
-                const float* cn = cn_smem + acc * TC_BN;
-                const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN;
+                                       static_cast<uint32_t>(acc * TC_BN + c0);
+                const float* cn = cn_smem + acc * TC_BN + c0;
+                const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN + c0;
+                const int64_t jt = static_cast<int64_t>(ct) * TC_BN + c0;
                 uint32_t ra[32], rb2[32];
-                tmem_ld32(taddr, ra);
 #pragma unroll 1
-                for (int ch = 0; ch < TC_BN / 32; ch += 2) {
-                    // chunk ch in ra; fetch chunk ch+1 into rb2 while filtering ch
-                    tmem_ld32_issue(taddr + (ch + 1) * 32, rb2);
-                    filter_chunk<P>(ra, cn + ch * 32, cs + ch * 32, qscale, static_cast<int64_t>(ct) * TC_BN + ch * 32,
-                                    self, tau_v, gbuf, cnt);
+                for (int hs = 0; hs < 2; ++hs) {
+                    // two chunks of 32 columns, the second load overlapping the first filter
+                    tmem_ld32(taddr + hs * 64, ra);
+                    tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
+                    filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf, cnt_slot);
                     tmem_ld_wait();
-                    if (ch + 2 < TC_BN / 32) tmem_ld32_issue(taddr + (ch + 2) * 32, ra);
-                    filter_chunk<P>(rb2, cn + (ch + 1) * 32, cs + (ch + 1) * 32, qscale,
-                                    static_cast<int64_t>(ct) * TC_BN + (ch + 1) * 32, self, tau_v, gbuf, cnt);
-                    if (ch + 2 < TC_BN / 32) tmem_ld_wait();
-                    // keep room for the next 64 columns of every row of the warp
-                    uint32_t need = __ballot_sync(0xffffffffu, cnt > p.cap - 64);
+                    filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self, tau_f,
+                                    gbuf, cnt_slot);
+                    if (hs == 1) {
+                        // accumulator and staged norms of this tile no longer needed by this warp
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                    }
+                    // both warps of the quarter have finished this half-tile: shrink full lists
+                    pair_barrier(quarter);
+                    uint32_t need = __ballot_sync(0xffffffffu, valid && rs.cnt[row_in_block] > trigger);
+                    need &= partner_bit ? 0xaaaaaaaau : 0x55555555u;
                     while (need) {
                         const int owner = __ffs(need) - 1;
                         need &= need - 1;
-                        shrink_row(p, es, owner, grow, cnt, tau, truncated, window, keep_mid, trunc_mid, nullptr);
-                        if (static_cast<int>(lane) == owner) tau_v = tau_filter(tau);
+                        shrink_row(p, es, rs, quarter * 32 + owner, static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner,
+                                   p.E ? 2.f * p.E[static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner] : 0.f,
+                                   keep_mid, trunc_mid, nullptr);
                     }
+                    pair_barrier(quarter);
+                    tau_f = rs.tauf[row_in_block];
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&acc_empty[acc]);
             }
             if (!ok) break;
-            // final shrink of every row of the warp
-            for (int owner = 0; owner < 32; ++owner) {
-                const int n = __shfl_sync(0xffffffffu, cnt, owner);
-                const bool v = __shfl_sync(0xffffffffu, valid ? 1 : 0, owner) != 0;
-                if (!v) continue;
+            // final shrink of every row of the quarter, split between the pair by row parity
+            for (int owner = partner_bit; owner < 32; owner += 2) {
+                const int r = quarter * 32 + owner;
+                const int64_t g = static_cast<int64_t>(rb) * TC_BM + r;
+                if (g >= p.M) continue;
                 uint64_t band = KEY_MAX;
-                if (n > 0) shrink_row(p, es, owner, grow, cnt, tau, truncated, window, p.cap, p.cap, &band);
-                if (static_cast<int>(lane) == owner) {
-                    uint32_t fl = truncated ? ROW_TRUNCATED : 0u;
-                    if (tau_thr != KEY_MAX && (cnt < p.k || band > tau_thr)) fl |= ROW_THRESHOLD_MISS | ROW_TRUNCATED;
-                    p.count[grow] = cnt;
-                    p.bound[grow] = tau;
-                    p.flags[grow] = fl;
+                if (rs.cnt[r] > 0)
+                    shrink_row(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, &band);
+                if (lane == 0) {
+                    uint64_t tthr = KEY_MAX;
+                    if (p.thr) {
+                        const float t = p.thr[g];
+                        if (t == t && t < F_INF) tthr = key_ceiling(t);
+                    }
+                    const int c = rs.cnt[r];
+                    uint32_t fl = rs.trunc[r] ? ROW_TRUNCATED : 0u;
+                    if (tthr != KEY_MAX && (c < p.k || band > tthr)) fl |= ROW_THRESHOLD_MISS | ROW_TRUNCATED;
+                    p.count[g] = c;
+                    p.bound[g] = rs.tau[r];
+                    p.flags[g] = fl;
                 }
+                __syncwarp();
             }
+            // the next row block reinitialises the row state only after both warps are done
+            pair_barrier(quarter);
         }
         if (!ok && lane == 0) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
     }
@@ -632,12 +679,15 @@ int fused_cap(int k, int km) {
 }
 
 int fused_stages(int cap, int precision) {
+    if (cap > 512) return 0;  // a list is staged as at most 16 keys per lane
     for (int st = MAX_STAGES; st >= 2; --st)
         if (tc_smem_bytes(cap, st, precision) <= 232448) return st;
     return 0;
 }
 
-size_t fused_scratch_words(int cap, int grid) { return scratch_words_per_warp(cap) * 4 * static_cast<size_t>(grid); }
+size_t fused_scratch_words(int cap, int grid) {
+    return scratch_words_per_warp(cap) * EPI_WARPS * static_cast<size_t>(grid);
+}
 
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;

@@ -377,7 +377,7 @@ namespace knn {
 // values into 33 buckets; a shared-memory histogram of the buckets locates the bucket
 // of each rank, whose members are gathered into b and finished with a 32-lane sort
 // (or the quick multi-select when a bucket holds more than 32). a is preserved; b and
-// hist (at least 64 words) are scratch. Returns false only if the fallback overflows.
+// hist (at least 33 words) are scratch. Returns false only if the fallback overflows.
 __device__ __forceinline__ void two_ranks_sampled(const uint32_t* a, uint32_t* b, uint32_t* tmp, uint32_t* hist,
                                                   int n, int r1, int r2, uint32_t& v1, uint32_t& v2) {
     const uint32_t lane = lane_id();
@@ -385,7 +385,7 @@ __device__ __forceinline__ void two_ranks_sampled(const uint32_t* a, uint32_t* b
     // 1. pivots
     uint32_t piv = a[(static_cast<int64_t>(lane) * n) >> 5];
     piv = warp_sort32(piv);
-    for (int i = static_cast<int>(lane); i < 64; i += 32) hist[i] = 0u;
+    for (int i = static_cast<int>(lane); i < 33; i += 32) hist[i] = 0u;
     __syncwarp();
     // 2. bucket histogram: bucket(x) = number of pivots <= x (0..32)
     const uint32_t p31 = __shfl_sync(0xffffffffu, piv, 31);
