@@ -136,6 +136,22 @@ int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int
 int knn_distances(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, float* out_D, int64_t ldd,
                   int32_t full, const knn_options* opt);
 
+/*
+ * knn_select without any allocation (the paper has no counterpart: this is for
+ * callers that cannot let the library allocate -- code running inside CUDA graph
+ * capture, applications whose device memory is all owned by their own pool, and
+ * latency-critical paths that cannot pay cudaMalloc's implicit synchronisation).
+ * Same result as knn_select. D, out_idx and out_val must be DEVICE pointers (nothing
+ * is staged); stream is a cudaStream_t (NULL = legacy default stream). At most
+ * 1048576 rows per call (larger M returns KNN_EINVAL). The only scratch is a fixed
+ * 4 MiB device array inside the library, held by every GPU that loads it until exit.
+ * The first call on a device looks up that array's address (cudaGetSymbolAddress):
+ * make it before any stream capture. All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller. Synchronous like every call.
+ */
+int knn_select_noalloc(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx,
+                       float* out_val, void* stream);
+
 /* One problem of a batch. Pointers follow the conventions above. */
 typedef struct knn_problem {
     const float* Q;      /* M x d queries; NULL with exclude_self = 1 means Q = C (a graph) */

@@ -51,7 +51,8 @@ class KnnProblem(ctypes.Structure):
 
 # Every symbol include/knn.h declares (checked by the tests).
 EXPORTS = ("knn_options_init", "knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_distances",
-           "knn_search_batched", "knn_status_string", "knn_last_error", "knn_shutdown", "knn_version")
+           "knn_search_batched", "knn_status_string", "knn_last_error", "knn_shutdown", "knn_version",
+           "knn_select_noalloc")
 
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +90,8 @@ def load(path: str | None = None):
         lib.knn_select.argtypes = [vp, i64, i64, i64, i32, vp, vp, opt_p]
         lib.knn_distances.argtypes = [vp, i64, vp, i64, i32, vp, i64, i32, opt_p]
         lib.knn_search_batched.argtypes = [ctypes.POINTER(KnnProblem), i32, opt_p]
+        lib.knn_select_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp]
+        lib.knn_select_noalloc.restype = ctypes.c_int
         for f in ("knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_distances", "knn_search_batched"):
             getattr(lib, f).restype = ctypes.c_int
         lib.knn_status_string.argtypes = [ctypes.c_int]
@@ -207,6 +210,16 @@ def knn_select(D, k: int, n: int | None = None, out_idx=None, out_val=None, stre
     opt = make_options(stream=_stream_of(D, stream))
     _check(lib, lib.knn_select(_ptr(D), M, n, ldd, k, _ptr(oi), _ptr(ov), ctypes.byref(opt)))
     return oi, ov
+
+
+def knn_select_noalloc(D, k: int, out_idx, out_val, n: int | None = None, stream=None):
+    """knn_select into caller-provided device outputs, with no allocation inside the library."""
+    lib = load()
+    M, ldd = D.shape
+    n = ldd if n is None else n
+    _check(lib, lib.knn_select_noalloc(_ptr(D), M, n, ldd, k, _ptr(out_idx), _ptr(out_val),
+                                       _stream_of(D, stream) or None))
+    return out_idx, out_val
 
 
 def knn_distances(Q, C, full: bool = False, out=None, stream=None):
