@@ -245,7 +245,8 @@ __device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es,
     uint64_t band = KEY_MAX;
     if (n >= p.km) {
         uint32_t o_k = 0, o_km = 0;
-        two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k, o_km);
+        (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
+                                o_km);
         float bv = ord_to_float(o_km);
         if (window > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + window);
         band = key_ceiling(bv);

@@ -378,7 +378,7 @@ namespace knn {
 // of each rank, whose members are gathered into b and finished with a 32-lane sort
 // (or the quick multi-select when a bucket holds more than 32). a is preserved; b and
 // hist (at least 33 words) are scratch. Returns false only if the fallback overflows.
-__device__ __forceinline__ void two_ranks_sampled(const uint32_t* a, uint32_t* b, uint32_t* tmp, uint32_t* hist,
+__device__ __forceinline__ bool two_ranks_sampled(const uint32_t* a, uint32_t* b, uint32_t* tmp, uint32_t* hist,
                                                   int n, int r1, int r2, uint32_t& v1, uint32_t& v2) {
     const uint32_t lane = lane_id();
     const uint32_t lt_mask = lanemask_lt();
@@ -450,14 +450,17 @@ __device__ __forceinline__ void two_ranks_sampled(const uint32_t* a, uint32_t* b
             uint32_t v = static_cast<int>(lane) < w ? b[lane] : 0xffffffffu;
             v = warp_sort32(v);
             out[q] = __shfl_sync(0xffffffffu, v, rel);
-        } else {
+        } else if (tmp != nullptr) {
             out[q] = warp_rank_select<uint32_t>(b, tmp, w, rel);
+        } else {
+            return false;  // a crowded bucket (ties) and no auxiliary array: caller takes the exact path
         }
         (void)cnt;
         __syncwarp();
     }
     v1 = out[0];
     v2 = out[1];
+    return true;
 }
 
 }  // namespace knn
