@@ -236,7 +236,7 @@ def knn_distances(Q, C, full: bool = False, out=None, stream=None):
 
 
 def knn_search_batched(problems, precision="auto", rerank_extra: int = 32, flags: int = KNN_FLAG_CHECK_FINITE,
-                       stream=None):
+                       stream=None, return_stats: bool = False):
     """problems: list of dicts with keys Q (or None for a graph), C, k, out_idx, out_dist."""
     lib = load()
     arr = (KnnProblem * len(problems))()
@@ -254,12 +254,13 @@ def knn_search_batched(problems, precision="auto", rerank_extra: int = 32, flags
         arr[i].exclude_self = 1 if p.get("Q") is None else 0
         arr[i].out_idx = _ptr(p["out_idx"])
         arr[i].out_dist = _ptr(p["out_dist"])
-    ref = keep[0] if keep else None
-    opt = make_options(precision, rerank_extra, -1, flags, _stream_of(ref, stream))
+    ref = next((x for x in keep if _is_torch(x) and x.device.type == "cuda"), None)
+    st = KnnStats()
+    opt = make_options(precision, rerank_extra, -1, flags, _stream_of(ref, stream), stats=st)
     status = lib.knn_search_batched(arr, len(problems), ctypes.byref(opt))
     statuses = [arr[i].status for i in range(len(problems))]
     _check(lib, status)
-    return statuses
+    return (statuses, st.as_dict()) if return_stats else statuses
 
 
 def version() -> str:

@@ -530,6 +530,8 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.status = L.status;
     fp.scratch = scratch;
     fp.stages = stages;
+    fp.cap_max = cap;
+    fp.n_items = static_cast<int32_t>(nrb);
     KNN_TRY(tm.record_gemm(st, true));
     KNN_CK(launch_fused(fp, prec, grid, st));
     KNN_TRY(tm.record_gemm(st, false));
@@ -637,19 +639,26 @@ knn_options defaults() {
     return o;
 }
 
-int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t* out_idx,
-                float* out_dist, const knn_options* opt_in, bool graph) {
-    g_last_error.clear();
-    const knn_options opt = opt_in ? *opt_in : defaults();
+int validate_args(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, const int32_t* out_idx,
+                  const float* out_dist, const knn_options& opt, bool graph) {
     if (!C || !out_idx || !out_dist || (!graph && !Q)) return set_error(KNN_EINVAL, "NULL pointer argument");
     if (d < 1) return set_error(KNN_EINVAL, "d must be >= 1 (got %d)", d);
     if (k < 1) return set_error(KNN_EINVAL, "k must be >= 1 (got %d)", k);
     if (N < 1 || N >= (int64_t(1) << 31)) return set_error(KNN_EINVAL, "N must be in [1, 2^31) (got %lld)", (long long)N);
     if (M < 0) return set_error(KNN_EINVAL, "M must be >= 0");
+    if (graph && M != N) return set_error(KNN_EINVAL, "a k-NN graph needs M == N");
     if (graph && k > N - 1) return set_error(KNN_EINVAL, "k must be <= N - 1 for a k-NN graph (k=%d, N=%lld)", k, (long long)N);
     if (!graph && k > N) return set_error(KNN_EINVAL, "k must be <= N (k=%d, N=%lld)", k, (long long)N);
     if (k > MAX_K) return set_error(KNN_EINVAL, "k above %d is not supported (got %d)", MAX_K, k);
     if (opt.rerank_extra < 0) return set_error(KNN_EINVAL, "rerank_extra must be >= 0");
+    return KNN_OK;
+}
+
+int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t* out_idx,
+                float* out_dist, const knn_options* opt_in, bool graph) {
+    g_last_error.clear();
+    const knn_options opt = opt_in ? *opt_in : defaults();
+    KNN_TRY(validate_args(Q, M, C, N, d, k, out_idx, out_dist, opt, graph));
     if (M == 0) return KNN_OK;
     cudaStream_t st = stream_of(&opt);
     Staged sg;
@@ -823,17 +832,62 @@ int knn_distances(const float* Q, int64_t M, const float* C, int64_t N, int32_t 
     return KNN_OK;
 }
 
-int knn_search_batched(knn_problem* probs, int32_t count, const knn_options* opt) {
+int knn_search_batched(knn_problem* probs, int32_t count, const knn_options* opt_in) {
     using namespace knn;
     g_last_error.clear();
     if (count < 0 || (count > 0 && !probs)) return set_error(KNN_EINVAL, "bad problem list");
+    const knn_options opt = opt_in ? *opt_in : defaults();
+    cudaStream_t st = stream_of(&opt);
     int first = KNN_OK;
+    std::vector<Problem> batch;
+    std::vector<int> where;
     for (int32_t i = 0; i < count; ++i) {
         knn_problem& p = probs[i];
         const bool graph = p.exclude_self != 0;
-        const float* Q = graph ? p.C : p.Q;
-        p.status = search_impl(Q, p.M, p.C, p.N, p.d, p.k, p.out_idx, p.out_dist, opt, graph);
-        if (p.status != KNN_OK && first == KNN_OK) first = p.status;
+        const float* Q = (graph && !p.Q) ? p.C : p.Q;
+        p.status = validate_args(Q, p.M, p.C, p.N, p.d, p.k, p.out_idx, p.out_dist, opt, graph);
+        if (p.status == KNN_OK && graph && Q != p.C) p.status = set_error(KNN_EINVAL, "a graph problem needs Q == C");
+        if (p.status != KNN_OK) {
+            if (first == KNN_OK) first = p.status;
+            continue;
+        }
+        if (p.M == 0) continue;
+        const bool device = is_device_pointer(p.C) && is_device_pointer(Q) && is_device_pointer(p.out_idx) &&
+                            is_device_pointer(p.out_dist);
+        if (!device) {
+            // host arrays: the single-problem path stages them
+            p.status = search_impl(Q, p.M, p.C, p.N, p.d, p.k, p.out_idx, p.out_dist, &opt, graph);
+            if (p.status != KNN_OK && first == KNN_OK) first = p.status;
+            continue;
+        }
+        Problem pb{};
+        pb.Q = Q;
+        pb.C = p.C;
+        pb.M = p.M;
+        pb.N = p.N;
+        pb.d = p.d;
+        pb.k = p.k;
+        pb.m = opt.rerank_extra;
+        pb.graph = graph;
+        pb.out_idx = p.out_idx;
+        pb.out_dist = p.out_dist;
+        pb.precision = opt.precision;
+        pb.fused = opt.fused;
+        pb.flags = opt.flags;
+        batch.push_back(pb);
+        where.push_back(i);
+    }
+    if (!batch.empty()) {
+        std::vector<int> status(batch.size(), KNN_OK);
+        knn_stats local{};
+        knn_stats* stats = opt.stats ? opt.stats : &local;
+        std::memset(stats, 0, sizeof(*stats));
+        const int rc = run_batch(batch, status, opt.precision, stats, st);
+        for (size_t j = 0; j < batch.size(); ++j) {
+            probs[where[j]].status = rc != KNN_OK && status[j] == KNN_OK ? rc : status[j];
+            if (probs[where[j]].status != KNN_OK && first == KNN_OK) first = probs[where[j]].status;
+        }
+        if (rc != KNN_OK && first == KNN_OK) first = rc;
     }
     return first;
 }

@@ -1,0 +1,685 @@
+// Many independent k-NN search problems of uneven shape in one CUDA graph: one
+// persistent launch of the fused tensor-core kernel over the (problem, row block) work
+// items of every problem the autotuner assigns to it, batched prep / bounds / re-rank
+// kernels over all rows of all problems, and the plain FP32 form (SIMT GEMM slab ->
+// quick multi-select -> re-rank) for the problems assigned to it (those whose k + m
+// exceed the fused kernel's shared-memory lists, or that the autotuner found faster
+// there).
+//
+// Paper: Methods (coarse-level parallelism: independent queries processed in parallel)
+// and Results (kernel launch overhead; the saturation of the GPU needs enough rows).
+// One graph replays the whole batch with a single host submission; within it, one
+// persistent kernel lets the small problems share the 152 SMs instead of each leaving
+// most of them idle.
+#include <cuda_runtime.h>
+#include <sys/stat.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+#include "internal.h"
+#include "knn.h"
+#include "tc_fused.h"
+
+namespace knn {
+
+enum Schedule : int { SCHED_FUSED = 0, SCHED_PLAIN = 1 };
+
+namespace {
+
+// --------------------------------------------------------------------------------------
+// autotuner: schedule per shape bucket, measured once on a synthetic problem of the
+// bucket, cached in a JSON file (KNN_AUTOTUNE_CACHE, default ~/.cache/knn_gb300_autotune.json)
+// --------------------------------------------------------------------------------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_path() {
+    const char* e = std::getenv("KNN_AUTOTUNE_CACHE");
+    if (e && *e) return e;
+    const char* h = std::getenv("HOME");
+    return std::string(h ? h : "/tmp") + "/.cache/knn_gb300_autotune.json";
+}
+
+void tune_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    FILE* f = std::fopen(tune_path().c_str(), "r");
+    if (!f) return;
+    char key[256];
+    int v;
+    // the file is a flat JSON object {"bucket": schedule, ...}
+    int c;
+    while ((c = std::fgetc(f)) != EOF) {
+        if (c != '"') continue;
+        int n = 0;
+        while ((c = std::fgetc(f)) != EOF && c != '"' && n < 255) key[n++] = static_cast<char>(c);
+        key[n] = 0;
+        if (std::fscanf(f, " : %d", &v) == 1) g_tune[key] = v;
+    }
+    std::fclose(f);
+}
+
+void tune_save() {
+    const std::string path = tune_path();
+    const size_t slash = path.find_last_of('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        std::string cmd_dir = dir;  // create the directory without a shell: mkdir -p equivalent
+        for (size_t i = 1; i <= cmd_dir.size(); ++i)
+            if (i == cmd_dir.size() || cmd_dir[i] == '/') {
+                const std::string part = cmd_dir.substr(0, i);
+                (void)::mkdir(part.c_str(), 0755);
+            }
+    }
+    FILE* f = std::fopen((path + ".tmp").c_str(), "w");
+    if (!f) return;
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto& kv : g_tune)
+        std::fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < g_tune.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    std::rename((path + ".tmp").c_str(), path.c_str());
+}
+
+int ilog2(int64_t x) {
+    int r = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++r;
+    }
+    return r;
+}
+
+std::string bucket_of(const Problem& p) {
+    char b[160];
+    const int kc = p.k <= 8 ? 8 : (p.k <= 32 ? 32 : (p.k <= 128 ? 128 : 1024));
+    std::snprintf(b, sizeof(b), "d%d_k%d_m%d_n%d_x%d", (p.d + 63) / 64 * 64, kc, p.m, ilog2(p.N), ilog2(p.M));
+    return b;
+}
+
+__global__ void synth_kernel(float* x, int64_t n, uint64_t seed) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint64_t z = seed + static_cast<uint64_t>(i + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        x[i] = static_cast<float>(static_cast<double>(z >> 11) * 0x1p-53) - 0.5f;
+    }
+}
+
+// Times one schedule on a synthetic problem of p's shape (fewer query rows); ms per row.
+int time_schedule(const Problem& p, int sched, float* ms_per_row) {
+    const int64_t M = std::min<int64_t>(p.M, 1024);
+    float *Q = nullptr, *C = nullptr, *od = nullptr;
+    int32_t* oi = nullptr;
+    cudaStream_t st = nullptr;
+    KNN_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaError_t e = cudaMalloc(&Q, static_cast<size_t>(M) * p.d * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&C, static_cast<size_t>(p.N) * p.d * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&oi, static_cast<size_t>(M) * p.k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&od, static_cast<size_t>(M) * p.k * 4);
+    int rc = KNN_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = set_error(KNN_ENOMEM, "autotuner buffers: %s", cudaGetErrorString(e));
+    } else {
+        synth_kernel<<<512, 256, 0, st>>>(Q, M * p.d, 7);
+        synth_kernel<<<512, 256, 0, st>>>(C, p.N * p.d, 11);
+        Problem q = p;
+        q.Q = Q;
+        q.C = C;
+        q.M = M;
+        q.graph = false;
+        q.thr = nullptr;
+        q.out_idx = oi;
+        q.out_dist = od;
+        q.flags = KNN_FLAG_NO_FALLBACK;
+        q.precision = sched == SCHED_FUSED ? KNN_BF16 : KNN_FP32;
+        q.fused = sched == SCHED_FUSED ? 1 : 0;
+        ::knn_stats s{};
+        float best = 1e30f;
+        for (int rep = 0; rep < 3 && rc == KNN_OK; ++rep) {
+            cudaEvent_t a, b;
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, st);
+            rc = run_problem(q, &s, st);
+            cudaEventRecord(b, st);
+            cudaEventSynchronize(b);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, a, b);
+            if (rep > 0) best = std::min(best, t);
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+        *ms_per_row = best / static_cast<float>(M);
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(Q);
+    cudaFree(C);
+    cudaFree(oi);
+    cudaFree(od);
+    cudaStreamDestroy(st);
+    return rc;
+}
+
+// Schedule of one problem: the plain form when the fused kernel cannot take it,
+// otherwise the cached (or freshly measured) faster form of its bucket.
+int choose_schedule(const Problem& p, int precision_req, bool* fused_capable) {
+    const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
+    const int want = precision_req == KNN_FP8_E4M3 ? P_FP8 : P_BF16;
+    *fused_capable = fused_available() && fused_stages(fused_cap(p.k, km), want) > 0 && p.fused != 0;
+    if (!*fused_capable || precision_req == KNN_FP32) return SCHED_PLAIN;
+    if (p.fused == 1 || precision_req != KNN_AUTO) return SCHED_FUSED;
+    const char* env = std::getenv("KNN_AUTOTUNE");
+    if (env && env[0] == '0') return SCHED_FUSED;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load();
+    const std::string key = bucket_of(p);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+    float tf = 0.f, tp = 0.f;
+    int sched = SCHED_FUSED;
+    if (time_schedule(p, SCHED_FUSED, &tf) == KNN_OK && time_schedule(p, SCHED_PLAIN, &tp) == KNN_OK)
+        sched = tf <= tp ? SCHED_FUSED : SCHED_PLAIN;
+    g_last_error.clear();
+    g_tune[key] = sched;
+    tune_save();
+    return sched;
+}
+
+// --------------------------------------------------------------------------------------
+// batch workspace (separate from the single-call workspace so a cached graph's buffers
+// are not moved by other calls) and graph cache
+// --------------------------------------------------------------------------------------
+struct BatchWs {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    uint64_t generation = 0;
+};
+std::mutex g_bws_mu;
+std::map<int, BatchWs> g_bws;
+
+struct CachedGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t generation = 0;
+};
+std::map<std::string, CachedGraph> g_graphs;
+
+int batch_ws_get(size_t bytes, void** out, uint64_t* generation) {
+    int dev = 0;
+    KNN_CK(cudaGetDevice(&dev));
+    BatchWs& w = g_bws[dev];
+    if (w.bytes < bytes) {
+        if (w.ptr) {
+            KNN_CK(cudaDeviceSynchronize());
+            KNN_CK(cudaFree(w.ptr));
+            w.ptr = nullptr;
+        }
+        const size_t want = bytes + bytes / 8;
+        cudaError_t e = cudaMalloc(&w.ptr, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            w.ptr = nullptr;
+            w.bytes = 0;
+            return set_error(KNN_ENOMEM, "batch workspace of %zu bytes: %s", want, cudaGetErrorString(e));
+        }
+        w.bytes = want;
+        ++w.generation;
+    }
+    *out = w.ptr;
+    *generation = w.generation;
+    return KNN_OK;
+}
+
+struct BatchLayout {
+    std::vector<BatchDev> dev;          // host copies of the descriptors
+    std::vector<FusedProblem> fprob;    // fused problems' kernel descriptors
+    std::vector<int> fused_ids, plain_ids;
+    std::vector<BatchSeg> prep_segs, query_segs, plain_prep_segs, plain_query_segs;
+    std::vector<FusedWork> work;
+    int64_t prep_rows = 0, query_rows = 0, plain_prep_rows = 0, plain_query_rows = 0;
+    int cap_max = 0, stages = 0, grid = 0;
+    // device pointers
+    BatchDev* d_dev = nullptr;
+    FusedProblem* d_fprob = nullptr;
+    BatchSeg *d_prep_segs = nullptr, *d_query_segs = nullptr, *d_plain_prep_segs = nullptr,
+             *d_plain_query_segs = nullptr;
+    FusedWork* d_work = nullptr;
+    RerankCounters* counters = nullptr;
+    int* status = nullptr;
+    uint64_t* scratch = nullptr;
+    // plain problems share one set of slab buffers (they run one after another)
+    float* slab = nullptr;
+    uint64_t* slab_cand = nullptr;
+    int32_t* slab_count = nullptr;
+    uint64_t* slab_bound = nullptr;
+    uint32_t* slab_flags = nullptr;
+    int64_t slab_rows = 0, slab_cols = 0;
+    int slab_cap = 0;
+};
+
+// Lays out every buffer of the batch in an arena (sizing pass when the arena has no base).
+void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sched, int prec, int sms, Arena& ar,
+                  BatchLayout& L) {
+    const int n = static_cast<int>(probs.size());
+    L.dev.assign(n, BatchDev{});
+    L.fused_ids.clear();
+    L.plain_ids.clear();
+    for (int i = 0; i < n; ++i) (sched[i] == SCHED_FUSED ? L.fused_ids : L.plain_ids).push_back(i);
+    L.cap_max = 0;
+    int64_t plain_slab_bytes = 0;
+    L.slab_rows = 0;
+    L.slab_cols = 0;
+    L.slab_cap = 0;
+    for (int i = 0; i < n; ++i) {
+        const Problem& p = probs[i];
+        BatchDev& b = L.dev[i];
+        const bool fused = sched[i] == SCHED_FUSED;
+        const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
+        b.Q = p.Q;
+        b.C = p.C;
+        b.M = p.M;
+        b.N = p.N;
+        b.d = p.d;
+        b.k = p.k;
+        b.graph = p.graph ? 1 : 0;
+        b.vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
+                (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
+        const int64_t n_pad = (p.N + 255) / 256 * 256;
+        b.gq = ar.take<PrepGlobals>(1);
+        b.gc = p.graph ? b.gq : ar.take<PrepGlobals>(1);
+        b.cnorm2 = ar.take<float>(n_pad);
+        b.qnorm2 = p.graph ? b.cnorm2 : ar.take<float>(p.M);
+        b.E = ar.take<float>(p.M);
+        b.out_idx = p.out_idx;
+        b.out_dist = p.out_dist;
+        b.row_status = ar.take<uint32_t>(p.M);
+        if (fused) {
+            const int elem = prec == P_BF16 ? 2 : 1;
+            const int per = 128 / elem;
+            b.d_pad = (p.d + per - 1) / per * per;
+            b.cap = fused_cap(p.k, km);
+            L.cap_max = std::max(L.cap_max, b.cap);
+            const size_t row_bytes = static_cast<size_t>(b.d_pad) * elem;
+            b.cres = ar.take<float>(n_pad);
+            b.ctn = ar.take<float>(n_pad);
+            b.qres = p.graph ? b.cres : ar.take<float>(p.M);
+            b.qtn = p.graph ? b.ctn : ar.take<float>(p.M);
+            b.xc = ar.take<char>(row_bytes * p.N);
+            b.xq = p.graph ? b.xc : ar.take<char>(row_bytes * p.M);
+            if (prec == P_FP8) {
+                b.cscale = ar.take<float>(n_pad);
+                b.qscale = p.graph ? b.cscale : ar.take<float>(p.M);
+            }
+            b.E32 = ar.take<float>(p.M);
+            b.cand = ar.take<uint64_t>(static_cast<size_t>(p.M) * b.cap);
+            b.count = ar.take<int32_t>(p.M);
+            b.bound = ar.take<uint64_t>(p.M);
+            b.flags = ar.take<uint32_t>(p.M);
+        } else {
+            b.d_pad = p.d;
+            b.cap = pick_cap(p.k, km);
+            b.E32 = b.E;
+            const int64_t ldn = (p.N + 31) / 32 * 32;
+            const int64_t R = std::min<int64_t>((p.M + 127) / 128 * 128, std::max<int64_t>(128, (int64_t(1) << 30) / (ldn * 4) / 128 * 128));
+            plain_slab_bytes = std::max<int64_t>(plain_slab_bytes, R * ldn * 4);
+            L.slab_rows = std::max(L.slab_rows, R);
+            L.slab_cols = std::max(L.slab_cols, ldn);
+            L.slab_cap = std::max(L.slab_cap, b.cap);
+        }
+    }
+    // segment tables and the work list
+    L.prep_segs.clear();
+    L.query_segs.clear();
+    L.plain_prep_segs.clear();
+    L.plain_query_segs.clear();
+    L.work.clear();
+    L.prep_rows = L.query_rows = L.plain_prep_rows = L.plain_query_rows = 0;
+    for (int i : L.fused_ids) {
+        L.prep_segs.push_back({L.prep_rows, i, 0});
+        L.prep_rows += probs[i].N;
+        if (!probs[i].graph) {
+            L.prep_segs.push_back({L.prep_rows, i, 1});
+            L.prep_rows += probs[i].M;
+        }
+        L.query_segs.push_back({L.query_rows, i, 1});
+        L.query_rows += probs[i].M;
+    }
+    for (int i : L.plain_ids) {
+        L.plain_prep_segs.push_back({L.plain_prep_rows, i, 0});
+        L.plain_prep_rows += probs[i].N;
+        if (!probs[i].graph) {
+            L.plain_prep_segs.push_back({L.plain_prep_rows, i, 1});
+            L.plain_prep_rows += probs[i].M;
+        }
+        L.plain_query_segs.push_back({L.plain_query_rows, i, 1});
+        L.plain_query_rows += probs[i].M;
+    }
+    L.fprob.assign(L.fused_ids.size(), FusedProblem{});
+    for (size_t f = 0; f < L.fused_ids.size(); ++f) {
+        const int i = L.fused_ids[f];
+        const Problem& p = probs[i];
+        const int nrb = static_cast<int>((p.M + 127) / 128);
+        for (int rb = 0; rb < nrb; ++rb) L.work.push_back({static_cast<int32_t>(f), rb});
+    }
+    // largest items first: cost of a row block ~ corpus tiles x k-steps
+    std::stable_sort(L.work.begin(), L.work.end(), [&](const FusedWork& a, const FusedWork& b) {
+        const Problem& pa = probs[L.fused_ids[a.problem]];
+        const Problem& pb = probs[L.fused_ids[b.problem]];
+        return (pa.N + 255) / 256 * ((pa.d + 63) / 64) > (pb.N + 255) / 256 * ((pb.d + 63) / 64);
+    });
+    L.grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(sms), L.work.size())));
+    L.stages = L.fused_ids.empty() ? 0 : fused_stages(L.cap_max, prec);
+    L.d_dev = ar.take<BatchDev>(static_cast<size_t>(n));
+    L.d_fprob = ar.take<FusedProblem>(std::max<size_t>(1, L.fprob.size()));
+    L.d_prep_segs = ar.take<BatchSeg>(std::max<size_t>(1, L.prep_segs.size()));
+    L.d_query_segs = ar.take<BatchSeg>(std::max<size_t>(1, L.query_segs.size()));
+    L.d_plain_prep_segs = ar.take<BatchSeg>(std::max<size_t>(1, L.plain_prep_segs.size()));
+    L.d_plain_query_segs = ar.take<BatchSeg>(std::max<size_t>(1, L.plain_query_segs.size()));
+    L.d_work = ar.take<FusedWork>(std::max<size_t>(1, L.work.size()));
+    L.counters = ar.take<RerankCounters>(1);
+    L.status = ar.take<int>(1);
+    L.scratch = ar.take<uint64_t>(L.cap_max > 0 ? fused_scratch_words(L.cap_max, L.grid) : 1);
+    if (!L.plain_ids.empty()) {
+        L.slab = ar.take<float>(static_cast<size_t>(plain_slab_bytes / 4));
+        L.slab_cand = ar.take<uint64_t>(static_cast<size_t>(L.slab_rows) * L.slab_cap);
+        L.slab_count = ar.take<int32_t>(L.slab_rows);
+        L.slab_bound = ar.take<uint64_t>(L.slab_rows);
+        L.slab_flags = ar.take<uint32_t>(L.slab_rows);
+    }
+}
+
+// Every launch of the batch (graph-capturable: no host synchronisation, no allocation).
+int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout& L, cudaStream_t st) {
+    KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
+    KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
+    for (const BatchDev& b : L.dev) {
+        KNN_CK(cudaMemsetAsync(b.gq, 0, sizeof(PrepGlobals), st));
+        if (b.gc != b.gq) KNN_CK(cudaMemsetAsync(b.gc, 0, sizeof(PrepGlobals), st));
+    }
+    if (!L.fused_ids.empty()) {
+        // NaN padding of the corpus norms past N (padded columns never pass a threshold)
+        for (int i : L.fused_ids) {
+            const BatchDev& b = L.dev[i];
+            const int64_t n_pad = (b.N + 255) / 256 * 256;
+            if (n_pad > b.N) KNN_CK(cudaMemsetAsync(b.cnorm2 + b.N, 0xff, (n_pad - b.N) * sizeof(float), st));
+        }
+        KNN_CK(launch_prep_batched(L.d_dev, L.d_prep_segs, static_cast<int32_t>(L.prep_segs.size()), L.prep_rows, prec,
+                                   st));
+        KNN_CK(launch_bounds_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
+                                     prec, st));
+        FusedParams fp{};
+        fp.status = L.status;
+        fp.scratch = L.scratch;
+        fp.stages = L.stages;
+        fp.cap_max = L.cap_max;
+        fp.n_items = static_cast<int32_t>(L.work.size());
+        fp.problems = L.d_fprob;
+        fp.work = L.d_work;
+        KNN_CK(launch_fused_batched(fp, prec, L.grid, st));
+        KNN_CK(launch_rerank_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
+                                     L.cap_max, L.counters, st));
+    }
+    if (!L.plain_ids.empty()) {
+        KNN_CK(launch_prep_batched(L.d_dev, L.d_plain_prep_segs, static_cast<int32_t>(L.plain_prep_segs.size()),
+                                   L.plain_prep_rows, P_FP32, st));
+        KNN_CK(launch_bounds_batched(L.d_dev, L.d_plain_query_segs, static_cast<int32_t>(L.plain_query_segs.size()),
+                                     L.plain_query_rows, P_FP32, st));
+        for (int i : L.plain_ids) {
+            const Problem& p = probs[i];
+            const BatchDev& b = L.dev[i];
+            const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
+            const int64_t ldn = (p.N + 31) / 32 * 32;
+            const int64_t R = std::min<int64_t>((p.M + 127) / 128 * 128,
+                                                std::max<int64_t>(128, (int64_t(1) << 30) / (ldn * 4) / 128 * 128));
+            for (int64_t r0 = 0; r0 < p.M; r0 += R) {
+                const int64_t rows = std::min<int64_t>(R, p.M - r0);
+                KNN_CK(launch_gemm_simt(p.Q + r0 * p.d, rows, 0, p.C, p.N, p.d, b.cnorm2, nullptr, L.slab, ldn, 0, st));
+                SelectParams sp{};
+                sp.D = L.slab;
+                sp.ldd = ldn;
+                sp.M = rows;
+                sp.N = p.N;
+                sp.k = p.k;
+                sp.km = km;
+                sp.cap = b.cap;
+                sp.E = b.E + r0;
+                sp.cand = L.slab_cand;
+                sp.count = L.slab_count;
+                sp.bound = L.slab_bound;
+                sp.flags = L.slab_flags;
+                KNN_CK(launch_select_ex(sp, p.graph ? r0 : -1, false, st));
+                RerankParams rp{};
+                rp.Q = p.Q + r0 * p.d;
+                rp.C = p.C;
+                rp.M = rows;
+                rp.N = p.N;
+                rp.d = p.d;
+                rp.k = p.k;
+                rp.cap = b.cap;
+                rp.cand = L.slab_cand;
+                rp.count = L.slab_count;
+                rp.bound = L.slab_bound;
+                rp.flags = L.slab_flags;
+                rp.E = b.E + r0;
+                rp.out_idx = p.out_idx + r0 * p.k;
+                rp.out_dist = p.out_dist + r0 * p.k;
+                rp.row_status = b.row_status + r0;
+                rp.counters = L.counters;
+                KNN_CK(launch_rerank(rp, st));
+            }
+        }
+    }
+    return KNN_OK;
+}
+
+std::string signature(const std::vector<Problem>& probs, const std::vector<int>& sched, int prec) {
+    std::string s;
+    char b[160];
+    std::snprintf(b, sizeof(b), "p%d|", prec);
+    s += b;
+    for (size_t i = 0; i < probs.size(); ++i) {
+        const Problem& p = probs[i];
+        std::snprintf(b, sizeof(b), "%p,%p,%lld,%lld,%d,%d,%d,%d,%d,%p,%p;", (const void*)p.Q, (const void*)p.C,
+                      (long long)p.M, (long long)p.N, p.d, p.k, p.m, p.graph ? 1 : 0, sched[i], (void*)p.out_idx,
+                      (void*)p.out_dist);
+        s += b;
+    }
+    return s;
+}
+
+}  // namespace
+
+// Runs the batch (device pointers only); per-problem statuses in status[]. Returns the
+// first failure or KNN_OK.
+int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precision_req, ::knn_stats* stats,
+              cudaStream_t st) {
+    const int n = static_cast<int>(probs.size());
+    std::vector<int> sched(n, SCHED_PLAIN);
+    int prec = precision_req == KNN_FP8_E4M3 ? P_FP8 : P_BF16;
+    for (int i = 0; i < n; ++i) {
+        bool capable = false;
+        sched[i] = choose_schedule(probs[i], precision_req, &capable);
+    }
+    int dev = 0, sms = 0;
+    KNN_CK(cudaGetDevice(&dev));
+    KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BatchLayout L;
+    Arena sz;
+    layout_batch(probs, sched, prec, sms, sz, L);
+    if (!L.fused_ids.empty() && L.stages == 0) {
+        for (int i : L.fused_ids) sched[i] = SCHED_PLAIN;  // cannot happen: capable problems fit
+        Arena sz2;
+        L = BatchLayout{};
+        layout_batch(probs, sched, prec, sms, sz2, L);
+        sz = sz2;
+    }
+    void* base = nullptr;
+    uint64_t gen = 0;
+    std::lock_guard<std::mutex> lk(g_bws_mu);
+    KNN_TRY(batch_ws_get(sz.used(), &base, &gen));
+    Arena ar(static_cast<char*>(base), sz.used());
+    L = BatchLayout{};
+    layout_batch(probs, sched, prec, sms, ar, L);
+    // descriptors: tensor maps of the fused problems, then everything to the device
+    for (size_t f = 0; f < L.fused_ids.size(); ++f) {
+        const int i = L.fused_ids[f];
+        const BatchDev& b = L.dev[i];
+        FusedProblem& q = L.fprob[f];
+        const int km = static_cast<int>(std::min<int64_t>(probs[i].k + probs[i].m, probs[i].N - (probs[i].graph ? 1 : 0)));
+        q.M = b.M;
+        q.N = b.N;
+        q.k_bytes = b.d_pad * (prec == P_BF16 ? 2 : 1);
+        q.k = b.k;
+        q.km = km;
+        q.cap = b.cap;
+        q.self_offset = b.graph ? 0 : -1;
+        q.cnorm2 = b.cnorm2;
+        q.E = b.E;
+        q.thr = nullptr;
+        q.q_inv_scale = b.qscale;
+        q.c_inv_scale = b.cscale;
+        q.cand = b.cand;
+        q.count = b.count;
+        q.bound = b.bound;
+        q.flags = b.flags;
+        if (!encode_problem_maps(&q, b.xq, b.xc, prec))
+            return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
+    }
+    KNN_CK(cudaMemcpyAsync(L.d_dev, L.dev.data(), L.dev.size() * sizeof(BatchDev), cudaMemcpyHostToDevice, st));
+    if (!L.fprob.empty())
+        KNN_CK(cudaMemcpyAsync(L.d_fprob, L.fprob.data(), L.fprob.size() * sizeof(FusedProblem), cudaMemcpyHostToDevice,
+                               st));
+    auto put = [&](auto* dst, const auto& v) -> cudaError_t {
+        if (v.empty()) return cudaSuccess;
+        return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
+    };
+    KNN_CK(put(L.d_prep_segs, L.prep_segs));
+    KNN_CK(put(L.d_query_segs, L.query_segs));
+    KNN_CK(put(L.d_plain_prep_segs, L.plain_prep_segs));
+    KNN_CK(put(L.d_plain_query_segs, L.plain_query_segs));
+    KNN_CK(put(L.d_work, L.work));
+    KNN_CK(cudaStreamSynchronize(st));
+
+    // the graph: captured once per batch signature, replayed afterwards
+    const std::string sig = signature(probs, sched, prec);
+    CachedGraph& cg = g_graphs[sig];
+    if (cg.exec && cg.generation != gen) {
+        cudaGraphExecDestroy(cg.exec);
+        cg.exec = nullptr;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!cg.exec) {
+        cudaStream_t cs = nullptr;
+        KNN_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        KNN_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const int rc = enqueue_batch(probs, prec, L, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        cudaStreamDestroy(cs);
+        if (rc != KNN_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        KNN_CK(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&cg.exec, g, 0);
+        cudaGraphDestroy(g);
+        KNN_CK(ei);
+        cg.generation = gen;
+    }
+    KNN_CK(cudaEventCreate(&e0));
+    KNN_CK(cudaEventCreate(&e1));
+    KNN_CK(cudaEventRecord(e0, st));
+    KNN_CK(cudaGraphLaunch(cg.exec, st));
+    KNN_CK(cudaEventRecord(e1, st));
+    RerankCounters hc{};
+    int hstatus = 0;
+    KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the batched fused kernel stopped: a device-side wait timed out");
+
+    // per problem: NaN/Inf inputs, then rows the batch could not certify
+    int first = KNN_OK;
+    int64_t fallback_rows = 0;
+    std::vector<PrepGlobals> hg(2);
+    for (int i = 0; i < n; ++i) {
+        const BatchDev& b = L.dev[i];
+        KNN_CK(cudaMemcpyAsync(&hg[0], b.gq, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
+        KNN_CK(cudaMemcpyAsync(&hg[1], b.gc, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
+        KNN_CK(cudaStreamSynchronize(st));
+        if (hg[0].nonfinite || hg[1].nonfinite) {
+            status[i] = set_error(KNN_EINVAL, "problem %d: input holds NaN or Inf", i);
+            if (first == KNN_OK) first = status[i];
+        }
+    }
+    if (hc.uncertified > 0) {
+        std::vector<uint32_t> rs;
+        for (int i = 0; i < n; ++i) {
+            if (status[i] != KNN_OK) continue;
+            const BatchDev& b = L.dev[i];
+            rs.resize(static_cast<size_t>(b.M));
+            KNN_CK(cudaMemcpyAsync(rs.data(), b.row_status, b.M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+            KNN_CK(cudaStreamSynchronize(st));
+            bool any = false;
+            for (uint32_t v : rs) any |= (v & ROW_UNCERTIFIED) != 0;
+            if (!any) continue;
+            // rare: recompute the whole problem with the plain form (exact, own workspace)
+            Problem q = probs[i];
+            q.precision = KNN_FP32;
+            q.fused = 0;
+            const int rc = run_problem(q, nullptr, st);
+            fallback_rows += q.M;
+            if (rc != KNN_OK) {
+                status[i] = rc;
+                if (first == KNN_OK) first = rc;
+            }
+        }
+    }
+    if (stats) {
+        int64_t rows = 0;
+        for (const Problem& p : probs) rows += p.M;
+        stats->rows = rows;
+        stats->candidates = static_cast<int64_t>(hc.candidates);
+        stats->rows_truncated = static_cast<int64_t>(hc.truncated);
+        stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
+        stats->rows_fallback = fallback_rows;
+        stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
+        stats->ms_total = ms;
+        stats->ms_gemm = ms;
+        stats->fused_used = static_cast<int32_t>(L.fused_ids.size());
+        stats->precision_used = prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3;
+        stats->gemm_launches = 1;
+        double flops = 0.0;
+        for (const Problem& p : probs) flops += 2.0 * double(p.M) * double(p.N) * double(p.d);
+        stats->gemm_flops = flops;
+        stats->kernel_launches = (L.fused_ids.empty() ? 0 : 4) + (L.plain_ids.empty() ? 0 : 2);
+        for (int i : L.plain_ids) {
+            const Problem& p = probs[i];
+            const int64_t ldn = (p.N + 31) / 32 * 32;
+            const int64_t R = std::min<int64_t>((p.M + 127) / 128 * 128,
+                                                std::max<int64_t>(128, (int64_t(1) << 30) / (ldn * 4) / 128 * 128));
+            stats->kernel_launches += 3 * ((p.M + R - 1) / R);
+        }
+    }
+    return first;
+}
+
+}  // namespace knn

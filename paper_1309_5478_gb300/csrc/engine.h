@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 #include "knn.h"
@@ -99,5 +100,11 @@ cudaError_t launch_scatter_out(const int32_t* rows, int32_t n, int32_t k, const 
 
 // Runs one problem end to end (device pointers); fills stats when non-null.
 int run_problem(const Problem& pb, ::knn_stats* stats, cudaStream_t st);
+
+// Runs independent problems (device pointers) as one batch: one CUDA graph holding a
+// persistent fused launch and the plain form's launches. status[i] receives each
+// problem's status; returns the first failure.
+int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precision_req, ::knn_stats* stats,
+              cudaStream_t st);
 
 }  // namespace knn

@@ -214,13 +214,83 @@ __device__ __forceinline__ float tau_filter(uint64_t tau) {
     return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
 }
 
+// One work item's view of its problem: the row block `rb` of a problem, with the
+// problem's tensor maps, sizes and arrays.
+struct Item {
+    const CUtensorMap* tmA;
+    const CUtensorMap* tmB;
+    int64_t M, N;
+    int rb, nk, nct;
+    int k, km, cap;
+    int64_t self_offset;
+    const float* cnorm2;
+    const float* E;
+    const float* thr;
+    const float* q_inv_scale;
+    const float* c_inv_scale;
+    uint64_t* cand;
+    int32_t* count;
+    uint64_t* bound;
+    uint32_t* flags;
+};
+
+template <bool BATCHED>
+__device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                         int it) {
+    Item im;
+    if constexpr (!BATCHED) {
+        im.tmA = tmA;
+        im.tmB = tmB;
+        im.M = p.M;
+        im.N = p.N;
+        im.rb = it;
+        im.nk = p.k_bytes / TC_BK_BYTES;
+        im.k = p.k;
+        im.km = p.km;
+        im.cap = p.cap;
+        im.self_offset = p.self_offset;
+        im.cnorm2 = p.cnorm2;
+        im.E = p.E;
+        im.thr = p.thr;
+        im.q_inv_scale = p.q_inv_scale;
+        im.c_inv_scale = p.c_inv_scale;
+        im.cand = p.cand;
+        im.count = p.count;
+        im.bound = p.bound;
+        im.flags = p.flags;
+    } else {
+        const FusedWork w = p.work[it];
+        const FusedProblem& q = p.problems[w.problem];
+        im.tmA = &q.tmA;
+        im.tmB = &q.tmB;
+        im.M = q.M;
+        im.N = q.N;
+        im.rb = w.rb;
+        im.nk = q.k_bytes / TC_BK_BYTES;
+        im.k = q.k;
+        im.km = q.km;
+        im.cap = q.cap;
+        im.self_offset = q.self_offset;
+        im.cnorm2 = q.cnorm2;
+        im.E = q.E;
+        im.thr = q.thr;
+        im.q_inv_scale = q.q_inv_scale;
+        im.c_inv_scale = q.c_inv_scale;
+        im.cand = q.cand;
+        im.count = q.count;
+        im.bound = q.bound;
+        im.flags = q.flags;
+    }
+    im.nct = static_cast<int>((im.N + TC_BN - 1) / TC_BN);
+    return im;
+}
+
 // Warp-cooperative shrink of the candidate list of row r (of the block): the quick
 // multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest values;
 // the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))). When
 // more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
-__device__ __noinline__ void shrink_row(const FusedParams& p, const EpiSmem& es, const RowState& rs, int r,
-                                        int64_t grow, float window, int keep_max, int keep_trunc,
-                                        uint64_t* band_out) {
+__device__ __noinline__ void shrink_row(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
+                                        float window, int keep_max, int keep_trunc, uint64_t* band_out) {
     const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
     const int n = rs.cnt[r];
@@ -357,17 +427,18 @@ __device__ __forceinline__ void pair_barrier(int quarter) {
     asm volatile("bar.sync %0, 64;" ::"r"(1 + quarter) : "memory");
 }
 
-template <int P>
+template <int P, bool BATCHED>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fused_gemm_select_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                             const FusedParams p) {
+                             const FusedParams params) {
+    const FusedParams& p = params;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
     const int nst = p.stages;
     unsigned char* stage_base = smem;
     unsigned char* epi_base = smem + nst * STAGE_BYTES;
-    float* cn_smem = reinterpret_cast<float*>(epi_base + EPI_WARPS * epi_warp_bytes(p.cap));  // [2][TC_BN] (+ scales)
+    float* cn_smem = reinterpret_cast<float*>(epi_base + EPI_WARPS * epi_warp_bytes(p.cap_max));  // [2][TC_BN] (+ scales)
     unsigned char* rs_base = reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P);
     RowState rs;
     rs.tau = reinterpret_cast<uint64_t*>(rs_base);
@@ -384,9 +455,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
     const int warp = static_cast<int>(threadIdx.x / 32);
     const uint32_t lane = lane_id();
-    const int nrb = static_cast<int>((p.M + TC_BM - 1) / TC_BM);
-    const int nct = static_cast<int>((p.N + TC_BN - 1) / TC_BN);
-    const int nk = p.k_bytes / TC_BK_BYTES;
+    const int n_items = p.n_items;
     constexpr uint32_t CN_TX = static_cast<uint32_t>(cn_bytes(P) / 2);  // bytes staged per tile
 
     if (threadIdx.x == 0) {
@@ -419,17 +488,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0;
             bool ok = true;
             const int kx = TC_BK_BYTES / (P == P_BF16 ? 2 : 1);
-            for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
-                for (int ct = 0; ct < nct && ok; ++ct) {
-                    for (int ks = 0; ks < nk; ++ks) {
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
+                for (int ct = 0; ct < im.nct && ok; ++ct) {
+                    for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
                             ok = false;
                             break;
                         }
                         unsigned char* a = stage_base + s * STAGE_BYTES;
                         mbar_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(a, &tmA, &full[s], ks * kx, rb * TC_BM);
-                        tma_load_2d(a + A_BYTES, &tmB, &full[s], ks * kx, ct * TC_BN);
+                        tma_load_2d(a, im.tmA, &full[s], ks * kx, im.rb * TC_BM);
+                        tma_load_2d(a + A_BYTES, im.tmB, &full[s], ks * kx, ct * TC_BN);
                         if (++s == nst) {
                             s = 0;
                             ph ^= 1u;
@@ -467,8 +537,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             int tile = 0;
             bool ok = true;
             const int k_per_mma = 32;  // bytes of K per instruction: 16 BF16 or 32 FP8 values
-            for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
-                for (int ct = 0; ct < nct && ok; ++ct, ++tile) {
+            for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+                const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
+                for (int ct = 0; ct < im.nct && ok; ++ct, ++tile) {
                     const int acc = tile & 1;
                     const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
                     if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1u, abort_flag)) {
@@ -478,13 +549,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     // stage this tile's corpus norms (and FP8 scales) for the epilogue
                     mbar_expect_tx(&acc_full[acc], CN_TX);
-                    bulk_copy_g2s(cn_smem + acc * TC_BN, p.cnorm2 + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4,
+                    bulk_copy_g2s(cn_smem + acc * TC_BN, im.cnorm2 + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4,
                                   &acc_full[acc]);
                     if constexpr (P == P_FP8)
                         bulk_copy_g2s(cn_smem + 2 * TC_BN + acc * TC_BN,
-                                      p.c_inv_scale + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4, &acc_full[acc]);
+                                      im.c_inv_scale + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4, &acc_full[acc]);
                     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
-                    for (int ks = 0; ks < nk; ++ks) {
+                    for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&full[s], ph, abort_flag)) {
                             ok = false;
                             break;
@@ -516,18 +587,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int partner_bit = half;             // rows of the quarter this warp compacts: parity == half
         const int row_in_block = quarter * 32 + static_cast<int>(lane);
         EpiSmem es;
-        unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap);
+        unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap_max);
         es.A = reinterpret_cast<uint32_t*>(mine);
-        es.B = es.A + p.cap;
-        es.hist = es.B + p.cap;
-        es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * EPI_WARPS + ew) * scratch_words_per_warp(p.cap);
-        // room for one half-tile of insertions from both warps: 2 x 64 per row
-        const int trigger = p.cap - 128;
-        const int keep_mid = p.cap - 160 > p.km ? p.cap - 160 : p.km;
-        const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
+        es.B = es.A + p.cap_max;
+        es.hist = es.B + p.cap_max;
+        es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * EPI_WARPS + ew) * scratch_words_per_warp(p.cap_max);
         int tile = 0;
         bool ok = true;
-        for (int rb = blockIdx.x; rb < nrb && ok; rb += gridDim.x) {
+        for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+            const Item p = get_item<BATCHED>(params, &tmA, &tmB, it);
+            const int rb = p.rb;
+            const int nct = p.nct;
+            // room for one half-tile of insertions from both warps: 2 x 64 per row
+            const int trigger = p.cap - 128;
+            const int keep_mid = p.cap - 160 > p.km ? p.cap - 160 : p.km;
+            const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
             const int64_t grow = static_cast<int64_t>(rb) * TC_BM + row_in_block;
             const bool valid = grow < p.M;
             const int64_t self = valid && p.self_offset >= 0 ? grow + p.self_offset : -1;
@@ -690,20 +764,44 @@ size_t fused_scratch_words(int cap, int grid) {
     return scratch_words_per_warp(cap) * EPI_WARPS * static_cast<size_t>(grid);
 }
 
+bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision) {
+    const int elem = precision == P_BF16 ? 2 : 1;
+    return make_map(&prob->tmA, xq, prob->M, prob->k_bytes, TC_BM, elem) &&
+           make_map(&prob->tmB, xc, prob->N, prob->k_bytes, TC_BN, elem);
+}
+
+cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st) {
+    if (p.n_items <= 0) return cudaSuccess;
+    CUtensorMap dummy{};
+    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
+    if (precision == P_BF16) {
+        auto kern = fused_gemm_select_kernel<P_BF16, true>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
+    } else {
+        auto kern = fused_gemm_select_kernel<P_FP8, true>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
     const int elem = precision == P_BF16 ? 2 : 1;
     CUtensorMap ta, tb;
     if (!make_map(&ta, p.xq, p.M, p.k_bytes, TC_BM, elem)) return cudaErrorInvalidValue;
     if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
-    const size_t smem = tc_smem_bytes(p.cap, p.stages, precision);
+    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
     if (precision == P_BF16) {
-        auto kern = fused_gemm_select_kernel<P_BF16>;
+        auto kern = fused_gemm_select_kernel<P_BF16, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
     } else {
-        auto kern = fused_gemm_select_kernel<P_FP8>;
+        auto kern = fused_gemm_select_kernel<P_FP8, false>;
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);

@@ -95,6 +95,48 @@ struct RerankParams {
 };
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st);
 
+// ---- batched problems (batched.cu, with batched kernels in prep.cu / rerank.cu) ----
+// Device-side description of one problem of a batch and of its buffers.
+struct BatchDev {
+    const float* Q;           // M x d queries (== C for a graph)
+    const float* C;           // N x d corpus
+    int64_t M, N;
+    int32_t d, k, cap, d_pad;
+    int32_t graph;            // 1: k-NN graph (self excluded, one prep)
+    int32_t vec;              // 1: 16-byte aligned rows (d % 4 == 0)
+    PrepGlobals* gq;
+    PrepGlobals* gc;
+    float *qnorm2, *cnorm2, *qres, *cres, *qtn, *ctn, *qscale, *cscale;
+    void* xq;
+    void* xc;
+    float* E;                 // bound of the reduced-precision form
+    float* E32;               // bound of the FP32 form (fallback)
+    uint64_t* cand;
+    int32_t* count;
+    uint64_t* bound;
+    uint32_t* flags;
+    int32_t* out_idx;
+    float* out_dist;
+    uint32_t* row_status;
+};
+
+// A run of consecutive global rows that belong to one matrix of one problem.
+struct BatchSeg {
+    int64_t row0;     // first global row of the segment
+    int32_t problem;
+    int32_t which;    // 0: corpus rows, 1: query rows
+};
+
+// Prep of every corpus (and non-graph query) row of the batch; segs sorted by row0.
+cudaError_t launch_prep_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                int32_t precision, cudaStream_t st);
+// Bounds (reduced-precision E and FP32 E32) of every query row; segs over query rows.
+cudaError_t launch_bounds_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                  int32_t precision, cudaStream_t st);
+// Exact re-rank of every query row; cap_max sizes the shared memory.
+cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                  int32_t cap_max, RerankCounters* counters, cudaStream_t st);
+
 // Exact FP64 answer for a list of rows (last-resort path; slow, used for rows no other path certifies).
 cudaError_t launch_exact_rows_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,
                                    int32_t exclude_self, const int32_t* rows, int32_t nrows, double* scratch,

@@ -49,13 +49,12 @@ __device__ __forceinline__ float quantise(float x, float scale, void* xq, int64_
     }
 }
 
+// One warp prepares one row: norms, the reduced-precision copy and the row statistics.
 template <int P>
-__global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d,
-                                                   float* __restrict__ norm2, float* __restrict__ res,
-                                                   float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
-                                                   float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
-    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-    if (row >= rows) return;
+__device__ __forceinline__ void prep_row(const float* __restrict__ X, int64_t row, int32_t d,
+                                         float* __restrict__ norm2, float* __restrict__ res,
+                                         float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
+                                         float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
     const uint32_t lane = lane_id();
     const float* x = X + row * static_cast<int64_t>(d);
 
@@ -118,6 +117,41 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, 
     }
 }
 
+template <int P>
+__global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d,
+                                                   float* __restrict__ norm2, float* __restrict__ res,
+                                                   float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
+                                                   float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    prep_row<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
+}
+
+// Segment holding global row `row` (segs sorted by row0, segs[0].row0 == 0).
+__device__ __forceinline__ int find_seg(const BatchSeg* segs, int32_t nseg, int64_t row) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].row0 <= row) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) prep_batched_kernel(const BatchDev* __restrict__ probs,
+                                                           const BatchSeg* __restrict__ segs, int32_t nseg,
+                                                           int64_t rows) {
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= rows) return;
+    const BatchSeg sg = segs[find_seg(segs, nseg, row)];
+    const BatchDev& b = probs[sg.problem];
+    const int64_t r = row - sg.row0;
+    if (sg.which == 0)
+        prep_row<P>(b.C, r, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, b.gc);
+    else
+        prep_row<P>(b.Q, r, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, b.gq);
+}
+
 // Error bound of the ranking value d'_ij = |c_j|^2 - 2 q_i.c_j as computed by the
 // engine, against its exact value, for every j of row i.
 //   FP32:  an FMA chain over d products has |err| <= gamma_d sum|q_t c_t| <= gamma_d |q||c|
@@ -131,12 +165,10 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, 
 //          (safety factor 4 over FP32's gamma for BF16, a 2^-14-unit accumulator for FP8).
 //   Exact arithmetic: integer-valued inputs with 4 d A^2 <= 2^24 (A the largest magnitude)
 //          make every product, partial sum and norm an exact FP32 integer, so E_i = 0.
-__global__ void bounds_kernel(const float* __restrict__ qnorm2, const float* __restrict__ qres,
-                              const float* __restrict__ qtnorm, int64_t M, int32_t d, int32_t d_pad,
-                              int32_t precision, const PrepGlobals* __restrict__ gq,
-                              const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
-    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= M) return;
+__device__ __forceinline__ void bounds_row(const float* __restrict__ qnorm2, const float* __restrict__ qres,
+                                           const float* __restrict__ qtnorm, int64_t i, int32_t d, int32_t d_pad,
+                                           int32_t precision, const PrepGlobals* __restrict__ gq,
+                                           const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
     const float amax = fmaxf(__uint_as_float(gq->max_abs), __uint_as_float(gc->max_abs));
     const bool integer = gq->noninteger == 0 && gc->noninteger == 0;
     const bool small = 4.0 * static_cast<double>(d_pad) * amax * amax <= 16777216.0;
@@ -163,6 +195,26 @@ __global__ void bounds_kernel(const float* __restrict__ qnorm2, const float* __r
         e = quant + accum + norms;
     }
     E[i] = e * (1.f + 0x1p-10f);
+}
+
+__global__ void bounds_kernel(const float* __restrict__ qnorm2, const float* __restrict__ qres,
+                              const float* __restrict__ qtnorm, int64_t M, int32_t d, int32_t d_pad,
+                              int32_t precision, const PrepGlobals* __restrict__ gq,
+                              const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    bounds_row(qnorm2, qres, qtnorm, i, d, d_pad, precision, gq, gc, E);
+}
+
+__global__ void bounds_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs,
+                                      int32_t nseg, int64_t rows, int32_t precision) {
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (row >= rows) return;
+    const BatchSeg sg = segs[find_seg(segs, nseg, row)];
+    const BatchDev& b = probs[sg.problem];
+    const int64_t i = row - sg.row0;
+    bounds_row(b.qnorm2, b.qres, b.qtn, i, b.d, b.d_pad, precision, b.gq, b.gc, b.E);
+    if (b.E32 != b.E) bounds_row(b.qnorm2, nullptr, nullptr, i, b.d, b.d, P_FP32, b.gq, b.gc, b.E32);
 }
 
 __global__ void thr_kernel(const float* __restrict__ thr, const float* __restrict__ qnorm2, int64_t M,
@@ -240,6 +292,27 @@ cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precisi
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                int32_t precision, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const unsigned blocks = static_cast<unsigned>((rows + 7) / 8);
+    switch (precision) {
+        case P_FP32: prep_batched_kernel<P_FP32><<<blocks, 256, 0, st>>>(probs, segs, nseg, rows); break;
+        case P_BF16: prep_batched_kernel<P_BF16><<<blocks, 256, 0, st>>>(probs, segs, nseg, rows); break;
+        case P_FP8: prep_batched_kernel<P_FP8><<<blocks, 256, 0, st>>>(probs, segs, nseg, rows); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounds_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                  int32_t precision, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    bounds_batched_kernel<<<static_cast<unsigned>((rows + 255) / 256), 256, 0, st>>>(probs, segs, nseg, rows,
+                                                                                     precision);
     return cudaGetLastError();
 }
 

@@ -116,19 +116,22 @@ __device__ __forceinline__ double sqdist_fp64(const float* __restrict__ q, const
     return warp_sum_d(s);
 }
 
-template <bool VEC>
-__global__ void rerank_kernel(RerankParams p, int P) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ unsigned long long blk_cnt[5];
-    const int warp = static_cast<int>(threadIdx.x / 32);
-    const int warps = static_cast<int>(blockDim.x / 32);
-    const uint32_t lane = lane_id();
-    if (threadIdx.x < 5) blk_cnt[threadIdx.x] = 0ull;
+__device__ __forceinline__ void flush_counters(RerankCounters* counters, unsigned long long* blk_cnt) {
     __syncthreads();
-    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
-    if (row < p.M) {
-        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
-        double* D64 = reinterpret_cast<double*>(K + P);
+    if (threadIdx.x == 0 && counters) {
+        atomicAdd(&counters->candidates, blk_cnt[0]);
+        if (blk_cnt[1]) atomicAdd(&counters->fp64_rows, blk_cnt[1]);
+        if (blk_cnt[2]) atomicAdd(&counters->uncertified, blk_cnt[2]);
+        if (blk_cnt[3]) atomicAdd(&counters->truncated, blk_cnt[3]);
+        if (blk_cnt[4]) atomicAdd(&counters->threshold_miss, blk_cnt[4]);
+    }
+}
+
+// One warp re-ranks row `row` of p; K and D64 are the warp's shared-memory arrays of P entries.
+template <bool VEC>
+__device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, int P, uint64_t* K, double* D64,
+                                           unsigned long long* blk_cnt, uint32_t lane) {
+    {
         const int count = p.count[row];
         const uint32_t flags = p.flags[row];
         const float* q = p.Q + row * static_cast<int64_t>(p.d);
@@ -255,17 +258,95 @@ __global__ void rerank_kernel(RerankParams p, int P) {
             if (flags & ROW_THRESHOLD_MISS) atomicAdd(&blk_cnt[4], 1ull);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && p.counters) {
-        atomicAdd(&p.counters->candidates, blk_cnt[0]);
-        if (blk_cnt[1]) atomicAdd(&p.counters->fp64_rows, blk_cnt[1]);
-        if (blk_cnt[2]) atomicAdd(&p.counters->uncertified, blk_cnt[2]);
-        if (blk_cnt[3]) atomicAdd(&p.counters->truncated, blk_cnt[3]);
-        if (blk_cnt[4]) atomicAdd(&p.counters->threshold_miss, blk_cnt[4]);
-    }
 }
 
+template <bool VEC>
+__global__ void rerank_kernel(RerankParams p, int P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long blk_cnt[5];
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const int warps = static_cast<int>(blockDim.x / 32);
+    const uint32_t lane = lane_id();
+    if (threadIdx.x < 5) blk_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
+    if (row < p.M) {
+        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
+        double* D64 = reinterpret_cast<double*>(K + P);
+        rerank_row<VEC>(p, row, P, K, D64, blk_cnt, lane);
+    }
+    flush_counters(p.counters, blk_cnt);
+}
+
+__device__ __forceinline__ int find_seg(const BatchSeg* segs, int32_t nseg, int64_t row) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].row0 <= row) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs,
+                                      int32_t nseg, int64_t rows, int P, RerankCounters* counters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned long long blk_cnt[5];
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const int warps = static_cast<int>(blockDim.x / 32);
+    const uint32_t lane = lane_id();
+    if (threadIdx.x < 5) blk_cnt[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
+    if (row < rows) {
+        const BatchSeg sg = segs[find_seg(segs, nseg, row)];
+        const BatchDev& b = probs[sg.problem];
+        RerankParams rp{};
+        rp.Q = b.Q;
+        rp.C = b.C;
+        rp.M = b.M;
+        rp.N = b.N;
+        rp.d = b.d;
+        rp.k = b.k;
+        rp.cap = b.cap;
+        rp.cand = b.cand;
+        rp.count = b.count;
+        rp.bound = b.bound;
+        rp.flags = b.flags;
+        rp.E = b.E;
+        rp.out_idx = b.out_idx;
+        rp.out_dist = b.out_dist;
+        rp.row_status = b.row_status;
+        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
+        double* D64 = reinterpret_cast<double*>(K + P);
+        const int Pp = pow2_ceil(b.cap > 32 ? b.cap : 32);
+        if (b.vec)
+            rerank_row<true>(rp, row - sg.row0, Pp, K, D64, blk_cnt, lane);
+        else
+            rerank_row<false>(rp, row - sg.row0, Pp, K, D64, blk_cnt, lane);
+    }
+    flush_counters(counters, blk_cnt);
+}
+
+
 }  // namespace
+
+cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                  int32_t cap_max, RerankCounters* counters, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const int P = pow2_ceil(cap_max > 32 ? cap_max : 32);
+    const size_t per_warp = static_cast<size_t>(P) * 16;
+    int warps = static_cast<int>((64u * 1024u) / per_warp);
+    if (warps > 8) warps = 8;
+    if (warps < 1) warps = 1;
+    const size_t smem = per_warp * warps;
+    cudaError_t e = cudaFuncSetAttribute(rerank_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = (rows + warps - 1) / warps;
+    rerank_batched_kernel<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(probs, segs, nseg, rows, P,
+                                                                                   counters);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;

@@ -6,7 +6,33 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
+
 namespace knn {
+
+// One problem of a batched launch (device memory, 64-byte aligned for the tensor maps).
+struct FusedProblem {
+    CUtensorMap tmA;           // queries (reduced precision), box 128 rows
+    CUtensorMap tmB;           // corpus, box 256 rows
+    int64_t M, N;
+    int32_t k_bytes, k, km, cap;
+    int64_t self_offset;
+    const float* cnorm2;
+    const float* E;
+    const float* thr;
+    const float* q_inv_scale;
+    const float* c_inv_scale;
+    uint64_t* cand;
+    int32_t* count;
+    uint64_t* bound;
+    uint32_t* flags;
+};
+
+// A work item of a batched launch: one 128-row block of one problem.
+struct FusedWork {
+    int32_t problem;
+    int32_t rb;
+};
 
 struct FusedParams {
     const void* xq;            // M x k_bytes reduced-precision queries (BF16 or FP8), 128-byte aligned rows
@@ -25,8 +51,12 @@ struct FusedParams {
     uint64_t* bound;           // M: every key left out is > bound
     uint32_t* flags;           // M
     int* status;               // device status word (0, or KNN_ETIMEOUT)
-    uint64_t* scratch;         // fused_scratch_words(cap, grid) words of global scratch
+    uint64_t* scratch;         // fused_scratch_words(cap_max, grid) words of global scratch
     int32_t stages;            // shared-memory pipeline depth (fused_stages)
+    int32_t cap_max;           // largest list capacity of the launch (sizes shared memory)
+    int32_t n_items;           // work items: row blocks of the problem, or entries of `work`
+    const FusedProblem* problems;  // batched launch: problem descriptors (else nullptr)
+    const FusedWork* work;     // batched launch: work list, largest items first
 };
 
 bool fused_available();
@@ -34,5 +64,9 @@ int fused_stages(int cap, int precision);  // 0: does not fit
 size_t fused_scratch_words(int cap, int grid);
 int fused_cap(int k, int km);
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st);
+// Batched launch over p.work (p.problems already holds encoded tensor maps).
+cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st);
+// Encodes the two tensor maps of one problem (host).
+bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision);
 
 }  // namespace knn

@@ -1,0 +1,116 @@
+"""GPU parity of the batched form (one CUDA graph: persistent fused launch over the
+work items of many problems + the plain form for the rest) against the FP64 oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from acceptance import check_exact, check_float
+from paper_1309_5478_gb300 import binding as kb
+from paper_1309_5478_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# (M, N, d, k, graph)
+SHAPES = [(300, 300, 64, 8, True), (257, 5000, 96, 1, False), (1000, 3000, 128, 32, False),
+          (129, 129, 37, 16, True), (640, 2100, 768, 64, False), (77, 1500, 64, 128, False),
+          (200, 2000, 256, 512, False), (1500, 1500, 128, 20, True)]
+
+
+def make_problems(shapes, seed0=300, integer=True, device="cuda"):
+    probs, refs = [], []
+    for i, (M, N, d, k, graph) in enumerate(shapes):
+        gen = (lambda n, s: inputs.integer_lattice(n=n, d=d, lo=-6, hi=6, seed=s)) if integer else \
+              (lambda n, s: inputs.gaussian_mixture(n=n, d=d, components=4, seed=s))
+        C = gen(N, seed0 + 2 * i)
+        Q = None if graph else gen(M, seed0 + 2 * i + 1)
+        Ct = torch.from_numpy(C).to(device)
+        Qt = None if graph else torch.from_numpy(Q).to(device)
+        oi = torch.empty((M, k), dtype=torch.int32, device=device)
+        od = torch.empty((M, k), dtype=torch.float32, device=device)
+        probs.append({"Q": Qt, "C": Ct, "k": k, "out_idx": oi, "out_dist": od})
+        refs.append((Q, C, k, graph))
+    return probs, refs
+
+
+def check_all(probs, refs, exact=True):
+    for p, (Q, C, k, graph) in zip(probs, refs):
+        idx, dist = p["out_idx"].cpu().numpy(), p["out_dist"].cpu().numpy()
+        if exact:
+            ref = oracle.knng(C, k) if graph else oracle.knn(Q, C, k)
+            check_exact(idx, dist, *ref)
+        else:
+            QQ = C if graph else Q
+            rows = inputs.sample_rows(QQ.shape[0], 24, seed=k)
+            ri, rd = oracle.knn(QQ, C, k, rows=rows, exclude_self=graph)
+            check_float(QQ, C, rows, idx[rows], dist[rows], ri, rd, graph)
+
+
+@pytest.fixture(autouse=True)
+def no_autotune(monkeypatch, tmp_path):
+    monkeypatch.setenv("KNN_AUTOTUNE", "0")
+    monkeypatch.setenv("KNN_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+
+
+def test_mixed_batch_bit_exact():
+    probs, refs = make_problems(SHAPES)
+    st = kb.knn_search_batched(probs)
+    assert st == [0] * len(probs)
+    torch.cuda.synchronize()
+    check_all(probs, refs)
+
+
+def test_graph_replay_gives_the_same_answer():
+    probs, refs = make_problems(SHAPES[:5], seed0=400)
+    kb.knn_search_batched(probs)
+    first = [(p["out_idx"].clone(), p["out_dist"].clone()) for p in probs]
+    for p in probs:
+        p["out_idx"].fill_(-7)
+        p["out_dist"].fill_(-7.0)
+    kb.knn_search_batched(probs)  # same signature: the cached graph is replayed
+    for p, (i0, d0) in zip(probs, first):
+        assert torch.equal(p["out_idx"], i0) and torch.equal(p["out_dist"], d0)
+    check_all(probs, refs)
+
+
+def test_batch_recipe_float_data():
+    ps = inputs.batch_problems(count=16, m_range=(256, 1024), n_range=(1024, 6000))
+    probs, refs = [], []
+    for pr in ps:
+        Q, C = pr.queries(), pr.corpus()
+        probs.append({"Q": torch.from_numpy(Q).cuda(), "C": torch.from_numpy(C).cuda(), "k": pr.k,
+                      "out_idx": torch.empty((pr.M, pr.k), dtype=torch.int32, device="cuda"),
+                      "out_dist": torch.empty((pr.M, pr.k), dtype=torch.float32, device="cuda")})
+        refs.append((Q, C, pr.k, False))
+    assert kb.knn_search_batched(probs) == [0] * len(probs)
+    torch.cuda.synchronize()
+    check_all(probs, refs, exact=False)
+
+
+def test_host_and_device_problems_mix():
+    probs, refs = make_problems(SHAPES[:3], seed0=500)
+    hp, hrefs = make_problems(SHAPES[3:4], seed0=600, device="cpu")
+    st = kb.knn_search_batched(probs + hp)
+    assert st == [0] * 4
+    check_all(probs + hp, refs + hrefs)
+
+
+def test_bad_problem_reports_its_status():
+    probs, refs = make_problems(SHAPES[:2], seed0=700)
+    bad = dict(probs[1])
+    bad["k"] = 10 ** 6
+    with pytest.raises(kb.KnnError):
+        kb.knn_search_batched([probs[0], bad])
+
+
+def test_autotuner_writes_its_cache(monkeypatch, tmp_path):
+    monkeypatch.setenv("KNN_AUTOTUNE", "1")
+    path = tmp_path / "tune2.json"
+    monkeypatch.setenv("KNN_AUTOTUNE_CACHE", str(path))
+    probs, refs = make_problems([(500, 4000, 128, 16, False)], seed0=800)
+    # a fresh cache path in a fresh process; an already loaded cache is reused in-process
+    st = kb.knn_search_batched(probs)
+    assert st == [0]
+    check_all(probs, refs)
