@@ -121,7 +121,7 @@ __global__ void synth_kernel(float* x, int64_t n, uint64_t seed) {
 
 // Times one schedule on a synthetic problem of p's shape (fewer query rows); ms per row.
 int time_schedule(const Problem& p, int sched, float* ms_per_row) {
-    const int64_t M = std::min<int64_t>(p.M, 1024);
+    const int64_t M = std::min<int64_t>(p.M, 4096);
     float *Q = nullptr, *C = nullptr, *od = nullptr;
     int32_t* oi = nullptr;
     cudaStream_t st = nullptr;
@@ -163,6 +163,16 @@ int time_schedule(const Problem& p, int sched, float* ms_per_row) {
             if (rep > 0) best = std::min(best, t);
             cudaEventDestroy(a);
             cudaEventDestroy(b);
+        }
+        // In a batch the fused kernel's row blocks share every SM with other problems'
+        // work items; alone, a problem of nrb row blocks occupies only nrb SMs. Charge the
+        // fused form for the share of the GPU it actually used.
+        if (sched == SCHED_FUSED) {
+            int dev = 0, sms = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const double nrb = static_cast<double>((M + 127) / 128);
+            best *= static_cast<float>(std::min(1.0, nrb / sms));
         }
         *ms_per_row = best / static_cast<float>(M);
     }
