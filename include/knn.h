@@ -171,6 +171,57 @@ typedef struct knn_problem {
  */
 int knn_search_batched(knn_problem* probs, int32_t count, const knn_options* opt);
 
+/*
+ * Learned per-row threshold (the paper has no counterpart). A small network
+ * proposes, for each query row, a squared distance below which its k nearest
+ * neighbours lie; passed as knn_options.row_threshold it pre-filters candidates, and
+ * rows where it cuts into the answer are recomputed without it, so results stay exact.
+ *   features (KNN_MLP_FEATURES per row): log |q|^2 and the sorted log squared distances
+ *     to KNN_MLP_FEATURES - 1 corpus samples chosen by the caller;
+ *   network: KNN_MLP_FEATURES -> KNN_MLP_HIDDEN (ReLU) -> 1, FP32, predicting the log of
+ *     the row's exact k-th squared distance from standardised features;
+ *   parameters: one FP32 array of knn_mlp_param_count() entries laid out as
+ *     W1[H][F] | b1[H] | W2[H] | b2 | mu[F] | sigma[F] | margin
+ *     (the first H*F + 2H + 1 are trained; mu/sigma standardise the features; margin is
+ *     added to the log prediction to form the threshold).
+ * All arrays are device pointers; the caller owns them. Calls are synchronous.
+ */
+#define KNN_MLP_FEATURES 257
+#define KNN_MLP_HIDDEN 128
+
+int32_t knn_mlp_param_count(void);
+
+/* Features of the M query rows Q (M x d) against the samples S (KNN_MLP_FEATURES-1 x d);
+ * out_features: M x KNN_MLP_FEATURES. */
+int knn_mlp_features(const float* Q, int64_t M, const float* S, int32_t d, float* out_features,
+                     const knn_options* opt);
+
+/* Mean squared error 1/n sum (y - t)^2 of the network on (features, targets) and its
+ * gradient with respect to the trained parameters (out_grad: H*F + 2H + 1 floats,
+ * device; out_loss: host). mu and sigma in params are used as they are. */
+int knn_mlp_loss_grad(const float* features, const float* targets, int64_t n, const float* params,
+                      double* out_loss, float* out_grad, const knn_options* opt);
+
+/* Trains params in place with Adam (lr, betas 0.9/0.999) on mini-batches of `batch` rows
+ * in the given row order for `epochs` epochs, holding out the last round(holdout n) rows;
+ * mu/sigma are set from those rows first. The margin is set to the margin_quantile
+ * quantile of the held-out residuals t - y (at least 0). out_history (host, optional,
+ * `epochs` floats) receives the mean training loss of every epoch. */
+int knn_mlp_train(const float* features, const float* targets, int64_t n, float* params, int32_t epochs,
+                  int32_t batch, float lr, float holdout, float margin_quantile, float* out_history,
+                  const knn_options* opt);
+
+/* Predictions: out_log_kth (optional) receives y; out_threshold (optional) receives
+ * exp(y + margin), the squared-distance threshold for knn_options.row_threshold. */
+int knn_mlp_predict(const float* features, int64_t n, const float* params, float* out_log_kth,
+                    float* out_threshold, const knn_options* opt);
+
+/* Parameter file: magic "KNNMLP01", int32 features, int32 hidden, int32 count, then
+ * count FP32 parameters (little-endian). params may be a host or a device pointer;
+ * knn_mlp_load rejects a file of another network shape with KNN_EINVAL. */
+int knn_mlp_save(const char* path, const float* params);
+int knn_mlp_load(const char* path, float* params);
+
 /* Human-readable name of a status code. */
 const char* knn_status_string(int status);
 

@@ -52,7 +52,10 @@ class KnnProblem(ctypes.Structure):
 # Every symbol include/knn.h declares (checked by the tests).
 EXPORTS = ("knn_options_init", "knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_distances",
            "knn_search_batched", "knn_status_string", "knn_last_error", "knn_shutdown", "knn_version",
-           "knn_select_noalloc")
+           "knn_select_noalloc", "knn_mlp_param_count", "knn_mlp_features", "knn_mlp_loss_grad", "knn_mlp_train",
+           "knn_mlp_predict", "knn_mlp_save", "knn_mlp_load")
+MLP_FEATURES, MLP_HIDDEN = 257, 128
+MLP_TRAINED = MLP_HIDDEN * MLP_FEATURES + 2 * MLP_HIDDEN + 1
 
 _lock = threading.Lock()
 _lib = None
@@ -92,6 +95,16 @@ def load(path: str | None = None):
         lib.knn_search_batched.argtypes = [ctypes.POINTER(KnnProblem), i32, opt_p]
         lib.knn_select_noalloc.argtypes = [vp, i64, i64, i64, i32, vp, vp, vp]
         lib.knn_select_noalloc.restype = ctypes.c_int
+        lib.knn_mlp_param_count.restype = ctypes.c_int32
+        lib.knn_mlp_features.argtypes = [vp, i64, vp, i32, vp, opt_p]
+        lib.knn_mlp_loss_grad.argtypes = [vp, vp, i64, vp, ctypes.POINTER(ctypes.c_double), vp, opt_p]
+        lib.knn_mlp_train.argtypes = [vp, vp, i64, vp, i32, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      vp, opt_p]
+        lib.knn_mlp_predict.argtypes = [vp, i64, vp, vp, vp, opt_p]
+        lib.knn_mlp_save.argtypes = [ctypes.c_char_p, vp]
+        lib.knn_mlp_load.argtypes = [ctypes.c_char_p, vp]
+        for f in ("knn_mlp_save", "knn_mlp_load", "knn_mlp_features", "knn_mlp_loss_grad", "knn_mlp_train", "knn_mlp_predict"):
+            getattr(lib, f).restype = ctypes.c_int
         for f in ("knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_distances", "knn_search_batched"):
             getattr(lib, f).restype = ctypes.c_int
         lib.knn_status_string.argtypes = [ctypes.c_int]
@@ -261,6 +274,70 @@ def knn_search_batched(problems, precision="auto", rerank_extra: int = 32, flags
     statuses = [arr[i].status for i in range(len(problems))]
     _check(lib, status)
     return (statuses, st.as_dict()) if return_stats else statuses
+
+
+def mlp_param_count() -> int:
+    return int(load().knn_mlp_param_count())
+
+
+def mlp_features(Q, S, out=None, stream=None):
+    """Features (M x 257) of the query rows Q against the 256 corpus samples S (device tensors)."""
+    lib = load()
+    Q = _as_f32(Q)
+    S = _as_f32(S)
+    M, d = Q.shape
+    assert S.shape == (MLP_FEATURES - 1, d)
+    o = out if out is not None else _empty_like_out(Q, (M, MLP_FEATURES), "f")
+    opt = make_options(stream=_stream_of(Q, stream))
+    _check(lib, lib.knn_mlp_features(_ptr(Q), M, _ptr(S), d, _ptr(o), ctypes.byref(opt)))
+    return o
+
+
+def mlp_loss_grad(features, targets, params, stream=None):
+    """(loss, gradient of the trained parameters) of the network on (features, targets)."""
+    import torch
+    lib = load()
+    g = torch.empty(MLP_TRAINED, dtype=torch.float32, device=features.device)
+    loss = ctypes.c_double()
+    opt = make_options(stream=_stream_of(features, stream))
+    _check(lib, lib.knn_mlp_loss_grad(_ptr(features), _ptr(targets), features.shape[0], _ptr(params),
+                                      ctypes.byref(loss), _ptr(g), ctypes.byref(opt)))
+    return loss.value, g
+
+
+def mlp_train(features, targets, params, epochs: int = 40, batch: int = 1024, lr: float = 1e-3,
+              holdout: float = 0.1, margin_quantile: float = 0.99, stream=None):
+    """Trains params in place on the GPU; returns the per-epoch mean training loss."""
+    lib = load()
+    hist = (ctypes.c_float * epochs)()
+    opt = make_options(stream=_stream_of(features, stream))
+    _check(lib, lib.knn_mlp_train(_ptr(features), _ptr(targets), features.shape[0], _ptr(params), epochs, batch,
+                                  lr, holdout, margin_quantile, hist, ctypes.byref(opt)))
+    return list(hist)
+
+
+def mlp_predict(features, params, stream=None):
+    """(predicted log k-th squared distance, squared-distance threshold) per row."""
+    import torch
+    lib = load()
+    n = features.shape[0]
+    y = torch.empty(n, dtype=torch.float32, device=features.device)
+    t = torch.empty(n, dtype=torch.float32, device=features.device)
+    opt = make_options(stream=_stream_of(features, stream))
+    _check(lib, lib.knn_mlp_predict(_ptr(features), n, _ptr(params), _ptr(y), _ptr(t), ctypes.byref(opt)))
+    return y, t
+
+
+def mlp_save(path: str, params) -> None:
+    """Writes the parameter array (host numpy or device tensor) to a parameter file."""
+    lib = load()
+    _check(lib, lib.knn_mlp_save(str(path).encode(), _ptr(params)))
+
+
+def mlp_load(path: str, params) -> None:
+    """Reads a parameter file into params (host numpy float32 or device tensor)."""
+    lib = load()
+    _check(lib, lib.knn_mlp_load(str(path).encode(), _ptr(params)))
 
 
 def version() -> str:

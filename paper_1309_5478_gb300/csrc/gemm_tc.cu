@@ -684,7 +684,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                     const int c = rs.cnt[r];
                     uint32_t fl = rs.trunc[r] ? ROW_TRUNCATED : 0u;
-                    if (tthr != KEY_MAX && (c < p.k || band > tthr)) fl |= ROW_THRESHOLD_MISS | ROW_TRUNCATED;
+                    // a supplied threshold drops every key above it: the list is truncated
+                    // there and the re-rank certificate decides whether it held the answer;
+                    // fewer than k survivors is a miss outright
+                    (void)band;
+                    if (tthr != KEY_MAX) fl |= ROW_TRUNCATED | (c < p.k ? ROW_THRESHOLD_MISS : 0u);
                     p.count[g] = c;
                     p.bound[g] = rs.tau[r];
                     p.flags[g] = fl;

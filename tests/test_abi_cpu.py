@@ -70,3 +70,27 @@ def test_argument_checks_need_no_device(lib):
 def test_library_is_built_for_sm_103a():
     from paper_1309_5478_gb300 import build
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.NVCC_FLAGS)
+
+
+def test_mlp_parameter_file_round_trip_on_host(lib, tmp_path):
+    from paper_1309_5478_gb300 import binding
+    n = lib.knn_mlp_param_count()
+    assert n == binding.MLP_TRAINED + 2 * binding.MLP_FEATURES + 1
+    p = (np.arange(n, dtype=np.float32) * 0.001 - 3.0).astype(np.float32)
+    path = tmp_path / "net.bin"
+    binding.mlp_save(path, p)
+    assert path.stat().st_size == 8 + 12 + 4 * n
+    q = np.zeros(n, dtype=np.float32)
+    binding.mlp_load(path, q)
+    assert np.array_equal(p, q)
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(path.read_bytes()[:100])
+    with pytest.raises(binding.KnnError):
+        binding.mlp_load(bad, q)
+    raw = bytearray(path.read_bytes())
+    raw[12:16] = (64).to_bytes(4, "little")  # another hidden width
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(binding.KnnError):
+        binding.mlp_load(bad, q)
+    with pytest.raises(binding.KnnError):
+        binding.mlp_load(tmp_path / "missing.bin", q)
