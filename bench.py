@@ -51,9 +51,13 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--mode", choices=["knng", "select", "batch"], default="knng",
+    ap.add_argument("--mode", choices=["knng", "select", "batch", "mlp"], default="knng",
                     help="select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
-                         "batch: 512 independent search problems of uneven shape in one graph")
+                         "batch: 512 independent search problems of uneven shape in one graph; "
+                         "mlp: k-NN graph of a 524288 x 768 anisotropic mixture, k=100, with learned per-row "
+                         "thresholds against the same graph without them")
+    ap.add_argument("--train-rows", type=int, default=50000, help="mlp mode: training rows")
+    ap.add_argument("--epochs", type=int, default=40, help="mlp mode: training epochs")
     ap.add_argument("--problems", type=int, default=512, help="batch mode: number of problems")
     ap.add_argument("--q", type=int, default=16384, help="select mode: rows")
     ap.add_argument("--cols", type=int, default=65536, help="select mode: row length n")
@@ -125,6 +129,118 @@ def run_batch(args):
         nrows += Qh.shape[0]
     line["cpu_baseline"] = {"value": nrows / t_cpu, "unit": "rows/s", "cores": oracle.threads(), "kind": "oracle",
                             "sample": f"8 query rows of each of {len(shapes[::max(1, len(shapes)//8)])} problems"}
+    print(json.dumps(line), flush=True)
+
+
+def run_mlp(args):
+    """k-NN graph with learned per-row thresholds: N=524288 points of a 256-component anisotropic
+    Gaussian mixture in d=768 (diagonal scales log-uniform in [0.1, 2]), k=100, fused BF16 form.
+    The network is trained on 50000 seeded rows whose targets (log k-th squared distance without
+    the row itself) come from the engine; a step is features + prediction + knng_build with the
+    proposed thresholds, against knng_build alone on the same data."""
+    import torch
+    from paper_1309_5478_gb300 import binding as kb
+    from paper_1309_5478_gb300 import inputs
+    n = args.n if args.n != N_DEFAULT else 524288
+    d = args.d if args.d != D_DEFAULT else 768
+    k = args.k if args.k != K_DEFAULT else 100
+    X = inputs.anisotropic_mixture(n=n, d=d)
+    Xd = torch.from_numpy(X).cuda()
+    P = peaks()
+    F = kb.MLP_FEATURES
+    # training
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = Xd[torch.from_numpy(inputs.sample_rows(n, F - 1, seed=501)).cuda()].contiguous()
+    rows = torch.from_numpy(inputs.sample_rows(n, args.train_rows, seed=502)).cuda()
+    _, dt = kb.knn_search(Xd[rows].contiguous(), Xd, k + 1, precision="bf16")
+    targets = torch.log(dt[:, k].contiguous())
+    feats = kb.mlp_features(Xd, S)
+    torch.cuda.synchronize()
+    t_targets = time.perf_counter() - t0
+    params = torch.zeros(kb.mlp_param_count(), dtype=torch.float32, device="cuda")
+    gen = torch.Generator().manual_seed(503)
+    params[:kb.MLP_TRAINED] = (torch.randn(kb.MLP_TRAINED, generator=gen) * 0.02).cuda()
+    # training rows in a seeded shuffled order (the hold-out is the tail)
+    perm = torch.from_numpy(inputs.permutation(504, 0, args.train_rows)).cuda()
+    t1 = time.perf_counter()
+    hist = kb.mlp_train(feats[rows[perm]].contiguous(), targets[perm].contiguous(), params,
+                        epochs=args.epochs, batch=1024, lr=1e-3, holdout=0.1, margin_quantile=0.99)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+
+    oi = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    od = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    oi2 = torch.empty_like(oi)
+    od2 = torch.empty_like(od)
+    fbuf = torch.empty((n, F), dtype=torch.float32, device="cuda")
+    thr = torch.empty(n, dtype=torch.float32, device="cuda")
+
+    def with_mlp():
+        kb.mlp_features(Xd, S, out=fbuf)
+        _, t = kb.mlp_predict(fbuf, params)
+        thr.copy_(t)
+        return kb.knng_build(Xd, k, out_idx=oi, out_dist=od, precision="bf16", fused=1, row_threshold=thr,
+                             flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True)[2]
+
+    def without_mlp():
+        return kb.knng_build(Xd, k, out_idx=oi2, out_dist=od2, precision="bf16", fused=1,
+                             flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True)[2]
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        st = [fn() for _ in range(args.steps)]
+        ev1.record()
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / args.steps, st
+
+    clocks = ClockSampler(0)
+    clocks.start()
+    ms_with, st_with = timed(with_mlp)
+    ms_without, st_without = timed(without_mlp)
+    clk = clocks.stop()
+    identical = bool(torch.equal(oi, oi2) and torch.equal(od, od2))
+    s1, s0 = st_with[-1], st_without[-1]
+    dk = od2[:, k - 1].double()
+    lr = torch.log(thr.double() / dk)
+    flops = float(s1["gemm_flops"])
+    ach = flops / (float(np.mean([s["ms_gemm"] for s in st_with])) / 1e3) / 1e12
+    line = {"metric": "exact k-NNG rows/s with learned per-row thresholds, N=524288 d=768 k=100",
+            "value": n / (ms_with / 1e3), "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_with, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": f"k-NN graph, N={n} points of a 256-component anisotropic Gaussian mixture in "
+                                   f"d={d} (diagonal scales log-uniform in [0.1,2]), k={k}, learned thresholds "
+                                   f"from a 257-128-1 network trained on {args.train_rows} rows",
+                       "N": n, "d": d, "k": k, "train_rows": args.train_rows, "epochs": args.epochs,
+                       "l2": "input 1.6 GB > L2: no flush needed"},
+            "without_mlp": {"rows_per_s": n / (ms_without / 1e3), "ms_per_step": ms_without,
+                            "candidates_per_row": s0["candidates"] / n, "ms_select": s0["ms_select"],
+                            "ms_rerank": s0["ms_rerank"]},
+            "with_mlp": {"candidates_per_row": s1["candidates"] / n, "ms_select": s1["ms_select"],
+                         "ms_rerank": s1["ms_rerank"], "ms_fallback": s1["ms_fallback"],
+                         "threshold_misses": int(s1["threshold_misses"]),
+                         "rows_uncertified": int(s1["rows_uncertified"]), "rows_fallback": int(s1["rows_fallback"])},
+            "speedup_vs_without": ms_without / ms_with,
+            "identical_to_without": identical,
+            "pass_rate": 1.0 - (s1["rows_uncertified"] + s1["threshold_misses"]) / n,
+            "proposal_log_ratio": {"median": float(lr.median()), "p01": float(torch.quantile(lr.float(), 0.01)),
+                                   "frac_at_or_above_kth": float((lr >= 0).double().mean())},
+            "training": {"targets_and_features_s": t_targets, "train_s": t_train, "loss_first": hist[0],
+                         "loss_last": hist[-1], "margin": float(params[-1])},
+            "roofline": {"bound": "tensor", "achieved": ach, "peak": P["bf16_sustained"], "unit": "TFLOP/s",
+                         "frac": ach / P["bf16_sustained"], "traffic": None, "kernel": "knn_fused_gemm_select",
+                         "peak_source": f"{P['source']} bf16 sustained"},
+            "clocks": clk,
+            # engine launches of the graph builds, plus the feature (2 norm + 2 per 65536-row slab) and
+            # prediction (2) kernels of every step
+            "gpu_launches": int(sum(s["kernel_launches"] for s in st_with)) + args.steps * (4 + 2 * -(-n // 65536))}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample_rate(X, k, args.cpu_seconds, seed=505)
     print(json.dumps(line), flush=True)
 
 
@@ -320,10 +436,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.mode in ("select", "batch"):
+    if args.mode in ("select", "batch", "mlp"):
         import torch
         torch.cuda.set_device(local)
-        (run_select_only if args.mode == "select" else run_batch)(args)
+        {"select": run_select_only, "batch": run_batch, "mlp": run_mlp}[args.mode](args)
         return
 
     import torch

@@ -81,7 +81,7 @@ typedef struct knn_stats {
     int32_t precision_used;    /* knn_precision actually run */
     int32_t fused_used;        /* 1 when the select ran inside the GEMM epilogue */
     int32_t exact_arithmetic;  /* 1 when the inputs made the GEMM exact (integer-valued, small) */
-    int32_t reserved;
+    int32_t list_capacity;     /* candidate-list capacity per row of the first pass (largest in a batch) */
 } knn_stats;
 
 typedef struct knn_options {

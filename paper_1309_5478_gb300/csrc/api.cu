@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -210,7 +211,7 @@ int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* 
         rp.row_status = row_status + r0;
         rp.counters = counters;
         KNN_CK(launch_rerank(rp, st));
-        tm.launches += 3;
+        tm.launches += 2 + rerank_launches(B.cap);
         tm.gemm_launches += 1;
     }
     return KNN_OK;
@@ -232,6 +233,8 @@ struct CommonLayout {
     int32_t* fb_oi = nullptr;
     float* fb_od = nullptr;
     uint32_t* fb_status = nullptr;
+    void* fb_xq = nullptr;       // gathered reduced-precision rows (second fused pass)
+    float* fb_qscale = nullptr;  // and their FP8 scales
     PlainBuffers fb_plain{};
     double* fp64_scratch = nullptr;
     int64_t n_pad = 0;
@@ -281,6 +284,10 @@ void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena&
         L.fb_oi = ar.take<int32_t>(static_cast<size_t>(L.fb_rows_max) * pb.k);
         L.fb_od = ar.take<float>(static_cast<size_t>(L.fb_rows_max) * pb.k);
         L.fb_status = ar.take<uint32_t>(L.fb_rows_max);
+        if (prec != P_FP32) {
+            L.fb_xq = ar.take<char>(static_cast<size_t>(L.fb_rows_max) * ps.d_pad * (prec == P_BF16 ? 2 : 1));
+            if (prec == P_FP8) L.fb_qscale = ar.take<float>(L.fb_rows_max);
+        }
         layout_plain_buffers(pb, L.fb_rows_max, ar, L.fb_plain);
     }
 }
@@ -463,6 +470,120 @@ int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     KNN_TRY(ev.rec(4, st));
     KNN_CK(cudaStreamSynchronize(st));
     fill_stats(stats, pb, hc, fallback, KNN_FP32, 0, tm, ev.ev);
+    if (stats) stats->list_capacity = B.cap;
+    return KNN_OK;
+}
+
+// Sampled rows of the band probe and the smallest problem it runs on (M N pairs).
+constexpr int PROBE_ROWS = 64;
+constexpr double PROBE_MIN_PAIRS = 17179869184.0;  // 2^34
+
+struct ProbeBuffers {
+    int32_t* rows = nullptr;   // PROBE_ROWS sampled query rows
+    float* Qs = nullptr;       // their coordinates
+    float* Es = nullptr;       // their reduced-precision bounds
+    float* D = nullptr;        // PROBE_ROWS x N FP32 d'
+    int32_t* oi = nullptr;     // PROBE_ROWS x km
+    float* ov = nullptr;
+    uint32_t* fl = nullptr;
+    int32_t* cnt = nullptr;
+};
+
+// List capacity of the fused form from the band of a few sampled rows: the 90th
+// percentile band plus a quarter, plus room for one half-tile of insertions from both
+// warps of a row (128) and slack (32), but never below the default for k + m.
+int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffers& pr, cudaStream_t st,
+              Timing& tm, int* cap_out) {
+    std::vector<int32_t> rows(PROBE_ROWS);
+    for (int i = 0; i < PROBE_ROWS; ++i) rows[i] = static_cast<int32_t>((pb.M * (2 * i + 1)) / (2 * PROBE_ROWS));
+    KNN_CK(cudaMemcpyAsync(pr.rows, rows.data(), PROBE_ROWS * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    KNN_CK(launch_gather_rows(pb.Q, pb.d, pr.rows, PROBE_ROWS, L.ps.E, nullptr, pr.Qs, pr.Es, nullptr, st));
+    KNN_CK(launch_gemm_simt(pr.Qs, PROBE_ROWS, 0, pb.C, pb.N, pb.d, L.ps.cnorm2, nullptr, pr.D, pb.N, 0, st));
+    SelectParams sp{};
+    sp.D = pr.D;
+    sp.ldd = pb.N;
+    sp.M = PROBE_ROWS;
+    sp.N = pb.N;
+    sp.k = km;
+    sp.km = km;
+    sp.cap = km;
+    sp.flags = pr.fl;
+    sp.self_col = pb.graph ? pr.rows : nullptr;
+    KNN_CK(launch_select_topk(sp, pr.oi, pr.ov, st));
+    KNN_CK(launch_band_count(pr.D, PROBE_ROWS, pb.N, pb.N, pr.ov, pb.k, km, pr.Es, sp.self_col, pr.cnt, st));
+    tm.launches += 4;
+    std::vector<int32_t> cnt(PROBE_ROWS);
+    KNN_CK(cudaMemcpyAsync(cnt.data(), pr.cnt, PROBE_ROWS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    std::sort(cnt.begin(), cnt.end());
+    const int band = cnt[(PROBE_ROWS * 9) / 10];
+    int cap = (band + band / 4 + 160 + 31) / 32 * 32;
+    cap = std::max(cap, fused_cap(pb.k, km));
+    *cap_out = std::min(cap, FUSED_CAP_MAX);
+    return KNN_OK;
+}
+
+// Second fused pass over the rows the first could not certify (a band wider than the
+// list, or a threshold that cut into the answer): the widest lists and no threshold,
+// over the gathered rows, in chunks that fit the first pass's candidate buffer. Rows it
+// cannot certify either are returned in `still`.
+int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedParams& first, size_t cand_keys,
+                const std::vector<int32_t>& rows, int sms, cudaStream_t st, Timing& tm, std::vector<int32_t>& still) {
+    const int cap2 = FUSED_CAP_MAX;
+    const int stages2 = fused_stages(cap2, prec);
+    const int64_t chunk = std::min<int64_t>(L.fb_rows_max, static_cast<int64_t>(cand_keys / cap2));
+    if (stages2 == 0 || chunk < 1) {
+        still = rows;
+        return KNN_OK;
+    }
+    const int row_bytes = L.ps.d_pad * (prec == P_BF16 ? 2 : 1);
+    for (size_t r0 = 0; r0 < rows.size(); r0 += static_cast<size_t>(chunk)) {
+        const int32_t n = static_cast<int32_t>(std::min<size_t>(chunk, rows.size() - r0));
+        KNN_CK(cudaMemcpyAsync(L.fb_rows, rows.data() + r0, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        KNN_CK(launch_gather_rows(pb.Q, pb.d, L.fb_rows, n, L.ps.E, nullptr, L.fb_Q, L.fb_E, nullptr, st));
+        KNN_CK(launch_gather_qrows(L.ps.xq, row_bytes, prec == P_FP8 ? L.ps.qscale : nullptr, L.fb_rows, n, L.fb_xq,
+                                   L.fb_qscale, st));
+        FusedParams fp = first;
+        fp.xq = L.fb_xq;
+        fp.M = n;
+        fp.cap = cap2;
+        fp.cap_max = cap2;
+        fp.stages = stages2;
+        fp.E = L.fb_E;
+        fp.thr = nullptr;
+        fp.q_inv_scale = L.fb_qscale;
+        fp.self_offset = -1;
+        fp.self_col = pb.graph ? L.fb_rows : nullptr;
+        fp.n_items = static_cast<int32_t>((n + 127) / 128);
+        KNN_CK(launch_fused(fp, prec, std::min(sms, fp.n_items), st));
+        int hstatus = 0;
+        KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        KNN_CK(cudaStreamSynchronize(st));
+        if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the fused kernel stopped: a device-side wait timed out");
+        RerankParams rp{};
+        rp.Q = L.fb_Q;
+        rp.C = pb.C;
+        rp.M = n;
+        rp.N = pb.N;
+        rp.d = pb.d;
+        rp.k = pb.k;
+        rp.cap = cap2;
+        rp.cand = first.cand;
+        rp.count = first.count;
+        rp.bound = first.bound;
+        rp.flags = first.flags;
+        rp.E = L.fb_E;
+        rp.out_idx = L.fb_oi;
+        rp.out_dist = L.fb_od;
+        rp.row_status = L.fb_status;
+        rp.counters = L.counters;  // the first pass's counts were read before
+        KNN_CK(launch_rerank(rp, st));
+        KNN_CK(launch_scatter_out(L.fb_rows, n, pb.k, L.fb_oi, L.fb_od, pb.out_idx, pb.out_dist, st));
+        tm.launches += 4 + rerank_launches(cap2);
+        std::vector<int32_t> bad;
+        KNN_TRY(rows_with(L.fb_status, n, ROW_UNCERTIFIED, st, bad));
+        for (int32_t b : bad) still.push_back(rows[r0 + static_cast<size_t>(b)]);
+    }
     return KNN_OK;
 }
 
@@ -473,21 +594,39 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     uint64_t* bound = nullptr;
     uint32_t* flags = nullptr;
     const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
-    const int cap = fused_cap(pb.k, km);
-    const int stages = fused_stages(cap, prec);
+    int cap = fused_cap(pb.k, km);
+    // a large problem first measures its band on sampled rows and may take a larger list
+    const bool probe = static_cast<double>(pb.M) * static_cast<double>(pb.N) >= PROBE_MIN_PAIRS &&
+                       pb.M >= 4 * PROBE_ROWS && fused_stages(FUSED_CAP_MAX, prec) > 0;
+    // tuning override: a list capacity between the default for k + m and the maximum
+    int cap_env = 0;
+    if (const char* e = std::getenv("KNN_FUSED_CAP"))
+        cap_env = std::min(FUSED_CAP_MAX, std::max(cap, (std::atoi(e) + 31) / 32 * 32));
+    const int cap_alloc = probe ? FUSED_CAP_MAX : std::max(cap, cap_env);
     int dev = 0, sms = 0;
     KNN_CK(cudaGetDevice(&dev));
     KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int64_t nrb = (pb.M + 127) / 128;
     const int grid = static_cast<int>(std::min<int64_t>(sms, nrb));
     uint64_t* scratch = nullptr;
+    ProbeBuffers pr;
     auto layout = [&](Arena& ar) {
         layout_common(pb, prec, true, ar, L);
-        cand = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap);
+        cand = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap_alloc);
         count = ar.take<int32_t>(pb.M);
         bound = ar.take<uint64_t>(pb.M);
         flags = ar.take<uint32_t>(pb.M);
-        scratch = ar.take<uint64_t>(fused_scratch_words(cap, grid));
+        scratch = ar.take<uint64_t>(fused_scratch_words(FUSED_CAP_MAX, grid));  // also serves the second pass
+        if (probe) {
+            pr.rows = ar.take<int32_t>(PROBE_ROWS);
+            pr.Qs = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * pb.d);
+            pr.Es = ar.take<float>(PROBE_ROWS);
+            pr.D = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * pb.N);
+            pr.oi = ar.take<int32_t>(static_cast<size_t>(PROBE_ROWS) * km);
+            pr.ov = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * km);
+            pr.fl = ar.take<uint32_t>(PROBE_ROWS);
+            pr.cnt = ar.take<int32_t>(PROBE_ROWS);
+        }
     };
     {
         Arena sz;
@@ -506,6 +645,10 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     KNN_TRY(prep_and_check(pb, prec, L, st, stats, tm));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
+    if (probe) KNN_TRY(probe_cap(pb, km, L, pr, st, tm, &cap));
+    if (cap_env > 0) cap = cap_env;
+    const int stages = fused_stages(cap, prec);
+    if (stages == 0) return set_error(KNN_EINTERNAL, "fused list capacity %d does not fit", cap);
     KNN_TRY(ev.rec(1, st));
 
     FusedParams fp{};
@@ -561,7 +704,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     rp.row_status = L.row_status;
     rp.counters = L.counters;
     KNN_CK(launch_rerank(rp, st));
-    ++tm.launches;
+    tm.launches += rerank_launches(cap);
     KNN_TRY(ev.rec(3, st));
     RerankCounters hc{};
     KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -570,14 +713,20 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     if (hc.uncertified > 0 && !(pb.flags & KNN_FLAG_NO_FALLBACK)) {
         std::vector<int32_t> rows;
         KNN_TRY(rows_with(L.row_status, pb.M, ROW_UNCERTIFIED, st, rows));
+        std::vector<int32_t> still;
+        if (cap < FUSED_CAP_MAX || pb.thr)
+            KNN_TRY(fused_retry(pb, prec, L, fp, static_cast<size_t>(pb.M) * cap_alloc, rows, sms, st, tm, still));
+        else
+            still = rows;
         int64_t n64 = 0;
-        KNN_TRY(plain_fallback(pb, L, rows, st, tm, &n64));
+        KNN_TRY(plain_fallback(pb, L, still, st, tm, &n64));
         fallback = static_cast<int64_t>(rows.size());
     }
     KNN_TRY(ev.rec(4, st));
     KNN_CK(cudaStreamSynchronize(st));
     // the fallback's re-rank adds to the counters after they were read: report the first pass
     fill_stats(stats, pb, hc, fallback, prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3, 1, tm, ev.ev);
+    if (stats) stats->list_capacity = cap;
     return KNN_OK;
 }
 

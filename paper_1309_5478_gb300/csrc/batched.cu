@@ -675,6 +675,7 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         stats->ms_total = ms;
         stats->ms_gemm = ms;
         stats->fused_used = static_cast<int32_t>(L.fused_ids.size());
+        stats->list_capacity = L.cap_max;
         stats->precision_used = prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3;
         stats->gemm_launches = 1;
         double flops = 0.0;
@@ -686,7 +687,8 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
             const int64_t ldn = (p.N + 31) / 32 * 32;
             const int64_t R = std::min<int64_t>((p.M + 127) / 128 * 128,
                                                 std::max<int64_t>(128, (int64_t(1) << 30) / (ldn * 4) / 128 * 128));
-            stats->kernel_launches += 3 * ((p.M + R - 1) / R);
+            const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
+            stats->kernel_launches += (2 + rerank_launches(pick_cap(p.k, km))) * ((p.M + R - 1) / R);
         }
     }
     return first;

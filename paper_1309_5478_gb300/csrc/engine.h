@@ -95,6 +95,10 @@ cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool ch
 cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out, cudaStream_t st);
 cudaError_t launch_gather_rows(const float* Q, int32_t d, const int32_t* rows, int32_t n, const float* E,
                                const float* thr, float* Qs, float* Es, float* Ts, cudaStream_t st);
+// Gathers rows of a reduced-precision operand (row_bytes a multiple of 16) and, when
+// qscale is given, their scales.
+cudaError_t launch_gather_qrows(const void* xq, int32_t row_bytes, const float* qscale, const int32_t* rows, int32_t n,
+                                void* out, float* out_scale, cudaStream_t st);
 cudaError_t launch_scatter_out(const int32_t* rows, int32_t n, int32_t k, const int32_t* oi_s, const float* od_s,
                                int32_t* oi, float* od, cudaStream_t st);
 

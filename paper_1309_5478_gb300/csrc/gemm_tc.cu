@@ -223,6 +223,7 @@ struct Item {
     int rb, nk, nct;
     int k, km, cap;
     int64_t self_offset;
+    const int32_t* self_col;
     const float* cnorm2;
     const float* E;
     const float* thr;
@@ -249,6 +250,7 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.km = p.km;
         im.cap = p.cap;
         im.self_offset = p.self_offset;
+        im.self_col = p.self_col;
         im.cnorm2 = p.cnorm2;
         im.E = p.E;
         im.thr = p.thr;
@@ -271,6 +273,7 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.km = q.km;
         im.cap = q.cap;
         im.self_offset = q.self_offset;
+        im.self_col = nullptr;
         im.cnorm2 = q.cnorm2;
         im.E = q.E;
         im.thr = q.thr;
@@ -289,15 +292,15 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
 // multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest values;
 // the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))). When
 // more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
-__device__ __noinline__ void shrink_row(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
-                                        float window, int keep_max, int keep_trunc, uint64_t* band_out) {
+// The keys stay in registers, KPL per lane (cap <= 32 KPL).
+template <int KPL>
+__device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
+                                          float window, int keep_max, int keep_trunc, uint64_t* band_out) {
     const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
     const int n = rs.cnt[r];
     const uint64_t t = rs.tau[r];
     uint64_t* gbuf = p.cand + grow * p.cap;
-    // stage the values in A; keep the keys in registers (cap <= 32 * KEYS_PER_LANE)
-    constexpr int KPL = 16;
     uint64_t key[KPL];
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
@@ -374,6 +377,7 @@ __device__ __noinline__ void shrink_row(const Item& p, const EpiSmem& es, const 
     __syncwarp();
 }
 
+
 // Filters one 32-column chunk of the accumulator into the row's candidate list: every
 // ranking value v = |c_j|^2 - 2 acc is compared with the row's float threshold; the
 // survivors of a lane get consecutive slots of the row's list (one shared-memory atomic
@@ -427,7 +431,7 @@ __device__ __forceinline__ void pair_barrier(int quarter) {
     asm volatile("bar.sync %0, 64;" ::"r"(1 + quarter) : "memory");
 }
 
-template <int P, bool BATCHED>
+template <int P, bool BATCHED, int KPL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fused_gemm_select_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                              const FusedParams params) {
@@ -604,7 +608,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int trunc_mid = p.cap / 2 > p.km ? p.cap / 2 : p.km;
             const int64_t grow = static_cast<int64_t>(rb) * TC_BM + row_in_block;
             const bool valid = grow < p.M;
-            const int64_t self = valid && p.self_offset >= 0 ? grow + p.self_offset : -1;
+            const int64_t self = !valid ? -1
+                                 : p.self_col ? static_cast<int64_t>(p.self_col[grow])
+                                 : (p.self_offset >= 0 ? grow + p.self_offset : -1);
             uint64_t tau_thr = KEY_MAX;
             if (valid && p.thr) {
                 const float t = p.thr[grow];
@@ -659,7 +665,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     while (need) {
                         const int owner = __ffs(need) - 1;
                         need &= need - 1;
-                        shrink_row(p, es, rs, quarter * 32 + owner, static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner,
+                        shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner,
                                    p.E ? 2.f * p.E[static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner] : 0.f,
                                    keep_mid, trunc_mid, nullptr);
                     }
@@ -675,7 +681,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (g >= p.M) continue;
                 uint64_t band = KEY_MAX;
                 if (rs.cnt[r] > 0)
-                    shrink_row(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, &band);
+                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, &band);
                 if (lane == 0) {
                     uint64_t tthr = KEY_MAX;
                     if (p.thr) {
@@ -758,7 +764,7 @@ int fused_cap(int k, int km) {
 }
 
 int fused_stages(int cap, int precision) {
-    if (cap > 512) return 0;  // a list is staged as at most 16 keys per lane
+    if (cap > FUSED_CAP_MAX) return 0;  // a list is staged as at most 32 keys per lane
     for (int st = MAX_STAGES; st >= 2; --st)
         if (tc_smem_bytes(cap, st, precision) <= 232448) return st;
     return 0;
@@ -774,42 +780,40 @@ bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int
            make_map(&prob->tmB, xc, prob->N, prob->k_bytes, TC_BN, elem);
 }
 
+// Kernel instantiation for a precision, a launch form and the list capacity (keys
+// per lane of the register-staged shrink: 16 up to 512 keys, 32 up to 1024).
+template <bool BATCHED>
+void (*fused_kernel(int precision, int cap_max))(const CUtensorMap, const CUtensorMap, const FusedParams) {
+    const bool wide = cap_max > 512;
+    if (precision == P_BF16)
+        return wide ? fused_gemm_select_kernel<P_BF16, BATCHED, 32> : fused_gemm_select_kernel<P_BF16, BATCHED, 16>;
+    return wide ? fused_gemm_select_kernel<P_FP8, BATCHED, 32> : fused_gemm_select_kernel<P_FP8, BATCHED, 16>;
+}
+
 cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st) {
     if (p.n_items <= 0) return cudaSuccess;
+    if (p.cap_max > FUSED_CAP_MAX) return cudaErrorInvalidValue;
     CUtensorMap dummy{};
     const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
-    if (precision == P_BF16) {
-        auto kern = fused_gemm_select_kernel<P_BF16, true>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
-    } else {
-        auto kern = fused_gemm_select_kernel<P_FP8, true>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
-    }
+    auto kern = fused_kernel<true>(precision, p.cap_max);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
+    if (p.cap_max > FUSED_CAP_MAX) return cudaErrorInvalidValue;
     const int elem = precision == P_BF16 ? 2 : 1;
     CUtensorMap ta, tb;
     if (!make_map(&ta, p.xq, p.M, p.k_bytes, TC_BM, elem)) return cudaErrorInvalidValue;
     if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
-    if (precision == P_BF16) {
-        auto kern = fused_gemm_select_kernel<P_BF16, false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
-    } else {
-        auto kern = fused_gemm_select_kernel<P_FP8, false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-        if (e != cudaSuccess) return e;
-        kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
-    }
+    auto kern = fused_kernel<false>(precision, p.cap_max);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
     return cudaGetLastError();
 }
 

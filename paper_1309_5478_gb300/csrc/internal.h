@@ -92,8 +92,19 @@ struct RerankParams {
     float* out_dist;       // M x k
     uint32_t* row_status;  // M
     RerankCounters* counters;
+    int32_t count_min, count_max;  // rows whose list length lies outside are skipped (set by launch_rerank)
 };
+// Lists longer than 512 keys are re-ranked by a second launch with larger per-warp
+// buffers, so the common short lists keep the higher occupancy.
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st);
+inline int rerank_launches(int cap) { return cap > 512 ? 2 : 1; }
+
+// ---- band probe (probe.cu) ----
+// out_count[i] = #{ j != self_col[i] : D[i][j] <= max(vals[i][km-1], vals[i][k-1] + 2 E[i]) },
+// vals[i] holding row i's km smallest values in ascending order.
+cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
+                              int32_t km, const float* E, const int32_t* self_col, int32_t* out_count,
+                              cudaStream_t st);
 
 // ---- batched problems (batched.cu, with batched kernels in prep.cu / rerank.cu) ----
 // Device-side description of one problem of a batch and of its buffers.

@@ -239,6 +239,18 @@ __global__ void gather_rows_kernel(const float* __restrict__ Q, int32_t d, const
     }
 }
 
+// Rows of a reduced-precision operand (row_bytes a multiple of 16) and their scales.
+__global__ void gather_qrows_kernel(const uint4* __restrict__ xq, int32_t row_vec, const float* __restrict__ qscale,
+                                    const int32_t* __restrict__ rows, int32_t n, uint4* __restrict__ out,
+                                    float* __restrict__ out_scale) {
+    const int32_t i = blockIdx.x;
+    if (i >= n) return;
+    const int64_t r = rows[i];
+    for (int32_t t = threadIdx.x; t < row_vec; t += blockDim.x)
+        out[static_cast<int64_t>(i) * row_vec + t] = xq[r * row_vec + t];
+    if (threadIdx.x == 0 && qscale) out_scale[i] = qscale[r];
+}
+
 __global__ void scatter_out_kernel(const int32_t* __restrict__ rows, int32_t n, int32_t k,
                                    const int32_t* __restrict__ oi_s, const float* __restrict__ od_s,
                                    int32_t* __restrict__ oi, float* __restrict__ od) {
@@ -257,6 +269,15 @@ cudaError_t launch_gather_rows(const float* Q, int32_t d, const int32_t* rows, i
                                const float* thr, float* Qs, float* Es, float* Ts, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     gather_rows_kernel<<<n, 128, 0, st>>>(Q, d, rows, n, E, thr, Qs, Es, Ts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_qrows(const void* xq, int32_t row_bytes, const float* qscale, const int32_t* rows, int32_t n,
+                                void* out, float* out_scale, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (row_bytes % 16 != 0) return cudaErrorInvalidValue;
+    gather_qrows_kernel<<<n, 128, 0, st>>>(static_cast<const uint4*>(xq), row_bytes / 16, qscale, rows, n,
+                                           static_cast<uint4*>(out), out_scale);
     return cudaGetLastError();
 }
 

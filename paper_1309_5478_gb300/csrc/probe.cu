@@ -1,0 +1,48 @@
+// Band probe: how many candidates per row the band rule of the tensor-core form keeps.
+//
+// The fused selection keeps, for every row, the keys below T = max(v_(k+m), v_(k) + 2E)
+// (E the row's bound on the reduced-precision error of d'). When the inputs make that
+// band wide (d' values crowded within 2E of the k-th), a list capacity sized for k + m
+// overflows again and again and ends truncated. This kernel counts the band of a few
+// sampled rows from their FP32 d' values, so the host can size the list before the
+// fused launch.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+namespace {
+
+__global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_t ldd, const float* __restrict__ vals,
+                                  int32_t k, int32_t km, const float* __restrict__ E,
+                                  const int32_t* __restrict__ self_col, int32_t* __restrict__ out_count) {
+    const int64_t i = blockIdx.x;
+    const float* v = vals + i * km;
+    const float T = fmaxf(v[km - 1], v[k - 1] + 2.f * E[i]);
+    const float* row = D + i * ldd;
+    const int64_t self = self_col ? self_col[i] : -1;
+    int c = 0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) c += (row[j] <= T && j != self) ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ int part[32];
+    if ((threadIdx.x & 31u) == 0) part[threadIdx.x / 32] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += part[w];
+        out_count[i] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
+                              int32_t km, const float* E, const int32_t* self_col, int32_t* out_count,
+                              cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    band_count_kernel<<<static_cast<unsigned>(rows), 512, 0, st>>>(D, N, ldd, vals, k, km, E, self_col, out_count);
+    return cudaGetLastError();
+}
+
+}  // namespace knn

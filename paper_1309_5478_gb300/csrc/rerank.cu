@@ -18,6 +18,8 @@
 //     below the smallest value any left-out point can have, bound - E (in d' scale).
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "common.cuh"
 #include "internal.h"
 #include "select_core.cuh"
@@ -156,10 +158,12 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
             const float r0 = sqdist_fp32<VEC>(q, p.C + static_cast<int64_t>(j0) * d, d);
             if (lane == 0) K[c] = make_key(r0, j0);
         }
-        for (int i = count + static_cast<int>(lane); i < P; i += 32) K[i] = KEY_MAX;
-        for (int i = static_cast<int>(lane); i < P; i += 32) D64[i] = -1.0;
+        // sort only the power of two that holds the list (P bounds it)
+        const int Pc = pow2_ceil(count > 32 ? count : 32) < P ? pow2_ceil(count > 32 ? count : 32) : P;
+        for (int i = count + static_cast<int>(lane); i < Pc; i += 32) K[i] = KEY_MAX;
+        for (int i = static_cast<int>(lane); i < Pc; i += 32) D64[i] = -1.0;
         __syncwarp();
-        warp_bitonic_sort_smem(K, P);
+        warp_bitonic_sort_smem(K, Pc);
 
         // 2. near ties around the first k positions, settled in FP64 (skipped when the
         //    inputs make FP32 exact: then equal values are true ties, already ordered by index)
@@ -271,9 +275,12 @@ __global__ void rerank_kernel(RerankParams p, int P) {
     __syncthreads();
     const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
     if (row < p.M) {
-        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
-        double* D64 = reinterpret_cast<double*>(K + P);
-        rerank_row<VEC>(p, row, P, K, D64, blk_cnt, lane);
+        const int c = p.count[row];
+        if (c >= p.count_min && c <= p.count_max) {
+            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
+            double* D64 = reinterpret_cast<double*>(K + P);
+            rerank_row<VEC>(p, row, P, K, D64, blk_cnt, lane);
+        }
     }
     flush_counters(p.counters, blk_cnt);
 }
@@ -348,9 +355,10 @@ cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
-    if (p.M <= 0) return cudaSuccess;
-    const int P = pow2_ceil(p.cap > 32 ? p.cap : 32);
+namespace {
+cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cmax, cudaStream_t st) {
+    p.count_min = cmin;
+    p.count_max = cmax;
     const size_t per_warp = static_cast<size_t>(P) * 16;
     int warps = static_cast<int>((64u * 1024u) / per_warp);
     if (warps > 8) warps = 8;
@@ -364,6 +372,17 @@ cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
     const int64_t blocks = (p.M + warps - 1) / warps;
     kern<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(p, P);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const int P = pow2_ceil(p.cap > 32 ? p.cap : 32);
+    constexpr int P_SHORT = 512;
+    if (P <= P_SHORT) return launch_rerank_range(p, P, INT32_MIN, INT32_MAX, st);
+    cudaError_t e = launch_rerank_range(p, P_SHORT, INT32_MIN, P_SHORT, st);
+    if (e != cudaSuccess) return e;
+    return launch_rerank_range(p, P, P_SHORT + 1, INT32_MAX, st);
 }
 
 }  // namespace knn

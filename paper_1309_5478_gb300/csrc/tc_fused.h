@@ -46,6 +46,7 @@ struct FusedParams {
     const float* q_inv_scale;  // FP8: 1 / per-row scale of the queries
     const float* c_inv_scale;  // FP8: same for the corpus (padded like cnorm2)
     int64_t self_offset;       // >= 0: row i excludes column i + self_offset
+    const int32_t* self_col;   // or row i excludes column self_col[i] (non-batched launch; else nullptr)
     uint64_t* cand;            // M x cap candidate keys (value, column)
     int32_t* count;            // M
     uint64_t* bound;           // M: every key left out is > bound
@@ -58,6 +59,9 @@ struct FusedParams {
     const FusedProblem* problems;  // batched launch: problem descriptors (else nullptr)
     const FusedWork* work;     // batched launch: work list, largest items first
 };
+
+// Largest candidate-list capacity of the fused form (32 keys per lane of a warp).
+constexpr int FUSED_CAP_MAX = 1024;
 
 bool fused_available();
 int fused_stages(int cap, int precision);  // 0: does not fit

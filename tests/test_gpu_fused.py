@@ -89,3 +89,55 @@ def test_fp8_on_float_data_is_still_exact():
     idx, dist, st = graph(X, 10, "fp8")
     ref_idx, ref_dist = oracle.knng(X, 10, rows=np.arange(100))
     check_float(X, X, np.arange(100), idx[:100], dist[:100], ref_idx, ref_dist, exclude_self=True)
+
+
+@pytest.fixture
+def fused_cap_override(monkeypatch):
+    def set_cap(cap):
+        monkeypatch.setenv("KNN_FUSED_CAP", str(cap))
+    return set_cap
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_wide_lists_integer_bit_exact(precision, fused_cap_override):
+    # lists of up to 1024 keys (32 per lane in the shrink), more stages traded for list room
+    fused_cap_override(1024)
+    X = inputs.integer_lattice(n=5000, d=130, lo=-6, hi=6, seed=61)
+    idx, dist, st = graph(X, 40, precision)
+    assert st["list_capacity"] == 1024 and st["fused_used"] == 1
+    check_exact(idx, dist, *oracle.knng(X, 40))
+
+
+def test_wide_lists_float(fused_cap_override):
+    fused_cap_override(640)
+    X = inputs.anisotropic_mixture(n=9000, d=200, components=12, seed=62)
+    idx, dist, st = graph(X, 100)
+    assert st["list_capacity"] == 640
+    rows = inputs.sample_rows(len(X), 150, seed=63)
+    ref_idx, ref_dist = oracle.knng(X, 100, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_band_probe_on_a_large_graph():
+    # 2^34 pairs: the band of sampled rows sizes the lists before the fused launch
+    X = inputs.anisotropic_mixture(n=131072, d=256, components=256, seed=64)
+    idx, dist, st = graph(X, 100)
+    assert 448 <= st["list_capacity"] <= 1024
+    assert st["rows_fallback"] <= 0.02 * len(X), st
+    rows = inputs.sample_rows(len(X), 64, seed=65)
+    ref_idx, ref_dist = oracle.knng(X, 100, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_crowded_band_goes_through_every_fallback():
+    # points close together far from the origin: the reduced-precision error bound dwarfs
+    # the distances, every band holds the whole set, the lists overflow even at the widest
+    # capacity and the rows end in the plain FP32 form (or FP64) -- still exact
+    rng = np.random.default_rng(66)
+    base = rng.standard_normal(64).astype(np.float32) * 30
+    X = (base + 0.05 * rng.standard_normal((3000, 64))).astype(np.float32)
+    idx, dist, st = graph(X, 10)
+    assert st["rows_fallback"] == len(X)
+    rows = inputs.sample_rows(len(X), 100, seed=67)
+    ref_idx, ref_dist = oracle.knng(X, 10, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
