@@ -293,9 +293,18 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
 // the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))). When
 // more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
 // The keys stay in registers, KPL per lane (cap <= 32 KPL).
+//
+// With exact == false (shrinks during the sweep) the ranks are not computed: a value of
+// a 32-key sample of the list, sorted across the lanes, is taken as the threshold when
+// counting over the list shows that at least k + m values lie at or below it and at
+// least k lie at or below it minus the window (so it is >= max(v_km, v_k + window) and
+// the list still holds the band), preferring the smallest such sample value. One count
+// is a compare per key and two warp reductions. If no sample value passes, or the
+// threshold would keep more than keep_max keys, the exact ranks are computed.
 template <int KPL>
 __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
-                                          float window, int keep_max, int keep_trunc, uint64_t* band_out) {
+                                          float window, int keep_max, int keep_trunc, bool exact,
+                                          uint64_t* band_out) {
     const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
     const int n = rs.cnt[r];
@@ -316,7 +325,41 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     const int kk = p.k < n ? p.k : n;
     const int kme = p.km < n ? p.km : n;
     uint64_t band = KEY_MAX;
-    if (n >= p.km) {
+    bool have_band = false;
+    if (!exact && n >= p.km) {
+        // sample of the list's values, sorted across the lanes
+        const uint32_t smp = warp_sort32(es.A[(static_cast<int64_t>(lane) * n) >> 5]);
+        // number of values <= x over the whole list
+        auto count_le = [&](uint32_t x) {
+            int c = 0;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q) c += (q * 32 + lane < n && static_cast<uint32_t>(key[q] >> 32) <= x) ? 1 : 0;
+            return __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(c));
+        };
+        auto passes = [&](uint32_t cand) {
+            if (count_le(cand) < static_cast<uint32_t>(kme)) return false;
+            if (window <= 0.f) return true;
+            return count_le(float_to_ord(ord_to_float(cand) - window)) >= static_cast<uint32_t>(kk);
+        };
+        int s0 = (32 * kme + n - 1) / n;  // the sample position expected to hold about k + m values
+        s0 = s0 > 31 ? 31 : s0;
+        int sel = -1;
+        if (passes(__shfl_sync(0xffffffffu, smp, s0))) {
+            sel = s0;
+            while (sel > 0 && passes(__shfl_sync(0xffffffffu, smp, sel - 1))) --sel;
+        } else {
+            for (int s1 = s0 + 1; s1 < 32; ++s1)
+                if (passes(__shfl_sync(0xffffffffu, smp, s1))) {
+                    sel = s1;
+                    break;
+                }
+        }
+        if (sel >= 0) {
+            band = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, sel)));
+            have_band = true;
+        }
+    }
+    if (!have_band && n >= p.km) {
         uint32_t o_k = 0, o_km = 0;
         (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
                                 o_km);
@@ -330,6 +373,21 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+    if (have_band && keep > keep_max && n >= p.km) {
+        // the sample value keeps too much: the exact ranks before the exact path
+        uint32_t o_k = 0, o_km = 0;
+        (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
+                                o_km);
+        float bv = ord_to_float(o_km);
+        if (window > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + window);
+        band = key_ceiling(bv);
+        nt = band < t ? band : t;
+        keep = 0;
+#pragma unroll
+        for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
+    }
     int nn;
     bool tr = false;
     if (keep <= keep_max) {
@@ -667,7 +725,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         need &= need - 1;
                         shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner,
                                    p.E ? 2.f * p.E[static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner] : 0.f,
-                                   keep_mid, trunc_mid, nullptr);
+                                   keep_mid, trunc_mid, false, nullptr);
                     }
                     pair_barrier(quarter);
                     tau_f = rs.tauf[row_in_block];
@@ -681,7 +739,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (g >= p.M) continue;
                 uint64_t band = KEY_MAX;
                 if (rs.cnt[r] > 0)
-                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, &band);
+                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, true, &band);
                 if (lane == 0) {
                     uint64_t tthr = KEY_MAX;
                     if (p.thr) {
