@@ -554,6 +554,8 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
         fp.q_inv_scale = L.fb_qscale;
         fp.self_offset = -1;
         fp.self_col = pb.graph ? L.fb_rows : nullptr;
+        fp.spec = 0;
+        fp.perm_a = 1;
         fp.n_items = static_cast<int32_t>((n + 127) / 128);
         KNN_CK(launch_fused(fp, prec, std::min(sms, fp.n_items), st));
         int hstatus = 0;
@@ -585,6 +587,33 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
         for (int32_t b : bad) still.push_back(rows[r0 + static_cast<size_t>(b)]);
     }
     return KNN_OK;
+}
+
+// Speculative thresholds pay off when a row block's sweep is long; below this many
+// corpus points the plain running threshold is kept. KNN_SPECULATE=0 turns them off.
+constexpr int64_t SPEC_MIN_N = 16384;
+
+bool speculate(const Problem& pb) {
+    if (const char* e = std::getenv("KNN_SPECULATE")) return std::atoi(e) != 0 && pb.N >= 2 * 256;
+    return pb.N >= SPEC_MIN_N;
+}
+
+// Tile stride of the sweep order ct * a mod n: a odd, coprime to n, near 0.618 n, so that
+// any prefix of the sweep is spread over the whole corpus (speculation assumes the
+// columns seen first are a fair sample of the row's distances).
+int tile_stride(int64_t n) {
+    if (n <= 2) return 1;
+    auto gcd = [](int64_t a, int64_t b) {
+        while (b) {
+            const int64_t t = a % b;
+            a = b;
+            b = t;
+        }
+        return a;
+    };
+    for (int64_t a = static_cast<int64_t>(0.6180339887 * static_cast<double>(n)) | 1; a > 1; a -= 2)
+        if (gcd(a, n) == 1) return static_cast<int>(a);
+    return 1;
 }
 
 int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
@@ -675,6 +704,8 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.stages = stages;
     fp.cap_max = cap;
     fp.n_items = static_cast<int32_t>(nrb);
+    fp.spec = speculate(pb) ? 1 : 0;
+    fp.perm_a = fp.spec ? tile_stride((pb.N + 255) / 256) : 1;
     KNN_TRY(tm.record_gemm(st, true));
     KNN_CK(launch_fused(fp, prec, grid, st));
     KNN_TRY(tm.record_gemm(st, false));
@@ -714,7 +745,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
         std::vector<int32_t> rows;
         KNN_TRY(rows_with(L.row_status, pb.M, ROW_UNCERTIFIED, st, rows));
         std::vector<int32_t> still;
-        if (cap < FUSED_CAP_MAX || pb.thr)
+        if (cap < FUSED_CAP_MAX || pb.thr || fp.spec)
             KNN_TRY(fused_retry(pb, prec, L, fp, static_cast<size_t>(pb.M) * cap_alloc, rows, sms, st, tm, still));
         else
             still = rows;

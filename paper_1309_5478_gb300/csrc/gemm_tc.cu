@@ -179,14 +179,33 @@ struct EpiSmem {
     uint64_t* scratch;  // global: exact 64-bit path (2 cap keys + reference list)
 };
 
-// Shared candidate-list state of the 128 rows of the current row block; both warps of a
-// lane quarter insert into the same lists (slots from a shared-memory atomic).
+// Shared candidate-list state of the 128 rows of the current row block. Both warps of a
+// lane quarter insert into the same list of a row without atomics: the warp of the first
+// column half fills it from the front, the other from the back; a shrink compacts both
+// segments to the front.
 struct RowState {
-    int* cnt;         // [128] list length
+    uint16_t* cnt;    // [128][2] keys at the front and at the back of the list
     uint64_t* tau;    // [128] threshold key: every key left out is > tau
     float* tauf;      // [128] float form of tau for the column filter (tau_filter)
-    uint32_t* trunc;  // [128] 1 when the list was truncated
+    uint32_t* flags;  // [128] RS_TRUNC | RS_SPEC
 };
+constexpr uint32_t RS_TRUNC = 1u;  // the list was truncated
+constexpr uint32_t RS_SPEC = 2u;   // a speculative shrink lowered the threshold
+
+// Speculative thresholds. Having seen a fraction f of the corpus, a mid-sweep shrink aims
+// at ranks max(SPEC_RMIN, SPEC_ALPHA * f * r) instead of r (r = k and k + m): for columns in
+// random order the final list then still holds about SPEC_ALPHA * r keys, while far fewer
+// keys are inserted before the threshold settles. A row whose final band is not inside
+// the threshold it ended with is reported truncated there; the re-rank certificate then
+// decides, and rows it rejects are recomputed without speculation.
+constexpr float SPEC_ALPHA = 3.f;
+constexpr int SPEC_RMIN = 16;
+
+__device__ __forceinline__ int spec_rank(int r, int64_t seen, int64_t N) {
+    const float t = ceilf(SPEC_ALPHA * static_cast<float>(r) * (static_cast<float>(seen) / static_cast<float>(N)));
+    const int s = t > static_cast<float>(SPEC_RMIN) ? static_cast<int>(t) : SPEC_RMIN;
+    return s < r ? s : r;
+}
 
 __host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
     return static_cast<size_t>(cap) * 8 + HIST_WORDS * 4;
@@ -222,6 +241,7 @@ struct Item {
     int64_t M, N;
     int rb, nk, nct;
     int k, km, cap;
+    int spec, perm_a;
     int64_t self_offset;
     const int32_t* self_col;
     const float* cnorm2;
@@ -260,6 +280,8 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.count = p.count;
         im.bound = p.bound;
         im.flags = p.flags;
+        im.spec = p.spec;
+        im.perm_a = p.perm_a > 1 ? p.perm_a : 1;
     } else {
         const FusedWork w = p.work[it];
         const FusedProblem& q = p.problems[w.problem];
@@ -283,38 +305,52 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.count = q.count;
         im.bound = q.bound;
         im.flags = q.flags;
+        im.spec = 0;
+        im.perm_a = 1;
     }
     im.nct = static_cast<int>((im.N + TC_BN - 1) / TC_BN);
     return im;
 }
 
+// Corpus tile swept at step ct of a row block's sweep.
+__device__ __forceinline__ int tile_at(const Item& im, int ct) {
+    return im.perm_a == 1 ? ct : static_cast<int>((static_cast<int64_t>(ct) * im.perm_a) % im.nct);
+}
+
 // Warp-cooperative shrink of the candidate list of row r (of the block): the quick
-// multi-select (sampled, on the 32-bit values) finds the k-th and km-th smallest values;
-// the list keeps the keys <= tau = min(tau, ceiling(max(v_km, v_k + window))). When
+// multi-select (sampled, on the 32-bit values) finds the values of ranks rk and rkm;
+// the list keeps the keys <= tau = min(tau, ceiling(max(v_rkm, v_rk + window))). When
 // more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
-// The keys stay in registers, KPL per lane (cap <= 32 KPL).
+// The list's two segments (front and back) are read into registers, KPL keys per lane
+// (cap <= 32 KPL), and the survivors are compacted to the front.
 //
 // With exact == false (shrinks during the sweep) the ranks are not computed: a value of
 // a 32-key sample of the list, sorted across the lanes, is taken as the threshold when
-// counting over the list shows that at least k + m values lie at or below it and at
-// least k lie at or below it minus the window (so it is >= max(v_km, v_k + window) and
-// the list still holds the band), preferring the smallest such sample value. One count
-// is a compare per key and two warp reductions. If no sample value passes, or the
-// threshold would keep more than keep_max keys, the exact ranks are computed.
+// counting over the list shows that at least rkm values lie at or below it and at
+// least rk lie at or below it minus the window (so it is >= max(v_rkm, v_rk + window) and
+// the list still holds the band of those ranks), preferring the smallest such sample
+// value. One count is a compare per key and two warp reductions. If no sample value
+// passes, or the threshold would keep more than keep_max keys, the exact ranks are
+// computed. Ranks below (k, k + m) make the shrink speculative (RS_SPEC is recorded when
+// it lowers the threshold). With exact == true (the row's final shrink, rk = k and
+// rkm = k + m) a row whose band is not inside the threshold it ended with, after a
+// speculative shrink, is marked truncated at that threshold.
 template <int KPL>
 __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
-                                          float window, int keep_max, int keep_trunc, bool exact,
+                                          float window, int rk, int rkm, int keep_max, int keep_trunc, bool exact,
                                           uint64_t* band_out) {
     const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
-    const int n = rs.cnt[r];
+    const int n0 = rs.cnt[2 * r];
+    const int n = n0 + rs.cnt[2 * r + 1];
     const uint64_t t = rs.tau[r];
     uint64_t* gbuf = p.cand + grow * p.cap;
     uint64_t key[KPL];
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
         const int i = q * 32 + lane;
-        key[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + i) : KEY_MAX;
+        const int pos = i < n0 ? i : p.cap - 1 - (i - n0);
+        key[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + pos) : KEY_MAX;
     }
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
@@ -322,11 +358,11 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
         if (i < n) es.A[i] = static_cast<uint32_t>(key[q] >> 32);
     }
     __syncwarp();
-    const int kk = p.k < n ? p.k : n;
-    const int kme = p.km < n ? p.km : n;
+    const int kk = rk < n ? rk : n;
+    const int kme = rkm < n ? rkm : n;
     uint64_t band = KEY_MAX;
     bool have_band = false;
-    if (!exact && n >= p.km) {
+    if (!exact && n >= rkm) {
         // sample of the list's values, sorted across the lanes
         const uint32_t smp = warp_sort32(es.A[(static_cast<int64_t>(lane) * n) >> 5]);
         // number of values <= x over the whole list
@@ -341,7 +377,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
             if (window <= 0.f) return true;
             return count_le(float_to_ord(ord_to_float(cand) - window)) >= static_cast<uint32_t>(kk);
         };
-        int s0 = (32 * kme + n - 1) / n;  // the sample position expected to hold about k + m values
+        int s0 = (32 * kme + n - 1) / n;  // the sample position expected to hold about rkm values
         s0 = s0 > 31 ? 31 : s0;
         int sel = -1;
         if (passes(__shfl_sync(0xffffffffu, smp, s0))) {
@@ -359,7 +395,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
             have_band = true;
         }
     }
-    if (!have_band && n >= p.km) {
+    if (!have_band && n >= rkm) {
         uint32_t o_k = 0, o_km = 0;
         (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
                                 o_km);
@@ -373,7 +409,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) keep += __shfl_xor_sync(0xffffffffu, keep, o);
-    if (have_band && keep > keep_max && n >= p.km) {
+    if (have_band && keep > keep_max && n >= rkm) {
         // the sample value keeps too much: the exact ranks before the exact path
         uint32_t o_k = 0, o_km = 0;
         (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
@@ -409,7 +445,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
         for (int q = 0; q < KPL; ++q)
             if (q * 32 + lane < n) sA[q * 32 + lane] = key[q];
         __syncwarp();
-        CompactResult res = compact_row(sA, sB, seg_s, seg_e, n, p.k, p.km, window, t, keep_max, keep_trunc);
+        CompactResult res = compact_row(sA, sB, seg_s, seg_e, n, rk, rkm, window, t, keep_max, keep_trunc);
         if (res.ok) {
             for (int i = lane; i < res.n; i += 32) gbuf[i] = sA[i];
             nn = res.n;
@@ -424,26 +460,56 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
             tr = true;
         }
     }
+    const uint32_t fl = rs.flags[r];
+    // the final list of a row whose threshold was lowered by speculation: its band must lie
+    // inside that threshold (with fewer than k + m keys the (k+m)-th is beyond it)
+    if (exact && (fl & RS_SPEC) && (band > t || n < rkm)) tr = true;
+    const bool speculated = !exact && (rk < p.k || rkm < p.km) && nt < t;
     __syncwarp();
     if (lane == 0) {
-        rs.cnt[r] = nn;
+        rs.cnt[2 * r] = static_cast<uint16_t>(nn);
+        rs.cnt[2 * r + 1] = 0;
         rs.tau[r] = nt;
         rs.tauf[r] = tau_filter(nt);
-        if (tr) rs.trunc[r] = 1u;
+        rs.flags[r] = fl | (tr ? RS_TRUNC : 0u) | (speculated ? RS_SPEC : 0u);
     }
     if (band_out) *band_out = band;
     __syncwarp();
 }
 
 
+// Value of r[t] for a lane-dependent t (0..31) by a 5-level select tree (no local memory).
+__device__ __forceinline__ uint32_t select32(const uint32_t (&r)[32], int t) {
+    uint32_t a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (t & 16) ? r[i + 16] : r[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (t & 8) ? a[i + 8] : a[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (t & 4) ? a[i + 4] : a[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) a[i] = (t & 2) ? a[i + 2] : a[i];
+    return (t & 1) ? a[1] : a[0];
+}
+
+// Ranking value of column t of a chunk: v = |c_j|^2 - 2 acc (FP8: acc scaled back first).
+template <int P>
+__device__ __forceinline__ float chunk_value(uint32_t acc_bits, float cn, float cs, float qscale) {
+    float a = __uint_as_float(acc_bits);
+    if constexpr (P == P_FP8) a *= cs * qscale;
+    return fmaf(-2.f, a, cn);
+}
+
 // Filters one 32-column chunk of the accumulator into the row's candidate list: every
-// ranking value v = |c_j|^2 - 2 acc is compared with the row's float threshold; the
-// survivors of a lane get consecutive slots of the row's list (one shared-memory atomic
-// per lane) and are written with predicated stores, without per-column branches.
+// ranking value is compared with the row's float threshold; a lane's survivors (rare once
+// the threshold has settled) are then taken one per round, their value recomputed from
+// the accumulator register picked by a select tree, and appended to the lane's segment of
+// the row's list (slot base + dir * cnt). The warp runs as many rounds as its lane with
+// the most survivors.
 template <int P>
 __device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
-                                             int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int* cnt_slot) {
-    float v[32];
+                                             int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt,
+                                             int base, int dir) {
     uint32_t m8[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -452,34 +518,32 @@ __device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const floa
         float sv[4] = {1.f, 1.f, 1.f, 1.f};
         if constexpr (P == P_FP8) {
             const float4 sc = reinterpret_cast<const float4*>(cs)[q];
-            sv[0] = sc.x * qscale;
-            sv[1] = sc.y * qscale;
-            sv[2] = sc.z * qscale;
-            sv[3] = sc.w * qscale;
+            sv[0] = sc.x;
+            sv[1] = sc.y;
+            sv[2] = sc.z;
+            sv[3] = sc.w;
         }
         uint32_t mq = 0;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int t = q * 4 + e;
-            float a = __uint_as_float(r[t]);
-            if constexpr (P == P_FP8) a *= sv[e];
-            v[t] = fmaf(-2.f, a, cv[e]);
-            mq |= (v[t] <= tau_f) ? (1u << e) : 0u;
+            const float v = chunk_value<P>(r[q * 4 + e], cv[e], sv[e], qscale);
+            mq |= (v <= tau_f) ? (1u << e) : 0u;
         }
         m8[q] = mq << (4 * q);
     }
     uint32_t mask = ((m8[0] | m8[1]) | (m8[2] | m8[3])) | ((m8[4] | m8[5]) | (m8[6] | m8[7]));
     const uint64_t ds = static_cast<uint64_t>(self - j0);
     if (ds < 32u) mask &= ~(1u << ds);
-    if (__reduce_or_sync(0xffffffffu, mask) == 0u) return;
-    if (mask) {
-        const int base = atomicAdd(cnt_slot, __popc(mask));
-        const uint32_t jlo = static_cast<uint32_t>(j0);
-#pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const int pos = base + __popc(mask & ((1u << t) - 1u));
-            const uint64_t key = make_key(v[t], jlo + static_cast<uint32_t>(t));
-            if (mask & (1u << t)) gbuf[pos] = key;
+    const uint32_t rounds = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask)));
+    const uint32_t jlo = static_cast<uint32_t>(j0);
+    for (uint32_t it = 0; it < rounds; ++it) {
+        const int t = (__ffs(mask) - 1) & 31;
+        const bool has = mask != 0u;
+        mask &= mask - 1u;
+        const float v = chunk_value<P>(select32(r, t), cn[t], P == P_FP8 ? cs[t] : 1.f, qscale);
+        if (has) {
+            gbuf[base + dir * cnt] = make_key(v, jlo + static_cast<uint32_t>(t));
+            ++cnt;
         }
     }
 }
@@ -504,9 +568,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char* rs_base = reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P);
     RowState rs;
     rs.tau = reinterpret_cast<uint64_t*>(rs_base);
-    rs.cnt = reinterpret_cast<int*>(rs.tau + 128);
-    rs.tauf = reinterpret_cast<float*>(rs.cnt + 128);
-    rs.trunc = reinterpret_cast<uint32_t*>(rs.tauf + 128);
+    rs.cnt = reinterpret_cast<uint16_t*>(rs.tau + 128);
+    rs.tauf = reinterpret_cast<float*>(rs.cnt + 2 * 128);
+    rs.flags = reinterpret_cast<uint32_t*>(rs.tauf + 128);
     uint64_t* bars = reinterpret_cast<uint64_t*>(rs_base + ROWSTATE_BYTES);
     uint64_t* full = bars;                        // [MAX_STAGES]
     uint64_t* empty = bars + MAX_STAGES;          // [MAX_STAGES]
@@ -561,7 +625,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         unsigned char* a = stage_base + s * STAGE_BYTES;
                         mbar_expect_tx(&full[s], STAGE_BYTES);
                         tma_load_2d(a, im.tmA, &full[s], ks * kx, im.rb * TC_BM);
-                        tma_load_2d(a + A_BYTES, im.tmB, &full[s], ks * kx, ct * TC_BN);
+                        tma_load_2d(a + A_BYTES, im.tmB, &full[s], ks * kx, tile_at(im, ct) * TC_BN);
                         if (++s == nst) {
                             s = 0;
                             ph ^= 1u;
@@ -611,11 +675,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tc_fence_after();
                     // stage this tile's corpus norms (and FP8 scales) for the epilogue
                     mbar_expect_tx(&acc_full[acc], CN_TX);
-                    bulk_copy_g2s(cn_smem + acc * TC_BN, im.cnorm2 + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4,
-                                  &acc_full[acc]);
+                    const int64_t cphys = static_cast<int64_t>(tile_at(im, ct)) * TC_BN;
+                    bulk_copy_g2s(cn_smem + acc * TC_BN, im.cnorm2 + cphys, TC_BN * 4, &acc_full[acc]);
                     if constexpr (P == P_FP8)
-                        bulk_copy_g2s(cn_smem + 2 * TC_BN + acc * TC_BN,
-                                      im.c_inv_scale + static_cast<int64_t>(ct) * TC_BN, TC_BN * 4, &acc_full[acc]);
+                        bulk_copy_g2s(cn_smem + 2 * TC_BN + acc * TC_BN, im.c_inv_scale + cphys, TC_BN * 4,
+                                      &acc_full[acc]);
                     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
                     for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&full[s], ph, abort_flag)) {
@@ -675,16 +739,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 if (t == t && t < F_INF) tau_thr = key_ceiling(t);
             }
             if (half == 0) {
-                rs.cnt[row_in_block] = 0;
+                rs.cnt[2 * row_in_block] = 0;
+                rs.cnt[2 * row_in_block + 1] = 0;
                 rs.tau[row_in_block] = valid ? tau_thr : 0ull;
                 rs.tauf[row_in_block] = valid ? tau_filter(tau_thr) : -F_INF;
-                rs.trunc[row_in_block] = 0u;
+                rs.flags[row_in_block] = 0u;
             }
             pair_barrier(quarter);
             float tau_f = rs.tauf[row_in_block];
             const float qscale = (P == P_FP8 && valid) ? p.q_inv_scale[grow] : 1.f;
             uint64_t* gbuf = valid ? p.cand + grow * p.cap : nullptr;
-            int* cnt_slot = rs.cnt + row_in_block;
+            // this warp's segment of the row's list: front (first column half) or back
+            const int seg_base = half ? p.cap - 1 : 0;
+            const int seg_dir = half ? -1 : 1;
+            int my_cnt = 0;
 
             for (int ct = 0; ct < nct; ++ct, ++tile) {
                 const int acc = tile & 1;
@@ -699,17 +767,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                        static_cast<uint32_t>(acc * TC_BN + c0);
                 const float* cn = cn_smem + acc * TC_BN + c0;
                 const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN + c0;
-                const int64_t jt = static_cast<int64_t>(ct) * TC_BN + c0;
+                const int64_t jt = static_cast<int64_t>(tile_at(p, ct)) * TC_BN + c0;
                 uint32_t ra[32], rb2[32];
 #pragma unroll 1
                 for (int hs = 0; hs < 2; ++hs) {
                     // two chunks of 32 columns, the second load overlapping the first filter
                     tmem_ld32(taddr + hs * 64, ra);
                     tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
-                    filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf, cnt_slot);
+                    filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf, my_cnt,
+                                    seg_base, seg_dir);
                     tmem_ld_wait();
                     filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self, tau_f,
-                                    gbuf, cnt_slot);
+                                    gbuf, my_cnt, seg_base, seg_dir);
                     if (hs == 1) {
                         // accumulator and staged norms of this tile no longer needed by this warp
                         tc_fence_before();
@@ -717,18 +786,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         if (lane == 0) mbar_arrive(&acc_empty[acc]);
                     }
                     // both warps of the quarter have finished this half-tile: shrink full lists
+                    rs.cnt[2 * row_in_block + half] = static_cast<uint16_t>(my_cnt);
                     pair_barrier(quarter);
-                    uint32_t need = __ballot_sync(0xffffffffu, valid && rs.cnt[row_in_block] > trigger);
+                    const int total = rs.cnt[2 * row_in_block] + rs.cnt[2 * row_in_block + 1];
+                    uint32_t need = __ballot_sync(0xffffffffu, valid && total > trigger);
                     need &= partner_bit ? 0xaaaaaaaau : 0x55555555u;
-                    while (need) {
-                        const int owner = __ffs(need) - 1;
-                        need &= need - 1;
-                        shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner,
-                                   p.E ? 2.f * p.E[static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner] : 0.f,
-                                   keep_mid, trunc_mid, false, nullptr);
+                    if (need) {
+                        // target ranks: speculative while only part of the corpus has been seen
+                        const int64_t seen = static_cast<int64_t>(ct) * TC_BN + (hs + 1) * (TC_BN / 2);
+                        const int rk = p.spec ? spec_rank(p.k, seen, p.N) : p.k;
+                        const int rkm = p.spec ? spec_rank(p.km, seen, p.N) : p.km;
+                        while (need) {
+                            const int owner = __ffs(need) - 1;
+                            need &= need - 1;
+                            const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
+                            shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, p.E ? 2.f * p.E[g] : 0.f, rk, rkm,
+                                              keep_mid, trunc_mid, false, nullptr);
+                        }
                     }
                     pair_barrier(quarter);
                     tau_f = rs.tauf[row_in_block];
+                    my_cnt = rs.cnt[2 * row_in_block + half];
                 }
             }
             if (!ok) break;
@@ -738,16 +816,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int64_t g = static_cast<int64_t>(rb) * TC_BM + r;
                 if (g >= p.M) continue;
                 uint64_t band = KEY_MAX;
-                if (rs.cnt[r] > 0)
-                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.cap, p.cap, true, &band);
+                if (rs.cnt[2 * r] + rs.cnt[2 * r + 1] > 0)
+                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.k, p.km, p.cap, p.cap, true, &band);
                 if (lane == 0) {
                     uint64_t tthr = KEY_MAX;
                     if (p.thr) {
                         const float t = p.thr[g];
                         if (t == t && t < F_INF) tthr = key_ceiling(t);
                     }
-                    const int c = rs.cnt[r];
-                    uint32_t fl = rs.trunc[r] ? ROW_TRUNCATED : 0u;
+                    const int c = rs.cnt[2 * r];
+                    uint32_t fl = (rs.flags[r] & RS_TRUNC) ? ROW_TRUNCATED : 0u;
                     // a supplied threshold drops every key above it: the list is truncated
                     // there and the re-rank certificate decides whether it held the answer;
                     // fewer than k survivors is a miss outright

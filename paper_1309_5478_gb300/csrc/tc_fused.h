@@ -56,6 +56,9 @@ struct FusedParams {
     int32_t stages;            // shared-memory pipeline depth (fused_stages)
     int32_t cap_max;           // largest list capacity of the launch (sizes shared memory)
     int32_t n_items;           // work items: row blocks of the problem, or entries of `work`
+    int32_t spec;              // 1: speculative thresholds during the sweep (non-batched launch only)
+    int32_t perm_a;            // corpus tiles are swept in the order ct * perm_a mod (tiles), perm_a coprime
+                               // to the tile count (1 = natural order)
     const FusedProblem* problems;  // batched launch: problem descriptors (else nullptr)
     const FusedWork* work;     // batched launch: work list, largest items first
 };

@@ -141,3 +141,48 @@ def test_crowded_band_goes_through_every_fallback():
     rows = inputs.sample_rows(len(X), 100, seed=67)
     ref_idx, ref_dist = oracle.knng(X, 10, rows=rows)
     check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+@pytest.fixture
+def speculate(monkeypatch):
+    def set_spec(on):
+        monkeypatch.setenv("KNN_SPECULATE", "1" if on else "0")
+    return set_spec
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_speculative_thresholds_integer_bit_exact(precision, speculate):
+    # speculation forced on a small graph: mid-sweep shrinks aim at reduced ranks
+    speculate(True)
+    X = inputs.integer_lattice(n=4096, d=128)
+    idx, dist, st = graph(X, 16, precision)
+    check_exact(idx, dist, *oracle.knng(X, 16))
+
+
+def test_speculation_on_ordered_points_falls_back_exactly(speculate):
+    # points along a curve in index order: a row's neighbours sit in one or two corpus
+    # tiles, so wherever those tiles come early in the sweep a speculative threshold cuts
+    # into the answer; those rows must be caught (truncated, certificate, second pass)
+    speculate(True)
+    n, d = 6144, 64
+    t = np.arange(n, dtype=np.float64) * 0.01
+    rng = np.random.default_rng(71)
+    X = np.zeros((n, d), dtype=np.float64)
+    X[:, 0] = np.cos(t) * 3
+    X[:, 1] = np.sin(t) * 3
+    X[:, 2] = t
+    X += 1e-3 * rng.standard_normal((n, d))
+    X = X.astype(np.float32)
+    idx, dist, st = graph(X, 24)
+    rows = np.concatenate([np.arange(0, n, 97), np.arange(n - 40, n)])
+    ref_idx, ref_dist = oracle.knng(X, 24, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_speculation_does_not_change_answers(speculate):
+    X = inputs.gaussian_mixture(n=20000, d=128, components=32, seed=72)
+    speculate(False)
+    a = graph(X, 32)
+    speculate(True)
+    b = graph(X, 32)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
