@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -487,13 +488,20 @@ struct ProbeBuffers {
     float* ov = nullptr;
     uint32_t* fl = nullptr;
     int32_t* cnt = nullptr;
+    float* edge = nullptr;     // band edges of the sampled rows as squared distances
 };
 
 // List capacity of the fused form from the band of a few sampled rows: the 90th
 // percentile band plus a quarter, plus room for one half-tile of insertions from both
 // warps of a row (128) and slack (32), but never below the default for k + m.
+// With spec_d2 (speculative thresholds on) it also proposes a start threshold for every
+// row: the largest sampled band edge (a squared distance) plus twice its distance from
+// the median edge. For points whose bands are alike this starts every row's sweep near
+// its final threshold; a row whose band lies beyond it is caught at the end of the
+// sweep (truncated, re-rank certificate, second pass). Where the edges spread widely
+// the proposal is loose and costs nothing.
 int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffers& pr, cudaStream_t st,
-              Timing& tm, int* cap_out) {
+              Timing& tm, int* cap_out, float* spec_d2) {
     std::vector<int32_t> rows(PROBE_ROWS);
     for (int i = 0; i < PROBE_ROWS; ++i) rows[i] = static_cast<int32_t>((pb.M * (2 * i + 1)) / (2 * PROBE_ROWS));
     KNN_CK(cudaMemcpyAsync(pr.rows, rows.data(), PROBE_ROWS * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -510,11 +518,20 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
     sp.flags = pr.fl;
     sp.self_col = pb.graph ? pr.rows : nullptr;
     KNN_CK(launch_select_topk(sp, pr.oi, pr.ov, st));
-    KNN_CK(launch_band_count(pr.D, PROBE_ROWS, pb.N, pb.N, pr.ov, pb.k, km, pr.Es, sp.self_col, pr.cnt, st));
+    KNN_CK(launch_band_count(pr.D, PROBE_ROWS, pb.N, pb.N, pr.ov, pb.k, km, pr.Es, sp.self_col, L.ps.qnorm2,
+                             pr.rows, pr.cnt, pr.edge, st));
     tm.launches += 4;
     std::vector<int32_t> cnt(PROBE_ROWS);
+    std::vector<float> edge(PROBE_ROWS);
     KNN_CK(cudaMemcpyAsync(cnt.data(), pr.cnt, PROBE_ROWS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaMemcpyAsync(edge.data(), pr.edge, PROBE_ROWS * sizeof(float), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
+    if (spec_d2) {
+        std::sort(edge.begin(), edge.end());
+        const float med = edge[PROBE_ROWS / 2], mx = edge[PROBE_ROWS - 1];
+        const float t = mx + 2.f * (mx - med) + 1e-6f * std::fabs(mx);
+        *spec_d2 = std::isfinite(t) ? t : __builtin_huge_valf();
+    }
     std::sort(cnt.begin(), cnt.end());
     const int band = cnt[(PROBE_ROWS * 9) / 10];
     int cap = (band + band / 4 + 160 + 31) / 32 * 32;
@@ -556,6 +573,8 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
         fp.self_col = pb.graph ? L.fb_rows : nullptr;
         fp.spec = 0;
         fp.perm_a = 1;
+        fp.qnorm2 = nullptr;
+        fp.spec_d2 = __builtin_huge_valf();
         fp.n_items = static_cast<int32_t>((n + 127) / 128);
         KNN_CK(launch_fused(fp, prec, std::min(sms, fp.n_items), st));
         int hstatus = 0;
@@ -596,6 +615,12 @@ constexpr int64_t SPEC_MIN_N = 16384;
 bool speculate(const Problem& pb) {
     if (const char* e = std::getenv("KNN_SPECULATE")) return std::atoi(e) != 0 && pb.N >= 2 * 256;
     return pb.N >= SPEC_MIN_N;
+}
+
+// The probe's start threshold (part of speculation); KNN_SPEC_START=0 turns it off alone.
+bool spec_start() {
+    const char* e = std::getenv("KNN_SPEC_START");
+    return !e || std::atoi(e) != 0;
 }
 
 // Tile stride of the sweep order ct * a mod n: a odd, coprime to n, near 0.618 n, so that
@@ -655,6 +680,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
             pr.ov = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * km);
             pr.fl = ar.take<uint32_t>(PROBE_ROWS);
             pr.cnt = ar.take<int32_t>(PROBE_ROWS);
+            pr.edge = ar.take<float>(PROBE_ROWS);
         }
     };
     {
@@ -674,7 +700,9 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     KNN_TRY(prep_and_check(pb, prec, L, st, stats, tm));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
-    if (probe) KNN_TRY(probe_cap(pb, km, L, pr, st, tm, &cap));
+    float spec_d2 = __builtin_huge_valf();
+    const bool spec = speculate(pb);
+    if (probe) KNN_TRY(probe_cap(pb, km, L, pr, st, tm, &cap, spec && spec_start() ? &spec_d2 : nullptr));
     if (cap_env > 0) cap = cap_env;
     const int stages = fused_stages(cap, prec);
     if (stages == 0) return set_error(KNN_EINTERNAL, "fused list capacity %d does not fit", cap);
@@ -704,8 +732,10 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.stages = stages;
     fp.cap_max = cap;
     fp.n_items = static_cast<int32_t>(nrb);
-    fp.spec = speculate(pb) ? 1 : 0;
+    fp.spec = spec ? 1 : 0;
     fp.perm_a = fp.spec ? tile_stride((pb.N + 255) / 256) : 1;
+    fp.qnorm2 = L.ps.qnorm2;
+    fp.spec_d2 = spec_d2;
     KNN_TRY(tm.record_gemm(st, true));
     KNN_CK(launch_fused(fp, prec, grid, st));
     KNN_TRY(tm.record_gemm(st, false));

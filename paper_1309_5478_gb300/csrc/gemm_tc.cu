@@ -242,6 +242,8 @@ struct Item {
     int rb, nk, nct;
     int k, km, cap;
     int spec, perm_a;
+    float spec_d2;
+    const float* qnorm2;
     int64_t self_offset;
     const int32_t* self_col;
     const float* cnorm2;
@@ -282,6 +284,8 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.flags = p.flags;
         im.spec = p.spec;
         im.perm_a = p.perm_a > 1 ? p.perm_a : 1;
+        im.spec_d2 = p.qnorm2 ? p.spec_d2 : F_INF;
+        im.qnorm2 = p.qnorm2;
     } else {
         const FusedWork w = p.work[it];
         const FusedProblem& q = p.problems[w.problem];
@@ -307,6 +311,8 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.flags = q.flags;
         im.spec = 0;
         im.perm_a = 1;
+        im.spec_d2 = F_INF;
+        im.qnorm2 = nullptr;
     }
     im.nct = static_cast<int>((im.N + TC_BN - 1) / TC_BN);
     return im;
@@ -477,6 +483,81 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     __syncwarp();
 }
 
+
+// Fast path of a mid-sweep shrink of row r (inline, compact code): the sampled threshold
+// search of shrink_row_k and the ballot compaction. Returns false, with the list and the
+// row state untouched, when no sample value passes or the threshold would keep more than
+// keep_max keys; the caller then runs shrink_row_k.
+template <int KPL>
+__device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es, const RowState& rs, int r,
+                                                int64_t grow, float window, int rk, int rkm, int keep_max) {
+    const int lane = static_cast<int>(lane_id());
+    const int n0 = rs.cnt[2 * r];
+    const int n = n0 + rs.cnt[2 * r + 1];
+    if (n < rkm) return false;
+    const uint64_t t = rs.tau[r];
+    uint64_t* gbuf = p.cand + grow * p.cap;
+    uint64_t key[KPL];
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const int i = q * 32 + lane;
+        const int pos = i < n0 ? i : p.cap - 1 - (i - n0);
+        key[q] = i < n ? __ldcg(reinterpret_cast<const unsigned long long*>(gbuf) + pos) : KEY_MAX;
+    }
+#pragma unroll
+    for (int q = 0; q < KPL; ++q)
+        if (q * 32 + lane < n) es.A[q * 32 + lane] = static_cast<uint32_t>(key[q] >> 32);
+    __syncwarp();
+    const uint32_t smp = warp_sort32(es.A[(lane * n) >> 5]);
+    auto count_le = [&](uint32_t x) {
+        int c = 0;
+#pragma unroll
+        for (int q = 0; q < KPL; ++q) c += static_cast<uint32_t>(key[q] >> 32) <= x ? 1 : 0;  // padding is KEY_MAX
+        return __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(c));
+    };
+    auto passes = [&](uint32_t cand) {
+        if (count_le(cand) < static_cast<uint32_t>(rkm)) return false;
+        return window <= 0.f || count_le(float_to_ord(ord_to_float(cand) - window)) >= static_cast<uint32_t>(rk);
+    };
+    int s0 = (32 * rkm + n - 1) / n;
+    s0 = s0 > 31 ? 31 : s0;
+    int sel = -1;
+    if (passes(__shfl_sync(0xffffffffu, smp, s0))) {
+        sel = s0;
+        while (sel > 0 && passes(__shfl_sync(0xffffffffu, smp, sel - 1))) --sel;
+    } else {
+        for (int s1 = s0 + 1; s1 < 32 && sel < 0; ++s1)
+            if (passes(__shfl_sync(0xffffffffu, smp, s1))) sel = s1;
+    }
+    if (sel < 0) return false;
+    const uint64_t band = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, sel)));
+    const uint64_t nt = band < t ? band : t;
+    int keep = 0;
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
+    keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
+    if (keep > keep_max) return false;
+    const uint32_t lt_mask = lanemask_lt();
+    int nn = 0;
+#pragma unroll
+    for (int q = 0; q < KPL; ++q) {
+        const bool kp = key[q] <= nt;
+        const uint32_t b = __ballot_sync(0xffffffffu, kp);
+        if (kp) gbuf[nn + __popc(b & lt_mask)] = key[q];
+        nn += __popc(b);
+    }
+    const bool speculated = (rk < p.k || rkm < p.km) && nt < t;
+    __syncwarp();
+    if (lane == 0) {
+        rs.cnt[2 * r] = static_cast<uint16_t>(nn);
+        rs.cnt[2 * r + 1] = 0;
+        rs.tau[r] = nt;
+        rs.tauf[r] = tau_filter(nt);
+        if (speculated) rs.flags[r] |= RS_SPEC;
+    }
+    __syncwarp();
+    return true;
+}
 
 // Value of r[t] for a lane-dependent t (0..31) by a 5-level select tree (no local memory).
 __device__ __forceinline__ uint32_t select32(const uint32_t (&r)[32], int t) {
@@ -738,12 +819,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const float t = p.thr[grow];
                 if (t == t && t < F_INF) tau_thr = key_ceiling(t);
             }
+            uint32_t flags0 = 0u;
+            if (valid && p.spec_d2 < F_INF) {
+                // speculative start: a squared distance every row's band is expected to lie below
+                const uint64_t ts = key_ceiling(p.spec_d2 - p.qnorm2[grow]);
+                if (ts < tau_thr) {
+                    tau_thr = ts;
+                    flags0 = RS_SPEC;
+                }
+            }
             if (half == 0) {
                 rs.cnt[2 * row_in_block] = 0;
                 rs.cnt[2 * row_in_block + 1] = 0;
                 rs.tau[row_in_block] = valid ? tau_thr : 0ull;
                 rs.tauf[row_in_block] = valid ? tau_filter(tau_thr) : -F_INF;
-                rs.flags[row_in_block] = 0u;
+                rs.flags[row_in_block] = flags0;
             }
             pair_barrier(quarter);
             float tau_f = rs.tauf[row_in_block];
@@ -753,6 +843,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int seg_base = half ? p.cap - 1 : 0;
             const int seg_dir = half ? -1 : 1;
             int my_cnt = 0;
+            const float my_window = (valid && p.E) ? 2.f * p.E[grow] : 0.f;  // shuffled to the shrinking warp
 
             for (int ct = 0; ct < nct; ++ct, ++tile) {
                 const int acc = tile & 1;
@@ -800,8 +891,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int owner = __ffs(need) - 1;
                             need &= need - 1;
                             const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
-                            shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, p.E ? 2.f * p.E[g] : 0.f, rk, rkm,
-                                              keep_mid, trunc_mid, false, nullptr);
+                            const float w = __shfl_sync(0xffffffffu, my_window, owner);
+                            if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid))
+                                shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid, trunc_mid,
+                                                  false, nullptr);
                         }
                     }
                     pair_barrier(quarter);
@@ -816,8 +909,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int64_t g = static_cast<int64_t>(rb) * TC_BM + r;
                 if (g >= p.M) continue;
                 uint64_t band = KEY_MAX;
+                const float w = __shfl_sync(0xffffffffu, my_window, owner);
                 if (rs.cnt[2 * r] + rs.cnt[2 * r + 1] > 0)
-                    shrink_row_k<KPL>(p, es, rs, r, g, p.E ? 2.f * p.E[g] : 0.f, p.k, p.km, p.cap, p.cap, true, &band);
+                    shrink_row_k<KPL>(p, es, rs, r, g, w, p.k, p.km, p.cap, p.cap, true, &band);
                 if (lane == 0) {
                     uint64_t tthr = KEY_MAX;
                     if (p.thr) {

@@ -5,7 +5,8 @@
 // band wide (d' values crowded within 2E of the k-th), a list capacity sized for k + m
 // overflows again and again and ends truncated. This kernel counts the band of a few
 // sampled rows from their FP32 d' values, so the host can size the list before the
-// fused launch.
+// fused launch. It also reports each sampled row's band edge as a squared distance,
+// T + |q|^2, from which the host derives a speculative start threshold.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -16,7 +17,9 @@ namespace {
 
 __global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_t ldd, const float* __restrict__ vals,
                                   int32_t k, int32_t km, const float* __restrict__ E,
-                                  const int32_t* __restrict__ self_col, int32_t* __restrict__ out_count) {
+                                  const int32_t* __restrict__ self_col, const float* __restrict__ qnorm2,
+                                  const int32_t* __restrict__ rows, int32_t* __restrict__ out_count,
+                                  float* __restrict__ out_edge) {
     const int64_t i = blockIdx.x;
     const float* v = vals + i * km;
     const float T = fmaxf(v[km - 1], v[k - 1] + 2.f * E[i]);
@@ -32,16 +35,18 @@ __global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_
         int s = 0;
         for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += part[w];
         out_count[i] = s;
+        if (out_edge) out_edge[i] = T + qnorm2[rows[i]];
     }
 }
 
 }  // namespace
 
 cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
-                              int32_t km, const float* E, const int32_t* self_col, int32_t* out_count,
-                              cudaStream_t st) {
+                              int32_t km, const float* E, const int32_t* self_col, const float* qnorm2,
+                              const int32_t* row_ids, int32_t* out_count, float* out_edge, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
-    band_count_kernel<<<static_cast<unsigned>(rows), 512, 0, st>>>(D, N, ldd, vals, k, km, E, self_col, out_count);
+    band_count_kernel<<<static_cast<unsigned>(rows), 512, 0, st>>>(D, N, ldd, vals, k, km, E, self_col, qnorm2,
+                                                                   row_ids, out_count, out_edge);
     return cudaGetLastError();
 }
 

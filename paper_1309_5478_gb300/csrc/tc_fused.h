@@ -59,6 +59,8 @@ struct FusedParams {
     int32_t spec;              // 1: speculative thresholds during the sweep (non-batched launch only)
     int32_t perm_a;            // corpus tiles are swept in the order ct * perm_a mod (tiles), perm_a coprime
                                // to the tile count (1 = natural order)
+    const float* qnorm2;       // |q_i|^2 (needed with spec_d2)
+    float spec_d2;             // speculative start threshold in squared distance for every row (+inf: none)
     const FusedProblem* problems;  // batched launch: problem descriptors (else nullptr)
     const FusedWork* work;     // batched launch: work list, largest items first
 };
