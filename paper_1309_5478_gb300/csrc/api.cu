@@ -183,6 +183,7 @@ int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* 
         sp.ldd = B.ldn;
         sp.M = rows;
         sp.N = pb.N;
+        sp.spec = select_spec(sp.N);
         sp.k = pb.k;
         sp.km = B.km;
         sp.cap = B.cap;
@@ -239,6 +240,9 @@ struct CommonLayout {
     PlainBuffers fb_plain{};
     double* fp64_scratch = nullptr;
     int64_t n_pad = 0;
+    // integer inputs small enough that the error bounds can be zero: thresholds may then
+    // be exact keys, whose float filter assumes columns in increasing order
+    bool maybe_exact = false;
 };
 
 void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena& ar, CommonLayout& L) {
@@ -293,7 +297,7 @@ void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena&
     }
 }
 
-int prep_and_check(const Problem& pb, int prec, const CommonLayout& L, cudaStream_t st, knn_stats* stats,
+int prep_and_check(const Problem& pb, int prec, CommonLayout& L, cudaStream_t st, knn_stats* stats,
                    Timing& tm) {
     const PrepState& ps = L.ps;
     const bool same = pb.graph;
@@ -324,12 +328,12 @@ int prep_and_check(const Problem& pb, int prec, const CommonLayout& L, cudaStrea
     if ((pb.flags & KNN_FLAG_CHECK_FINITE) && (hq.nonfinite || hc.nonfinite))
         return set_error(KNN_EINVAL, "input holds NaN or Inf (%u query rows, %u corpus rows)", hq.nonfinite,
                          hc.nonfinite);
-    if (stats) {
+    {
         float amax;
         uint32_t u = std::max(hq.max_abs, hc.max_abs);
         std::memcpy(&amax, &u, 4);
-        stats->exact_arithmetic =
-            (hq.noninteger == 0 && hc.noninteger == 0 && 4.0 * ps.d_pad * double(amax) * amax <= 16777216.0) ? 1 : 0;
+        L.maybe_exact = hq.noninteger == 0 && hc.noninteger == 0 && 4.0 * ps.d_pad * double(amax) * amax <= 16777216.0;
+        if (stats) stats->exact_arithmetic = L.maybe_exact ? 1 : 0;
     }
     return KNN_OK;
 }
@@ -512,6 +516,7 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
     sp.ldd = pb.N;
     sp.M = PROBE_ROWS;
     sp.N = pb.N;
+    sp.spec = select_spec(sp.N);
     sp.k = km;
     sp.km = km;
     sp.cap = km;
@@ -733,7 +738,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.cap_max = cap;
     fp.n_items = static_cast<int32_t>(nrb);
     fp.spec = spec ? 1 : 0;
-    fp.perm_a = fp.spec ? tile_stride((pb.N + 255) / 256) : 1;
+    fp.perm_a = fp.spec && !L.maybe_exact ? tile_stride((pb.N + 255) / 256) : 1;
     fp.qnorm2 = L.ps.qnorm2;
     fp.spec_d2 = spec_d2;
     KNN_TRY(tm.record_gemm(st, true));
@@ -990,6 +995,7 @@ int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int
     sp.ldd = ldd;
     sp.M = M;
     sp.N = N;
+    sp.spec = select_spec(sp.N);
     sp.k = k;
     sp.km = k;
     sp.cap = k;

@@ -463,6 +463,7 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
                 sp.ldd = ldn;
                 sp.M = rows;
                 sp.N = p.N;
+                sp.spec = select_spec(sp.N);
                 sp.k = p.k;
                 sp.km = km;
                 sp.cap = b.cap;

@@ -192,20 +192,6 @@ struct RowState {
 constexpr uint32_t RS_TRUNC = 1u;  // the list was truncated
 constexpr uint32_t RS_SPEC = 2u;   // a speculative shrink lowered the threshold
 
-// Speculative thresholds. Having seen a fraction f of the corpus, a mid-sweep shrink aims
-// at ranks max(SPEC_RMIN, SPEC_ALPHA * f * r) instead of r (r = k and k + m): for columns in
-// random order the final list then still holds about SPEC_ALPHA * r keys, while far fewer
-// keys are inserted before the threshold settles. A row whose final band is not inside
-// the threshold it ended with is reported truncated there; the re-rank certificate then
-// decides, and rows it rejects are recomputed without speculation.
-constexpr float SPEC_ALPHA = 3.f;
-constexpr int SPEC_RMIN = 16;
-
-__device__ __forceinline__ int spec_rank(int r, int64_t seen, int64_t N) {
-    const float t = ceilf(SPEC_ALPHA * static_cast<float>(r) * (static_cast<float>(seen) / static_cast<float>(N)));
-    const int s = t > static_cast<float>(SPEC_RMIN) ? static_cast<int>(t) : SPEC_RMIN;
-    return s < r ? s : r;
-}
 
 __host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
     return static_cast<size_t>(cap) * 8 + HIST_WORDS * 4;
@@ -223,15 +209,6 @@ __host__ __device__ constexpr size_t scratch_words_per_warp(int cap) {
     return 2 * static_cast<size_t>(cap) + SEG_MAX;
 }
 
-// Float threshold for the column filter: v <= tau_filter(tau) exactly when
-// key(v, j) <= tau, for every column j after the ones tau was built from (the filter
-// visits columns in increasing order; a value tied with a non-ceiling threshold key is
-// then above it, so the float just below tau's value is used).
-__device__ __forceinline__ float tau_filter(uint64_t tau) {
-    if ((tau >> 32) == 0xffffffffull) return F_INF;
-    const float v = key_val(tau);
-    return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
-}
 
 // One work item's view of its problem: the row block `rb` of a problem, with the
 // problem's tensor maps, sizes and arrays.

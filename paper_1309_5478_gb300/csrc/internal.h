@@ -71,8 +71,12 @@ struct SelectParams {
     uint64_t* bound;       // M: every key left out of the list is > bound[i]
     uint32_t* flags;       // M: RowFlag bits
     const int32_t* self_col;  // per-row excluded column (or nullptr)
+    int32_t spec;          // 1: speculative thresholds while streaming a row (rows they fail are redone)
 };
 cudaError_t launch_select(const SelectParams& p, cudaStream_t st);
+// Whether rows of length N are selected with speculative thresholds (SelectParams::spec):
+// from 16384 columns on; KNN_SPECULATE=0/1 overrides.
+int select_spec(int64_t N);
 
 // Select output written directly as sorted (index, value) pairs: the k smallest per row.
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st);

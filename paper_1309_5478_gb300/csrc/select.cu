@@ -16,6 +16,8 @@
 // point whose exact distance can still be among the k smallest (the band argument
 // in the design notes). Output per row: the candidate keys, their count, tau
 // (every left-out key is > tau) and flags.
+#include <cstdlib>
+
 #include "internal.h"
 #include "select_core.cuh"
 
@@ -50,56 +52,26 @@ __device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t
     }
 }
 
-// Largest value a key <= tau can carry (+inf for the open threshold).
-__device__ __forceinline__ float tau_value(uint64_t tau) {
-    return (tau >> 32) == 0xffffffffull ? F_INF : key_val(tau);
-}
-
-// Survivor bits (4 per float4 group, SEL_U groups) of one lane: value <= tau_v.
-// NaN (including the padding past the row end) never passes.
-__device__ __forceinline__ uint32_t value_bits(const float (&v)[SEL_U][4], float tau_v) {
+// Survivor bits (4 per float4 group, SEL_U groups) of one lane: value <= thr, where thr
+// is the float form of the running threshold (tau_filter). NaN (including the padding
+// past the row end) never passes.
+__device__ __forceinline__ uint32_t value_bits(const float (&v)[SEL_U][4], float thr) {
     uint32_t m = 0;
 #pragma unroll
     for (int u = 0; u < SEL_U; ++u)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) m |= (v[u][c] <= tau_v) ? (1u << (u * 4 + c)) : 0u;
+        for (int c = 0; c < 4; ++c) m |= (v[u][c] <= thr) ? (1u << (u * 4 + c)) : 0u;
     return m;
 }
 
-// Removes from m the entries whose key is above tau (only entries tied with tau's value
-// can be, and only when tau is an exact key rather than a value ceiling) and the
-// excluded self column.
-__device__ __forceinline__ uint32_t refine_bits(uint32_t m, const float (&v)[SEL_U][4], int64_t base, int64_t self_col,
-                                               float tau_v, uint64_t tau, bool tau_ceil) {
-    const uint32_t lane = lane_id();
+// Clears the bit of the excluded self column.
+__device__ __forceinline__ uint32_t clear_self(uint32_t m, int64_t base, int64_t self_col) {
     if (self_col >= base && self_col < base + 32 * 4 * SEL_U) {
         const int64_t off = self_col - base;
         const int64_t q = off >> 2;
-        if ((q & 31) == lane) m &= ~(1u << ((q >> 5) * 4 + (off & 3)));
-    }
-    if (!tau_ceil && m) {
-#pragma unroll
-        for (int u = 0; u < SEL_U; ++u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint32_t bit = 1u << (u * 4 + c);
-                if ((m & bit) && v[u][c] == tau_v) {
-                    const int64_t j = base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c;
-                    if (make_key(v[u][c], static_cast<uint32_t>(j)) > tau) m &= ~bit;
-                }
-            }
+        if ((q & 31) == lane_id()) m &= ~(1u << ((q >> 5) * 4 + (off & 3)));
     }
     return m;
-}
-
-__device__ __forceinline__ int warp_incl_scan(int x) {
-    const uint32_t lane = lane_id();
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (static_cast<int>(lane) >= o) x += y;
-    }
-    return x;
 }
 
 template <bool VEC>
@@ -109,19 +81,76 @@ __device__ __forceinline__ void load_step(const float* rowp, int64_t N, int64_t 
     for (int u = 0; u < SEL_U; ++u) load_group<VEC>(rowp, N, base + (static_cast<int64_t>(u) * 32 + lane) * 4, v[u]);
 }
 
-// Streams one row, keeping keys <= tau in A (compacting when full). The next step's
-// loads are issued before the current step is filtered. Returns false on a
-// reference-list overflow. n, tau, truncated are updated in place.
+// Fast path of a mid-row shrink of A[0, n) (shared memory): a 32-key sample of the
+// values, sorted across the lanes, proposes thresholds; the smallest sample value with at
+// least rkm values at or below it and at least rk at or below it minus the window is
+// taken (so it is >= max(v_rkm, v_rk + window)), clamped by tau, and the keys above it are
+// compacted away in place with ballot/popc. Returns false, leaving A untouched, when no
+// sample value passes or more than keep_max keys would remain.
+__device__ __forceinline__ bool shrink_fast(uint64_t* A, int& n, uint64_t& tau, int rk, int rkm, float window,
+                                            int keep_max) {
+    const uint32_t lane = lane_id();
+    if (n < rkm) return false;
+    const uint32_t smp = warp_sort32(static_cast<uint32_t>(A[(static_cast<int64_t>(lane) * n) >> 5] >> 32));
+    auto count_le = [&](uint32_t x) {
+        int c = 0;
+        for (int i = static_cast<int>(lane); i < n; i += 32) c += static_cast<uint32_t>(A[i] >> 32) <= x ? 1 : 0;
+        return __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(c));
+    };
+    auto passes = [&](uint32_t cand) {
+        if (count_le(cand) < static_cast<uint32_t>(rkm)) return false;
+        return window <= 0.f || count_le(float_to_ord(ord_to_float(cand) - window)) >= static_cast<uint32_t>(rk);
+    };
+    int s0 = (32 * rkm + n - 1) / n;
+    s0 = s0 > 31 ? 31 : s0;
+    int sel = -1;
+    if (passes(__shfl_sync(0xffffffffu, smp, s0))) {
+        sel = s0;
+        while (sel > 0 && passes(__shfl_sync(0xffffffffu, smp, sel - 1))) --sel;
+    } else {
+        for (int s1 = s0 + 1; s1 < 32 && sel < 0; ++s1)
+            if (passes(__shfl_sync(0xffffffffu, smp, s1))) sel = s1;
+    }
+    if (sel < 0) return false;
+    const uint64_t band = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, sel)));
+    const uint64_t nt = band < tau ? band : tau;
+    int keep = 0;
+    for (int i = static_cast<int>(lane); i < n; i += 32) keep += A[i] <= nt ? 1 : 0;
+    keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
+    if (keep > keep_max) return false;
+    // in place: a lane writes at or below the positions this round has already read
+    const uint32_t lt = lanemask_lt();
+    int nn = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + static_cast<int>(lane);
+        const uint64_t key = i < n ? A[i] : KEY_MAX;
+        const bool kp = key <= nt;
+        const uint32_t b = __ballot_sync(0xffffffffu, kp);
+        if (kp) A[nn + __popc(b & lt)] = key;
+        nn += __popc(b);
+    }
+    __syncwarp();
+    n = nn;
+    tau = nt;
+    return true;
+}
+
+// Streams one row, keeping keys <= tau in A (shrinking it when an insertion would
+// overflow). The next step's loads are issued before the current step is filtered;
+// survivors are inserted one per lane and round at ballot/popc offsets. With spec,
+// shrinks aim at speculative ranks (spec_rank) and spec_used records that one of them
+// lowered the threshold. Returns false on a reference-list overflow. n, tau, truncated
+// are updated in place.
 template <bool VEC, bool CHECK_NAN>
 __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
-                                         int bufk, int k, int km, float window, int& n, uint64_t& tau,
-                                         bool& truncated, bool& nan_seen) {
+                                         int bufk, int k, int km, float window, bool spec, int& n, uint64_t& tau,
+                                         bool& truncated, bool& nan_seen, bool& spec_used) {
     const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
     const int keep_mid = bufk - 160 > km ? bufk - 160 : km;
     const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
     constexpr int STEP = 32 * 4 * SEL_U;
-    float tau_v = tau_value(tau);
-    bool tau_ceil = static_cast<uint32_t>(tau) == 0xffffffffu;
+    float thr = tau_filter(tau);
     float cur[SEL_U][4], nxt[SEL_U][4];
     load_step<VEC>(rowp, N, 0, cur);
     for (int64_t base = 0; base < N; base += STEP) {
@@ -134,38 +163,45 @@ __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t s
                     nan_seen |= (cur[u][c] != cur[u][c]) &&
                                 (base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c < N);
         }
-        uint32_t m = value_bits(cur, tau_v);
+        uint32_t m = clear_self(value_bits(cur, thr), base, self_col);
         if (__any_sync(0xffffffffu, m != 0)) {
-            m = refine_bits(m, cur, base, self_col, tau_v, tau, tau_ceil);
 #pragma unroll
             for (int u = 0; u < SEL_U; ++u) {
                 uint32_t mu = (m >> (u * 4)) & 0xfu;
-                if (!__any_sync(0xffffffffu, mu != 0)) continue;
-                int c = __popc(mu);
-                int incl = warp_incl_scan(c);
-                int total = __shfl_sync(0xffffffffu, incl, 31);
-                if (n + total > bufk) {
-                    __syncwarp();
-                    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, k, km, window, tau, keep_mid,
-                                                  trunc_mid);
-                    if (!r.ok) return false;
-                    n = r.n;
-                    tau = r.tau;
-                    truncated |= r.truncated;
-                    tau_v = tau_value(tau);
-                    tau_ceil = static_cast<uint32_t>(tau) == 0xffffffffu;
-                    m = refine_bits(value_bits(cur, tau_v), cur, base, self_col, tau_v, tau, tau_ceil);
+                uint32_t tot = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mu)));
+                if (tot == 0) continue;
+                if (n + static_cast<int>(tot) > bufk) {
+                    // full: shrink (speculative ranks while only part of the row has been seen)
+                    const int64_t seen = base + static_cast<int64_t>(u) * 128;
+                    const int rk = spec ? spec_rank(k, seen, N) : k;
+                    const int rkm = spec ? spec_rank(km, seen, N) : km;
+                    const uint64_t before = tau;
+                    if (!shrink_fast(rb.A, n, tau, rk, rkm, window, keep_mid)) {
+                        __syncwarp();
+                        CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, rk, rkm, window, tau,
+                                                      keep_mid, trunc_mid);
+                        if (!r.ok) return false;
+                        n = r.n;
+                        tau = r.tau;
+                        truncated |= r.truncated;
+                    }
+                    if ((rk < k || rkm < km) && tau < before) spec_used = true;
+                    thr = tau_filter(tau);
+                    m = clear_self(value_bits(cur, thr), base, self_col);
                     mu = (m >> (u * 4)) & 0xfu;
-                    c = __popc(mu);
-                    incl = warp_incl_scan(c);
-                    total = __shfl_sync(0xffffffffu, incl, 31);
                 }
-                int pos = n + incl - c;
+                // insertion rounds: each lane with survivors left places one per round
+                const uint32_t rounds = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mu)));
                 const int64_t idx4 = base + (static_cast<int64_t>(u) * 32 + lane) * 4;
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (mu & (1u << e)) rb.A[pos++] = make_key(cur[u][e], static_cast<uint32_t>(idx4 + e));
-                n += total;
+                for (uint32_t r = 0; r < rounds; ++r) {
+                    const int e = (__ffs(mu) - 1) & 3;
+                    const bool has = mu != 0u;
+                    mu &= mu - 1u;
+                    const float v = (e & 2) ? ((e & 1) ? cur[u][3] : cur[u][2]) : ((e & 1) ? cur[u][1] : cur[u][0]);
+                    const uint32_t b = __ballot_sync(0xffffffffu, has);
+                    if (has) rb.A[n + __popc(b & lt)] = make_key(v, static_cast<uint32_t>(idx4 + e));
+                    n += __popc(b);
+                }
             }
         }
 #pragma unroll
@@ -204,12 +240,14 @@ __global__ void __launch_bounds__(256, 3) select_rows_kernel(SelectParams p, int
     }
     uint32_t flags = 0;
     bool nan_seen = false;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    bool spec = p.spec != 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
         int n = 0;
         uint64_t tau = tau_thr;
         bool truncated = false;
-        bool ok = scan_row<VEC, CHECK_NAN>(rowp, p.N, self_col, rb, bufk, p.k, p.km, window, n, tau, truncated,
-                                           nan_seen);
+        bool spec_used = false;
+        bool ok = scan_row<VEC, CHECK_NAN>(rowp, p.N, self_col, rb, bufk, p.k, p.km, window, spec, n, tau,
+                                           truncated, nan_seen, spec_used);
         CompactResult r{};
         if (ok && n > 0) {
             r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, p.k, p.km, window, tau, p.cap, p.cap);
@@ -219,6 +257,11 @@ __global__ void __launch_bounds__(256, 3) select_rows_kernel(SelectParams p, int
             r.tau = tau;
             r.band = KEY_MAX;
             r.ok = ok;
+        }
+        if (ok && spec_used && (r.band > tau || n < p.km)) {
+            // a speculative threshold cut into the band: select the row again without it
+            spec = false;
+            continue;
         }
         if (!ok) {
             flags |= ROW_SELECT_ERROR;
@@ -297,6 +340,11 @@ cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool ch
 }
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t st) { return launch_select_ex(p, -1, false, st); }
+
+int select_spec(int64_t N) {
+    if (const char* e = std::getenv("KNN_SPECULATE")) return std::atoi(e) != 0 && N >= 2 * 32 * 4 * SEL_U ? 1 : 0;
+    return N >= 16384 ? 1 : 0;
+}
 
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;

@@ -28,6 +28,32 @@
 
 namespace knn {
 
+// Speculative thresholds (running-threshold selections over a stream of columns).
+// Having seen a fraction f of a row's columns, a mid-stream shrink may aim at ranks
+// max(SPEC_RMIN, SPEC_ALPHA * f * r) instead of r (r = k and k + m): for columns in
+// random order the final list then still holds about SPEC_ALPHA * r keys, while far fewer
+// keys are inserted before the threshold settles. Every caller checks at the end of the
+// row whether the band it needed lies inside the threshold it ended with, and otherwise
+// treats the row as truncated there or selects it again without speculation.
+constexpr float SPEC_ALPHA = 3.f;
+constexpr int SPEC_RMIN = 16;
+
+__device__ __forceinline__ int spec_rank(int r, int64_t seen, int64_t N) {
+    const float t = ceilf(SPEC_ALPHA * static_cast<float>(r) * (static_cast<float>(seen) / static_cast<float>(N)));
+    const int s = t > static_cast<float>(SPEC_RMIN) ? static_cast<int>(t) : SPEC_RMIN;
+    return s < r ? s : r;
+}
+
+// Float threshold for a running-threshold filter: v <= tau_filter(tau) exactly when
+// key(v, j) <= tau, for every column j after the ones tau was built from (columns are
+// visited in increasing order; a value tied with a non-ceiling threshold key is then
+// above it, so the float just below tau's value is used).
+__device__ __forceinline__ float tau_filter(uint64_t tau) {
+    if ((tau >> 32) == 0xffffffffull) return F_INF;
+    const float v = key_val(tau);
+    return static_cast<uint32_t>(tau) == 0xffffffffu ? v : nextafterf(v, -F_INF);
+}
+
 constexpr int SEG_MAX = 128;        // references kept per warp
 constexpr uint32_t SEG_IN_B = 1u << 30;
 constexpr uint32_t SEG_SORTED = 1u << 31;

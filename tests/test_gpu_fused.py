@@ -186,3 +186,14 @@ def test_speculation_does_not_change_answers(speculate):
     speculate(True)
     b = graph(X, 32)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_integer_ties_on_a_long_sweep_bit_exact():
+    # integer points with many equal distances and a sweep long enough for speculation:
+    # exact-arithmetic inputs keep the natural tile order, so thresholds that are exact
+    # keys (zero error window) never drop a tied key of a smaller index
+    X = inputs.integer_lattice(n=20000, d=16, lo=-2, hi=2, seed=73)
+    idx, dist, st = graph(X, 24)
+    rows = inputs.sample_rows(len(X), 120, seed=74)
+    ref_idx, ref_dist = oracle.knng(X, 24, rows=rows)
+    check_exact(idx[rows], dist[rows], ref_idx, ref_dist)

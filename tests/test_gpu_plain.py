@@ -171,3 +171,17 @@ def test_errors_are_statuses():
     D[1, 4] = np.nan
     with pytest.raises(kb.KnnError):
         kb.knn_select(dev(D), 2)
+
+
+@pytest.mark.parametrize("spec", ["0", "1"])
+def test_select_speculation_on_off(spec, monkeypatch):
+    # uniform rows (speculation pays off) and integer rows with heavy ties, with the
+    # speculative shrinks forced on and off: both are exact
+    monkeypatch.setenv("KNN_SPECULATE", spec)
+    for D in (inputs.uniform_matrix(257, 9000, seed=31),
+              inputs.integer_lattice(n=200, d=12000, lo=0, hi=40, seed=32)):
+        idx, val = kb.knn_select(dev(D), 64)
+        idx, val = idx.cpu().numpy(), val.cpu().numpy()
+        for r in range(0, D.shape[0], 7):
+            order = np.lexsort((np.arange(D.shape[1]), D[r]))[:64]
+            assert np.array_equal(idx[r], order) and np.array_equal(val[r], D[r][order])
