@@ -202,6 +202,7 @@ int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* 
         rp.N = pb.N;
         rp.d = pb.d;
         rp.k = pb.k;
+        rp.km = sp.km;
         rp.cap = B.cap;
         rp.cand = B.cand;
         rp.count = B.count;
@@ -541,7 +542,7 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
     const int band = cnt[(PROBE_ROWS * 9) / 10];
     int cap = (band + band / 4 + 160 + 31) / 32 * 32;
     cap = std::max(cap, fused_cap(pb.k, km));
-    *cap_out = std::min(cap, FUSED_CAP_MAX);
+    *cap_out = std::min(cap, FUSED_CAP_WIDE);
     return KNN_OK;
 }
 
@@ -549,9 +550,12 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
 // list, or a threshold that cut into the answer): the widest lists and no threshold,
 // over the gathered rows, in chunks that fit the first pass's candidate buffer. Rows it
 // cannot certify either are returned in `still`.
+// List capacity of the second fused pass after a first pass with capacity cap.
+int retry_cap(int cap) { return std::min(FUSED_CAP_MAX, std::max(FUSED_CAP_WIDE, cap + 256)); }
+
 int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedParams& first, size_t cand_keys,
                 const std::vector<int32_t>& rows, int sms, cudaStream_t st, Timing& tm, std::vector<int32_t>& still) {
-    const int cap2 = FUSED_CAP_MAX;
+    const int cap2 = retry_cap(first.cap);
     const int stages2 = fused_stages(cap2, prec);
     const int64_t chunk = std::min<int64_t>(L.fb_rows_max, static_cast<int64_t>(cand_keys / cap2));
     if (stages2 == 0 || chunk < 1) {
@@ -593,6 +597,7 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
         rp.N = pb.N;
         rp.d = pb.d;
         rp.k = pb.k;
+        rp.km = first.km;
         rp.cap = cap2;
         rp.cand = first.cand;
         rp.count = first.count;
@@ -656,12 +661,12 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     int cap = fused_cap(pb.k, km);
     // a large problem first measures its band on sampled rows and may take a larger list
     const bool probe = static_cast<double>(pb.M) * static_cast<double>(pb.N) >= PROBE_MIN_PAIRS &&
-                       pb.M >= 4 * PROBE_ROWS && fused_stages(FUSED_CAP_MAX, prec) > 0;
+                       pb.M >= 4 * PROBE_ROWS && fused_stages(FUSED_CAP_WIDE, prec) > 0;
     // tuning override: a list capacity between the default for k + m and the maximum
     int cap_env = 0;
     if (const char* e = std::getenv("KNN_FUSED_CAP"))
         cap_env = std::min(FUSED_CAP_MAX, std::max(cap, (std::atoi(e) + 31) / 32 * 32));
-    const int cap_alloc = probe ? FUSED_CAP_MAX : std::max(cap, cap_env);
+    const int cap_alloc = probe ? std::max(FUSED_CAP_WIDE, cap) : std::max(cap, cap_env);
     int dev = 0, sms = 0;
     KNN_CK(cudaGetDevice(&dev));
     KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -759,6 +764,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     rp.N = pb.N;
     rp.d = pb.d;
     rp.k = pb.k;
+    rp.km = km;
     rp.cap = cap;
     rp.cand = cand;
     rp.count = count;
@@ -780,7 +786,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
         std::vector<int32_t> rows;
         KNN_TRY(rows_with(L.row_status, pb.M, ROW_UNCERTIFIED, st, rows));
         std::vector<int32_t> still;
-        if (cap < FUSED_CAP_MAX || pb.thr || fp.spec)
+        if (retry_cap(cap) > cap || pb.thr || fp.spec)
             KNN_TRY(fused_retry(pb, prec, L, fp, static_cast<size_t>(pb.M) * cap_alloc, rows, sms, st, tm, still));
         else
             still = rows;

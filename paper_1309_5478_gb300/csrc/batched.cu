@@ -305,6 +305,7 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
         b.N = p.N;
         b.d = p.d;
         b.k = p.k;
+        b.km = km;
         b.graph = p.graph ? 1 : 0;
         b.vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
                 (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
@@ -480,6 +481,7 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
                 rp.N = p.N;
                 rp.d = p.d;
                 rp.k = p.k;
+                rp.km = km;
                 rp.cap = b.cap;
                 rp.cand = L.slab_cand;
                 rp.count = L.slab_count;
@@ -567,6 +569,7 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         q.count = b.count;
         q.bound = b.bound;
         q.flags = b.flags;
+        q.spec = b.N >= 16384 ? 1 : 0;
         if (!encode_problem_maps(&q, b.xq, b.xc, prec))
             return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
     }
@@ -682,7 +685,8 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         double flops = 0.0;
         for (const Problem& p : probs) flops += 2.0 * double(p.M) * double(p.N) * double(p.d);
         stats->gemm_flops = flops;
-        stats->kernel_launches = (L.fused_ids.empty() ? 0 : 4) + (L.plain_ids.empty() ? 0 : 2);
+        stats->kernel_launches =
+            (L.fused_ids.empty() ? 0 : 3 + rerank_launches(L.cap_max)) + (L.plain_ids.empty() ? 0 : 2);
         for (int i : L.plain_ids) {
             const Problem& p = probs[i];
             const int64_t ldn = (p.N + 31) / 32 * 32;

@@ -6,22 +6,25 @@
 // M x N matrix in global memory between the two; here the selection runs in the
 // GEMM's epilogue, so the matrix never leaves the chip.
 //
-// Structure (one persistent CTA per SM, 6 warps):
+// Structure (one persistent CTA per SM, 10 warps):
 //   warp 0     TMA producer: 128 x 64 query tiles (A) and 256 x 64 corpus tiles (B),
 //              128-byte swizzle, into a 4-stage shared-memory ring (mbarrier full/empty)
 //   warp 1     allocates 512 TMEM columns (two 128 x 256 FP32 accumulators) and issues
 //              tcgen05.mma (BF16 kind::f16, or FP8 e4m3 kind::f8f6f4) from one thread;
 //              tcgen05.commit releases smem stages and publishes finished accumulators
-//   warps 2-5  epilogue: thread t owns query row t of the 128-row block (its TMEM lane);
-//              tcgen05.ld 32 columns at a time, v = |c_j|^2 - 2 acc (FP8: acc scaled back),
-//              keep v when it passes the row's running threshold, appending the key
-//              (v, j) to the row's candidate list in global memory (L2-resident).
-//              When any list of the warp nears its capacity the warp shrinks it with the
-//              quick multi-select (select_core.cuh) in shared memory: the threshold becomes
-//              max(key_(k+m), ceiling(value(key_k) + 2E_i)), so the list always holds every
-//              point whose exact distance can still be among the row's k smallest.
+//   warps 2-9  epilogue: two warps per TMEM lane quarter (32 query rows, one per lane),
+//              each taking half of every tile's columns; tcgen05.ld 32 columns at a time,
+//              v = |c_j|^2 - 2 acc (FP8: acc scaled back), and a key (v, j) that passes the
+//              row's running threshold is appended to the row's candidate list in global
+//              memory (L2-resident): the first warp fills it from the front, the second
+//              from the back. When a list nears its capacity, the quick multi-select
+//              (select_core.cuh) shrinks it and the threshold falls to
+//              max(v_(k+m), v_(k) + 2E_i) (speculatively to lower ranks while only part
+//              of the corpus has been swept), so the list always holds every point whose
+//              exact distance can still be among the row's k smallest.
 // Work: row blocks of 128 queries; each CTA sweeps all corpus tiles of a row block
-// (the candidate state of a row lives in one CTA), then takes the next row block.
+// (the candidate state of a row lives in one CTA), then hands the rows' lists to the
+// re-rank (which reduces them to the band) and takes the next row block.
 // Every mbarrier wait is bounded; on expiry the kernel records KNN_ETIMEOUT in a status
 // word, stops issuing work, waits (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
@@ -168,15 +171,17 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 constexpr int MAX_STAGES = 4;
 
 constexpr int EPI_WARPS = 8;   // two per TMEM lane quarter; each takes half of every tile's columns
+constexpr int RAW_LIST_MAX = 512;  // longest list handed to the re-rank without a trim
 constexpr int HIST_WORDS = 36; // histogram of the sampled select (33 buckets used)
 
-// Per-epilogue-warp shared memory: two 32-bit value arrays (A, B) and a histogram for
-// the quick multi-select of one row's list (the keys stay in the global list).
+// Per-epilogue-warp working arrays for the quick multi-select of one row's list (the keys
+// stay in the global list): the 32-bit values A and a histogram in shared memory; the
+// rarely used auxiliary arrays in global scratch (L2-resident).
 struct EpiSmem {
-    uint32_t* A;
-    uint32_t* B;
-    uint32_t* hist;
-    uint64_t* scratch;  // global: exact 64-bit path (2 cap keys + reference list)
+    uint32_t* A;        // shared: cap values
+    uint32_t* hist;     // shared: HIST_WORDS
+    uint32_t* B;        // global: cap values (sampled two-rank select), then tmp (cap values)
+    uint64_t* scratch;  // global: exact 64-bit path (2 cap keys + reference list); B aliases its front
 };
 
 // Shared candidate-list state of the 128 rows of the current row block. Both warps of a
@@ -194,7 +199,7 @@ constexpr uint32_t RS_SPEC = 2u;   // a speculative shrink lowered the threshold
 
 
 __host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
-    return static_cast<size_t>(cap) * 8 + HIST_WORDS * 4;
+    return static_cast<size_t>(cap) * 4 + HIST_WORDS * 4;
 }
 constexpr size_t ROWSTATE_BYTES = 128 * (4 + 8 + 4 + 4);
 
@@ -286,7 +291,7 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.count = q.count;
         im.bound = q.bound;
         im.flags = q.flags;
-        im.spec = 0;
+        im.spec = q.spec;
         im.perm_a = 1;
         im.spec_d2 = F_INF;
         im.qnorm2 = nullptr;
@@ -300,28 +305,21 @@ __device__ __forceinline__ int tile_at(const Item& im, int ct) {
     return im.perm_a == 1 ? ct : static_cast<int>((static_cast<int64_t>(ct) * im.perm_a) % im.nct);
 }
 
-// Warp-cooperative shrink of the candidate list of row r (of the block): the quick
-// multi-select (sampled, on the 32-bit values) finds the values of ranks rk and rkm;
-// the list keeps the keys <= tau = min(tau, ceiling(max(v_rkm, v_rk + window))). When
-// more than keep_max keys remain, the exact 64-bit path keeps the keep_trunc smallest.
-// The list's two segments (front and back) are read into registers, KPL keys per lane
-// (cap <= 32 KPL), and the survivors are compacted to the front.
-//
-// With exact == false (shrinks during the sweep) the ranks are not computed: a value of
-// a 32-key sample of the list, sorted across the lanes, is taken as the threshold when
-// counting over the list shows that at least rkm values lie at or below it and at
-// least rk lie at or below it minus the window (so it is >= max(v_rkm, v_rk + window) and
-// the list still holds the band of those ranks), preferring the smallest such sample
-// value. One count is a compare per key and two warp reductions. If no sample value
-// passes, or the threshold would keep more than keep_max keys, the exact ranks are
-// computed. Ranks below (k, k + m) make the shrink speculative (RS_SPEC is recorded when
-// it lowers the threshold). With exact == true (the row's final shrink, rk = k and
-// rkm = k + m) a row whose band is not inside the threshold it ended with, after a
-// speculative shrink, is marked truncated at that threshold.
+// Warp-cooperative shrink of the candidate list of row r (of the block) during the
+// sweep, the out-of-line path behind shrink_mid_fast: a value of a 32-key sample of the
+// list, sorted across the lanes, is taken as the threshold when counting over the list
+// shows that at least rkm values lie at or below it and at least rk lie at or below it
+// minus the window (so it is >= max(v_rkm, v_rk + window) and the list still holds the
+// band of those ranks), preferring the smallest such sample value. If no sample value
+// passes, or the threshold would keep more than keep_max keys, the two ranks are found by
+// the sampled two-rank select, and when more than keep_max keys still remain the exact
+// 64-bit quick multi-select keeps the keep_trunc smallest (truncation). The list's two
+// segments (front and back) are read into registers, KPL keys per lane (cap <= 32 KPL), and
+// the survivors are compacted to the front. Ranks below (k, k + m) make the shrink
+// speculative (RS_SPEC is recorded when it lowers the threshold).
 template <int KPL>
 __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, const RowState& rs, int r, int64_t grow,
-                                          float window, int rk, int rkm, int keep_max, int keep_trunc, bool exact,
-                                          uint64_t* band_out) {
+                                          float window, int rk, int rkm, int keep_max, int keep_trunc) {
     const int lane = static_cast<int>(lane_id());
     const uint32_t lt_mask = lanemask_lt();
     const int n0 = rs.cnt[2 * r];
@@ -345,7 +343,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     const int kme = rkm < n ? rkm : n;
     uint64_t band = KEY_MAX;
     bool have_band = false;
-    if (!exact && n >= rkm) {
+    if (n >= rkm) {
         // sample of the list's values, sorted across the lanes
         const uint32_t smp = warp_sort32(es.A[(static_cast<int64_t>(lane) * n) >> 5]);
         // number of values <= x over the whole list
@@ -380,8 +378,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     }
     if (!have_band && n >= rkm) {
         uint32_t o_k = 0, o_km = 0;
-        (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
-                                o_km);
+        (void)two_ranks_sampled(es.A, es.B, es.B + p.cap, es.hist, n, kk - 1, kme - 1, o_k, o_km);
         float bv = ord_to_float(o_km);
         if (window > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + window);
         band = key_ceiling(bv);
@@ -395,8 +392,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
     if (have_band && keep > keep_max && n >= rkm) {
         // the sample value keeps too much: the exact ranks before the exact path
         uint32_t o_k = 0, o_km = 0;
-        (void)two_ranks_sampled(es.A, es.B, reinterpret_cast<uint32_t*>(es.scratch), es.hist, n, kk - 1, kme - 1, o_k,
-                                o_km);
+        (void)two_ranks_sampled(es.A, es.B, es.B + p.cap, es.hist, n, kk - 1, kme - 1, o_k, o_km);
         float bv = ord_to_float(o_km);
         if (window > 0.f) bv = fmaxf(bv, ord_to_float(o_k) + window);
         band = key_ceiling(bv);
@@ -444,10 +440,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
         }
     }
     const uint32_t fl = rs.flags[r];
-    // the final list of a row whose threshold was lowered by speculation: its band must lie
-    // inside that threshold (with fewer than k + m keys the (k+m)-th is beyond it)
-    if (exact && (fl & RS_SPEC) && (band > t || n < rkm)) tr = true;
-    const bool speculated = !exact && (rk < p.k || rkm < p.km) && nt < t;
+    const bool speculated = (rk < p.k || rkm < p.km) && nt < t;
     __syncwarp();
     if (lane == 0) {
         rs.cnt[2 * r] = static_cast<uint16_t>(nn);
@@ -456,7 +449,7 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
         rs.tauf[r] = tau_filter(nt);
         rs.flags[r] = fl | (tr ? RS_TRUNC : 0u) | (speculated ? RS_SPEC : 0u);
     }
-    if (band_out) *band_out = band;
+    (void)band;
     __syncwarp();
 }
 
@@ -773,9 +766,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         EpiSmem es;
         unsigned char* mine = epi_base + static_cast<size_t>(ew) * epi_warp_bytes(p.cap_max);
         es.A = reinterpret_cast<uint32_t*>(mine);
-        es.B = es.A + p.cap_max;
-        es.hist = es.B + p.cap_max;
+        es.hist = es.A + p.cap_max;
         es.scratch = p.scratch + (static_cast<size_t>(blockIdx.x) * EPI_WARPS + ew) * scratch_words_per_warp(p.cap_max);
+        es.B = reinterpret_cast<uint32_t*>(es.scratch);
         int tile = 0;
         bool ok = true;
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
@@ -870,8 +863,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
                             const float w = __shfl_sync(0xffffffffu, my_window, owner);
                             if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid))
-                                shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid, trunc_mid,
-                                                  false, nullptr);
+                                shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid, trunc_mid);
                         }
                     }
                     pair_barrier(quarter);
@@ -880,33 +872,40 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
             if (!ok) break;
-            // final shrink of every row of the quarter, split between the pair by row parity
-            for (int owner = partner_bit; owner < 32; owner += 2) {
-                const int r = quarter * 32 + owner;
-                const int64_t g = static_cast<int64_t>(rb) * TC_BM + r;
-                if (g >= p.M) continue;
-                uint64_t band = KEY_MAX;
-                const float w = __shfl_sync(0xffffffffu, my_window, owner);
-                if (rs.cnt[2 * r] + rs.cnt[2 * r + 1] > 0)
-                    shrink_row_k<KPL>(p, es, rs, r, g, w, p.k, p.km, p.cap, p.cap, true, &band);
-                if (lane == 0) {
-                    uint64_t tthr = KEY_MAX;
-                    if (p.thr) {
-                        const float t = p.thr[g];
-                        if (t == t && t < F_INF) tthr = key_ceiling(t);
-                    }
-                    const int c = rs.cnt[2 * r];
-                    uint32_t fl = (rs.flags[r] & RS_TRUNC) ? ROW_TRUNCATED : 0u;
-                    // a supplied threshold drops every key above it: the list is truncated
-                    // there and the re-rank certificate decides whether it held the answer;
-                    // fewer than k survivors is a miss outright
-                    (void)band;
-                    if (tthr != KEY_MAX) fl |= ROW_TRUNCATED | (c < p.k ? ROW_THRESHOLD_MISS : 0u);
-                    p.count[g] = c;
-                    p.bound[g] = rs.tau[r];
-                    p.flags[g] = fl;
+            // row block done: each row's list (both segments, every key <= its threshold)
+            // goes to the re-rank, which reduces it to the band of the k-th and (k+m)-th.
+            // Lists longer than RAW_LIST_MAX are trimmed here first (to a sampled band
+            // threshold, like a shrink with the ranks k and k + m), so that the re-rank
+            // sorts at most RAW_LIST_MAX keys per row.
+            {
+                const int total = rs.cnt[2 * row_in_block] + rs.cnt[2 * row_in_block + 1];
+                uint32_t need = __ballot_sync(0xffffffffu, valid && total > RAW_LIST_MAX);
+                need &= partner_bit ? 0xaaaaaaaau : 0x55555555u;
+                while (need) {
+                    const int owner = __ffs(need) - 1;
+                    need &= need - 1;
+                    const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
+                    const float w = __shfl_sync(0xffffffffu, my_window, owner);
+                    if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, p.k, p.km, RAW_LIST_MAX))
+                        shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, p.k, p.km, p.cap, p.cap);
                 }
-                __syncwarp();
+                pair_barrier(quarter);
+            }
+            if (half == 0 && valid) {
+                const int c0 = rs.cnt[2 * row_in_block], c1 = rs.cnt[2 * row_in_block + 1];
+                const uint32_t rfl = rs.flags[row_in_block];
+                uint32_t fl = ROW_RAW_LIST | ((rfl & RS_TRUNC) ? ROW_TRUNCATED : 0u) |
+                              ((rfl & RS_SPEC) ? ROW_SPECULATIVE : 0u);
+                // a supplied threshold drops every key above it: the list is truncated there
+                // and the re-rank certificate decides whether it held the answer; fewer than
+                // k survivors is a miss outright
+                if (p.thr) {
+                    const float t = p.thr[grow];
+                    if (t == t && t < F_INF) fl |= ROW_TRUNCATED | (c0 + c1 < p.k ? ROW_THRESHOLD_MISS : 0u);
+                }
+                p.count[grow] = c0 | (c1 << 16);
+                p.bound[grow] = rs.tau[row_in_block];
+                p.flags[grow] = fl;
             }
             // the next row block reinitialises the row state only after both warps are done
             pair_barrier(quarter);
@@ -971,7 +970,7 @@ int fused_cap(int k, int km) {
 }
 
 int fused_stages(int cap, int precision) {
-    if (cap > FUSED_CAP_MAX) return 0;  // a list is staged as at most 32 keys per lane
+    if (cap > FUSED_CAP_MAX) return 0;  // a list is staged as at most 48 keys per lane
     for (int st = MAX_STAGES; st >= 2; --st)
         if (tc_smem_bytes(cap, st, precision) <= 232448) return st;
     return 0;
@@ -988,13 +987,16 @@ bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int
 }
 
 // Kernel instantiation for a precision, a launch form and the list capacity (keys
-// per lane of the register-staged shrink: 16 up to 512 keys, 32 up to 1024).
+// per lane of the register-staged shrink: 16 up to 512 keys, 32 up to 1024, 48 up to 1536).
 template <bool BATCHED>
 void (*fused_kernel(int precision, int cap_max))(const CUtensorMap, const CUtensorMap, const FusedParams) {
-    const bool wide = cap_max > 512;
     if (precision == P_BF16)
-        return wide ? fused_gemm_select_kernel<P_BF16, BATCHED, 32> : fused_gemm_select_kernel<P_BF16, BATCHED, 16>;
-    return wide ? fused_gemm_select_kernel<P_FP8, BATCHED, 32> : fused_gemm_select_kernel<P_FP8, BATCHED, 16>;
+        return cap_max > 1024 ? fused_gemm_select_kernel<P_BF16, BATCHED, 48>
+               : cap_max > 512 ? fused_gemm_select_kernel<P_BF16, BATCHED, 32>
+                               : fused_gemm_select_kernel<P_BF16, BATCHED, 16>;
+    return cap_max > 1024 ? fused_gemm_select_kernel<P_FP8, BATCHED, 48>
+           : cap_max > 512 ? fused_gemm_select_kernel<P_FP8, BATCHED, 32>
+                           : fused_gemm_select_kernel<P_FP8, BATCHED, 16>;
 }
 
 cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st) {

@@ -25,6 +25,9 @@ enum RowFlag : uint32_t {
     ROW_TRUNCATED = 1u,       // candidate list reached capacity; the bound decides exactness
     ROW_THRESHOLD_MISS = 2u,  // a supplied threshold kept fewer than k candidates
     ROW_SELECT_ERROR = 4u,    // the select gave up (iteration limit)
+    ROW_SPECULATIVE = 8u,     // a speculative threshold was used: the band must be checked against the bound
+    ROW_RAW_LIST = 16u,       // the list holds every key <= bound, not yet reduced to the band, in two
+                              // segments: count = front | back << 16, the back filled from cand[cap - 1] down
 };
 
 enum RowStatus : uint32_t {
@@ -86,7 +89,7 @@ struct RerankParams {
     const float* Q;        // M x d queries (rows of this slab)
     const float* C;        // N x d corpus
     int64_t M, N;
-    int32_t d, k, cap;
+    int32_t d, k, km, cap;  // km: keys the band keeps at least (k + m)
     const uint64_t* cand;  // M x cap
     const int32_t* count;
     const uint64_t* bound;
@@ -98,10 +101,10 @@ struct RerankParams {
     RerankCounters* counters;
     int32_t count_min, count_max;  // rows whose list length lies outside are skipped (set by launch_rerank)
 };
-// Lists longer than 512 keys are re-ranked by a second launch with larger per-warp
-// buffers, so the common short lists keep the higher occupancy.
+// Lists longer than 512 (and 1024) keys are re-ranked by further launches with larger
+// per-warp buffers, so the common short lists keep the higher occupancy.
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st);
-inline int rerank_launches(int cap) { return cap > 512 ? 2 : 1; }
+inline int rerank_launches(int cap) { return cap > 1024 ? 3 : (cap > 512 ? 2 : 1); }
 
 // ---- band probe (probe.cu) ----
 // out_count[i] = #{ j != self_col[i] : D[i][j] <= max(vals[i][km-1], vals[i][k-1] + 2 E[i]) },
@@ -117,7 +120,7 @@ struct BatchDev {
     const float* Q;           // M x d queries (== C for a graph)
     const float* C;           // N x d corpus
     int64_t M, N;
-    int32_t d, k, cap, d_pad;
+    int32_t d, k, km, cap, d_pad;
     int32_t graph;            // 1: k-NN graph (self excluded, one prep)
     int32_t vec;              // 1: 16-byte aligned rows (d % 4 == 0)
     PrepGlobals* gq;

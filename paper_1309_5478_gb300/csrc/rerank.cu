@@ -134,17 +134,53 @@ template <bool VEC>
 __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, int P, uint64_t* K, double* D64,
                                            unsigned long long* blk_cnt, uint32_t lane) {
     {
-        const int count = p.count[row];
+        const int raw = p.count[row];
         const uint32_t flags = p.flags[row];
         const float* q = p.Q + row * static_cast<int64_t>(p.d);
         const uint64_t* cand = p.cand + row * static_cast<int64_t>(p.cap);
         const int d = p.d;
 
+        // 0. the row's candidate keys into K. A raw list (every key <= bound, in a front and
+        //    a back segment) is first reduced to the band of its approximate values, as the
+        //    select does: sorted, then the keys <= min(bound, max(key_(k+m), ceiling(v_(k) +
+        //    2E))) kept. A row whose bound came from a speculative threshold is truncated
+        //    there when that band reaches beyond it.
+        int count;
+        bool spec_cut = false;
+        if (flags & ROW_RAW_LIST) {
+            const int n0 = raw & 0xffff, n = n0 + (raw >> 16);
+            const int Pn = pow2_ceil(n > 32 ? n : 32) < P ? pow2_ceil(n > 32 ? n : 32) : P;
+            for (int i = static_cast<int>(lane); i < Pn; i += 32)
+                K[i] = i < n0 ? cand[i] : (i < n ? cand[p.cap - 1 - (i - n0)] : KEY_MAX);
+            __syncwarp();
+            warp_bitonic_sort_smem(K, Pn);
+            const int kk = n < p.k ? n : p.k;
+            uint64_t band = KEY_MAX;
+            if (n >= p.km && n > 0) {
+                band = K[p.km - 1];
+                const float window = p.E ? 2.f * p.E[row] : 0.f;
+                if (window > 0.f) {
+                    const uint64_t wk = key_ceiling(key_val(K[kk - 1]) + window);
+                    band = wk > band ? wk : band;
+                }
+            }
+            const uint64_t tau = p.bound[row];
+            const uint64_t nt = band < tau ? band : tau;
+            int keep = 0;
+            for (int i = static_cast<int>(lane); i < n; i += 32) keep += K[i] <= nt ? 1 : 0;
+            count = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
+            spec_cut = (flags & ROW_SPECULATIVE) && (band > tau || n < p.km);
+        } else {
+            count = raw;
+            for (int i = static_cast<int>(lane); i < count; i += 32) K[i] = cand[i];
+        }
+        __syncwarp();
+
         // 1. direct-difference FP32 distances
         int c = 0;
         for (; c + 1 < count; c += 2) {
-            const uint32_t j0 = key_idx(cand[c]);
-            const uint32_t j1 = key_idx(cand[c + 1]);
+            const uint32_t j0 = key_idx(K[c]);
+            const uint32_t j1 = key_idx(K[c + 1]);
             float r0, r1;
             sqdist_fp32_x2<VEC>(q, p.C + static_cast<int64_t>(j0) * d, p.C + static_cast<int64_t>(j1) * d, d, r0,
                                 r1);
@@ -154,7 +190,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
             }
         }
         if (c < count) {
-            const uint32_t j0 = key_idx(cand[c]);
+            const uint32_t j0 = key_idx(K[c]);
             const float r0 = sqdist_fp32<VEC>(q, p.C + static_cast<int64_t>(j0) * d, d);
             if (lane == 0) K[c] = make_key(r0, j0);
         }
@@ -241,8 +277,9 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
                 p.out_dist[ob + i] = F_INF;
             }
         }
+        const bool truncated = (flags & ROW_TRUNCATED) || spec_cut;
         bool certified = kk == k && !(flags & ROW_SELECT_ERROR) && !giant_tie;
-        if (certified && (flags & ROW_TRUNCATED) && !exact) {
+        if (certified && truncated && !exact) {
             // every left-out point has d' >= value(bound), so d2 >= value(bound) + |q|^2 - E
             double qn2 = 0.0;
             for (int t = static_cast<int>(lane); t < d; t += 32) qn2 = fma((double)q[t], (double)q[t], qn2);
@@ -258,10 +295,15 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
             atomicAdd(&blk_cnt[0], static_cast<unsigned long long>(count));
             if (used64) atomicAdd(&blk_cnt[1], 1ull);
             if (!certified) atomicAdd(&blk_cnt[2], 1ull);
-            if (flags & ROW_TRUNCATED) atomicAdd(&blk_cnt[3], 1ull);
+            if (truncated) atomicAdd(&blk_cnt[3], 1ull);
             if (flags & ROW_THRESHOLD_MISS) atomicAdd(&blk_cnt[4], 1ull);
         }
     }
+}
+
+// Keys in a row's list (a raw list's count holds its two segments' lengths).
+__device__ __forceinline__ int list_length(int raw, uint32_t flags) {
+    return (flags & ROW_RAW_LIST) ? (raw & 0xffff) + (raw >> 16) : raw;
 }
 
 template <bool VEC>
@@ -275,7 +317,7 @@ __global__ void rerank_kernel(RerankParams p, int P) {
     __syncthreads();
     const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
     if (row < p.M) {
-        const int c = p.count[row];
+        const int c = list_length(p.count[row], p.flags[row]);
         if (c >= p.count_min && c <= p.count_max) {
             uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
             double* D64 = reinterpret_cast<double*>(K + P);
@@ -295,7 +337,8 @@ __device__ __forceinline__ int find_seg(const BatchSeg* segs, int32_t nseg, int6
 }
 
 __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs,
-                                      int32_t nseg, int64_t rows, int P, RerankCounters* counters) {
+                                      int32_t nseg, int64_t rows, int P, int32_t count_min, int32_t count_max,
+                                      RerankCounters* counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long blk_cnt[5];
     const int warp = static_cast<int>(threadIdx.x / 32);
@@ -314,6 +357,7 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
         rp.N = b.N;
         rp.d = b.d;
         rp.k = b.k;
+        rp.km = b.km;
         rp.cap = b.cap;
         rp.cand = b.cand;
         rp.count = b.count;
@@ -323,13 +367,17 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
         rp.out_idx = b.out_idx;
         rp.out_dist = b.out_dist;
         rp.row_status = b.row_status;
-        uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
-        double* D64 = reinterpret_cast<double*>(K + P);
-        const int Pp = pow2_ceil(b.cap > 32 ? b.cap : 32);
-        if (b.vec)
-            rerank_row<true>(rp, row - sg.row0, Pp, K, D64, blk_cnt, lane);
-        else
-            rerank_row<false>(rp, row - sg.row0, Pp, K, D64, blk_cnt, lane);
+        const int64_t r = row - sg.row0;
+        const int c = list_length(b.count[r], b.flags[r]);
+        if (c >= count_min && c <= count_max) {
+            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
+            double* D64 = reinterpret_cast<double*>(K + P);
+            const int Pp = pow2_ceil(b.cap > 32 ? b.cap : 32) < P ? pow2_ceil(b.cap > 32 ? b.cap : 32) : P;
+            if (b.vec)
+                rerank_row<true>(rp, r, Pp, K, D64, blk_cnt, lane);
+            else
+                rerank_row<false>(rp, r, Pp, K, D64, blk_cnt, lane);
+        }
     }
     flush_counters(counters, blk_cnt);
 }
@@ -337,10 +385,10 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
 
 }  // namespace
 
-cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
-                                  int32_t cap_max, RerankCounters* counters, cudaStream_t st) {
-    if (rows <= 0) return cudaSuccess;
-    const int P = pow2_ceil(cap_max > 32 ? cap_max : 32);
+namespace {
+cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                        int P, int32_t cmin, int32_t cmax, RerankCounters* counters,
+                                        cudaStream_t st) {
     const size_t per_warp = static_cast<size_t>(P) * 16;
     int warps = static_cast<int>((64u * 1024u) / per_warp);
     if (warps > 8) warps = 8;
@@ -350,9 +398,27 @@ cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, i
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int64_t blocks = (rows + warps - 1) / warps;
-    rerank_batched_kernel<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(probs, segs, nseg, rows, P,
-                                                                                   counters);
+    rerank_batched_kernel<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(probs, segs, nseg, rows, P, cmin,
+                                                                                   cmax, counters);
     return cudaGetLastError();
+}
+}  // namespace
+
+// Rows are re-ranked by list length in up to three launches (at most 512, 1024, and the
+// largest capacity keys per warp buffer), so that a few long lists do not lower the
+// occupancy of the whole batch.
+cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
+                                  int32_t cap_max, RerankCounters* counters, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const int P = pow2_ceil(cap_max > 32 ? cap_max : 32);
+    int lo = INT32_MIN;
+    for (int tier : {512, 1024}) {
+        if (P <= tier) break;
+        cudaError_t e = launch_rerank_batched_range(probs, segs, nseg, rows, tier, lo, tier, counters, st);
+        if (e != cudaSuccess) return e;
+        lo = tier + 1;
+    }
+    return launch_rerank_batched_range(probs, segs, nseg, rows, P, lo, INT32_MAX, counters, st);
 }
 
 namespace {
@@ -378,11 +444,14 @@ cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cma
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
     const int P = pow2_ceil(p.cap > 32 ? p.cap : 32);
-    constexpr int P_SHORT = 512;
-    if (P <= P_SHORT) return launch_rerank_range(p, P, INT32_MIN, INT32_MAX, st);
-    cudaError_t e = launch_rerank_range(p, P_SHORT, INT32_MIN, P_SHORT, st);
-    if (e != cudaSuccess) return e;
-    return launch_rerank_range(p, P, P_SHORT + 1, INT32_MAX, st);
+    int lo = INT32_MIN;
+    for (int tier : {512, 1024}) {
+        if (P <= tier) break;
+        cudaError_t e = launch_rerank_range(p, tier, lo, tier, st);
+        if (e != cudaSuccess) return e;
+        lo = tier + 1;
+    }
+    return launch_rerank_range(p, P, lo, INT32_MAX, st);
 }
 
 }  // namespace knn

@@ -26,6 +26,7 @@ struct FusedProblem {
     int32_t* count;
     uint64_t* bound;
     uint32_t* flags;
+    int32_t spec;              // 1: speculative thresholds during the sweep (columns in natural order)
 };
 
 // A work item of a batched launch: one 128-row block of one problem.
@@ -65,8 +66,11 @@ struct FusedParams {
     const FusedWork* work;     // batched launch: work list, largest items first
 };
 
-// Largest candidate-list capacity of the fused form (32 keys per lane of a warp).
-constexpr int FUSED_CAP_MAX = 1024;
+// Largest candidate-list capacity of the fused form (48 keys per lane of a warp), and the
+// capacity of the band probe's largest proposal and of the second pass over rows the
+// first could not certify.
+constexpr int FUSED_CAP_MAX = 1536;
+constexpr int FUSED_CAP_WIDE = 1024;
 
 bool fused_available();
 int fused_stages(int cap, int precision);  // 0: does not fit

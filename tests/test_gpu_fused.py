@@ -197,3 +197,22 @@ def test_integer_ties_on_a_long_sweep_bit_exact():
     rows = inputs.sample_rows(len(X), 120, seed=74)
     ref_idx, ref_dist = oracle.knng(X, 24, rows=rows)
     check_exact(idx[rows], dist[rows], ref_idx, ref_dist)
+
+
+def test_large_k_integer_bit_exact():
+    # k + m = 632: lists of 1440 keys (48 per lane in the shrink), trimmed before the
+    # re-rank, whose longest tier then takes the rows
+    X = inputs.integer_lattice(n=3000, d=64, lo=-5, hi=5, seed=75)
+    idx, dist, st = graph(X, 600)
+    assert st["fused_used"] == 1 and st["list_capacity"] > 1024
+    check_exact(idx, dist, *oracle.knng(X, 600))
+
+
+def test_large_k_float_search():
+    C = inputs.gaussian_mixture(n=20000, d=64, components=16, seed=76)
+    Q = inputs.gaussian_mixture(n=300, d=64, components=16, seed=77)
+    idx, dist, st = kb.knn_search(dev(Q), dev(C), 500, precision="bf16", fused=1, return_stats=True)
+    assert st["fused_used"] == 1
+    rows = np.arange(0, 300, 10)
+    ref_idx, ref_dist = oracle.knn(Q, C, 500, rows=rows)
+    check_float(Q, C, rows, idx.cpu().numpy()[rows], dist.cpu().numpy()[rows], ref_idx, ref_dist, False)
