@@ -109,6 +109,29 @@ __device__ __forceinline__ void sqdist_fp32_x2(const float* __restrict__ q, cons
     r1 = warp_reduce_pair(s1, e1);
 }
 
+// Four candidates at once (more loads in flight per lane).
+template <bool VEC>
+__device__ __forceinline__ void sqdist_fp32_x4(const float* __restrict__ q, const float* const (&c)[4], int d,
+                                               float (&r)[4]) {
+    if (!VEC) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r[i] = sqdist_fp32<false>(q, c[i], d);
+        return;
+    }
+    const uint32_t lane = lane_id();
+    float s[4] = {0.f, 0.f, 0.f, 0.f}, e[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = static_cast<int>(lane) * 4; t < d; t += 128) {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(q + t));
+        float4 b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) b[i] = __ldg(reinterpret_cast<const float4*>(c[i] + t));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) group_sum(a, b[i], s[i], e[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = warp_reduce_pair(s[i], e[i]);
+}
+
 __device__ __forceinline__ double sqdist_fp64(const float* __restrict__ q, const float* __restrict__ c, int d) {
     double s = 0.0;
     for (int t = static_cast<int>(lane_id()); t < d; t += 32) {
@@ -129,9 +152,14 @@ __device__ __forceinline__ void flush_counters(RerankCounters* counters, unsigne
     }
 }
 
-// One warp re-ranks row `row` of p; K and D64 are the warp's shared-memory arrays of P entries.
+// Members of one near-tie group settled in FP64 at most (a larger group is left unordered
+// and its row reported uncertified).
+constexpr int TIE_MAX = 128;
+
+// One warp re-ranks row `row` of p; K is the warp's shared-memory array of P keys and T64
+// its TIE_MAX doubles for one near-tie group.
 template <bool VEC>
-__device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, int P, uint64_t* K, double* D64,
+__device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, int P, uint64_t* K, double* T64,
                                            unsigned long long* blk_cnt, uint32_t lane) {
     {
         const int raw = p.count[row];
@@ -176,8 +204,23 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         }
         __syncwarp();
 
-        // 1. direct-difference FP32 distances
+        // 1. direct-difference FP32 distances, four candidates at a time
         int c = 0;
+        for (; c + 3 < count; c += 4) {
+            uint32_t j[4];
+            const float* cp[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                j[i] = key_idx(K[c + i]);
+                cp[i] = p.C + static_cast<int64_t>(j[i]) * d;
+            }
+            float r[4];
+            sqdist_fp32_x4<VEC>(q, cp, d, r);
+            if (lane == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) K[c + i] = make_key(r[i], j[i]);
+            }
+        }
         for (; c + 1 < count; c += 2) {
             const uint32_t j0 = key_idx(K[c]);
             const uint32_t j1 = key_idx(K[c + 1]);
@@ -197,7 +240,6 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         // sort only the power of two that holds the list (P bounds it)
         const int Pc = pow2_ceil(count > 32 ? count : 32) < P ? pow2_ceil(count > 32 ? count : 32) : P;
         for (int i = count + static_cast<int>(lane); i < Pc; i += 32) K[i] = KEY_MAX;
-        for (int i = static_cast<int>(lane); i < Pc; i += 32) D64[i] = -1.0;
         __syncwarp();
         warp_bitonic_sort_smem(K, Pc);
 
@@ -208,6 +250,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         const bool exact = p.E != nullptr && p.E[row] == 0.f;
         bool used64 = false;
         bool giant_tie = false;
+        double dk64 = -1.0;  // FP64 distance placed at position kk - 1, when FP64 decided it
         if (!exact && kk > 0) {
             // near(i): positions i and i+1 cannot be ordered by their FP32 values
             auto near = [&](int i) -> bool {
@@ -224,40 +267,36 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
                     // group [s, e]: maximal run with near(s..e-1)
                     int e = s;
                     while (e + 1 < count && near(e)) ++e;
-                    if (e > s) {
+                    const int g = e - s + 1;
+                    if (g > TIE_MAX) {
+                        giant_tie = true;  // left unordered: the row is reported uncertified
+                    } else if (g > 1) {
                         for (int m = s; m <= e; ++m) {
                             const uint32_t j = key_idx(K[m]);
                             const double v = sqdist_fp64(q, p.C + static_cast<int64_t>(j) * d, d);
-                            if (lane == 0) D64[m] = v;
+                            if (lane == 0) T64[m - s] = v;
                         }
                         __syncwarp();
-                        // rank every member by (FP64 distance, index) and place it
-                        const int g = e - s + 1;
-                        uint64_t my_key[4];
-                        double my_val[4];
-                        int my_pos[4];
+                        // rank every member by (FP64 distance, index) and place it; its key
+                        // carries the FP64 distance rounded to FP32 (the output precision)
+                        uint64_t my_key[TIE_MAX / 32];
+                        int my_pos[TIE_MAX / 32];
                         int nm = 0;
-                        for (int m = s + static_cast<int>(lane); m <= e && nm < 4; m += 32, ++nm) {
-                            const double vm = D64[m];
+                        for (int m = s + static_cast<int>(lane); m <= e; m += 32, ++nm) {
+                            const double vm = T64[m - s];
                             const uint32_t jm = key_idx(K[m]);
                             int rank = 0;
                             for (int o = s; o <= e; ++o) {
-                                const double vo = D64[o];
+                                const double vo = T64[o - s];
                                 const uint32_t jo = key_idx(K[o]);
                                 rank += (vo < vm || (vo == vm && jo < jm)) ? 1 : 0;
                             }
                             my_key[nm] = make_key(static_cast<float>(vm), jm);
-                            my_val[nm] = vm;
                             my_pos[nm] = s + rank;
+                            if (s + rank == kk - 1) dk64 = vm;
                         }
                         __syncwarp();
-                        giant_tie |= g > 128;  // left unordered: the row is reported uncertified
-                        if (g <= 128) {
-                            for (int t = 0; t < nm; ++t) {
-                                K[my_pos[t]] = my_key[t];
-                                D64[my_pos[t]] = my_val[t];
-                            }
-                        }
+                        for (int t = 0; t < nm; ++t) K[my_pos[t]] = my_key[t];
                         __syncwarp();
                     }
                     s = e + 1;
@@ -269,9 +308,8 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         const int64_t ob = row * static_cast<int64_t>(k);
         for (int i = static_cast<int>(lane); i < k; i += 32) {
             if (i < kk) {
-                const double v64 = D64[i];
                 p.out_idx[ob + i] = static_cast<int32_t>(key_idx(K[i]));
-                p.out_dist[ob + i] = v64 >= 0.0 ? static_cast<float>(v64) : key_val(K[i]);
+                p.out_dist[ob + i] = key_val(K[i]);
             } else {
                 p.out_idx[ob + i] = -1;
                 p.out_dist[ob + i] = F_INF;
@@ -284,7 +322,10 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
             double qn2 = 0.0;
             for (int t = static_cast<int>(lane); t < d; t += 32) qn2 = fma((double)q[t], (double)q[t], qn2);
             qn2 = warp_sum_d(qn2);
-            const double dk = D64[kk - 1] >= 0.0 ? D64[kk - 1] : (double)key_val(K[kk - 1]) * (1.0 + 0x1p-19);
+            // the lane that placed position kk - 1 in FP64 (if any) holds its distance
+            const double dk64_w = __shfl_sync(0xffffffffu, dk64, __ffs(__ballot_sync(0xffffffffu, dk64 >= 0.0)) - 1);
+            const bool have64 = __any_sync(0xffffffffu, dk64 >= 0.0);
+            const double dk = have64 ? dk64_w : (double)key_val(K[kk - 1]) * (1.0 + 0x1p-19);
             const double bnd = (double)key_val(p.bound[row]);
             const double e = p.E ? (double)p.E[row] * (1.0 + 0x1p-10) : 0.0;
             const double slack = 0x1p-20 * (fabs(bnd) + qn2 + dk);
@@ -319,9 +360,9 @@ __global__ void rerank_kernel(RerankParams p, int P) {
     if (row < p.M) {
         const int c = list_length(p.count[row], p.flags[row]);
         if (c >= p.count_min && c <= p.count_max) {
-            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
-            double* D64 = reinterpret_cast<double*>(K + P);
-            rerank_row<VEC>(p, row, P, K, D64, blk_cnt, lane);
+            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * (P + TIE_MAX);
+            double* T64 = reinterpret_cast<double*>(K + P);
+            rerank_row<VEC>(p, row, P, K, T64, blk_cnt, lane);
         }
     }
     flush_counters(p.counters, blk_cnt);
@@ -370,13 +411,13 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
         const int64_t r = row - sg.row0;
         const int c = list_length(b.count[r], b.flags[r]);
         if (c >= count_min && c <= count_max) {
-            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * 2 * P;
-            double* D64 = reinterpret_cast<double*>(K + P);
+            uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * (P + TIE_MAX);
+            double* T64 = reinterpret_cast<double*>(K + P);
             const int Pp = pow2_ceil(b.cap > 32 ? b.cap : 32) < P ? pow2_ceil(b.cap > 32 ? b.cap : 32) : P;
             if (b.vec)
-                rerank_row<true>(rp, r, Pp, K, D64, blk_cnt, lane);
+                rerank_row<true>(rp, r, Pp, K, T64, blk_cnt, lane);
             else
-                rerank_row<false>(rp, r, Pp, K, D64, blk_cnt, lane);
+                rerank_row<false>(rp, r, Pp, K, T64, blk_cnt, lane);
         }
     }
     flush_counters(counters, blk_cnt);
@@ -389,7 +430,7 @@ namespace {
 cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
                                         int P, int32_t cmin, int32_t cmax, RerankCounters* counters,
                                         cudaStream_t st) {
-    const size_t per_warp = static_cast<size_t>(P) * 16;
+    const size_t per_warp = static_cast<size_t>(P + TIE_MAX) * 8;
     int warps = static_cast<int>((64u * 1024u) / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
@@ -425,7 +466,7 @@ namespace {
 cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cmax, cudaStream_t st) {
     p.count_min = cmin;
     p.count_max = cmax;
-    const size_t per_warp = static_cast<size_t>(P) * 16;
+    const size_t per_warp = static_cast<size_t>(P + TIE_MAX) * 8;
     int warps = static_cast<int>((64u * 1024u) / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
