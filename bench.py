@@ -115,7 +115,10 @@ def run_batch(args):
             "frac_of_bf16_sustained": flops / (ms / 1e3) / 1e12 / P["bf16_sustained"],
             "first_call_s": first_call_s, "clocks": clk,
             "batch_stats": {k: stats[k] for k in ("rows", "candidates", "rows_uncertified", "rows_fallback",
-                                                   "fused_used", "kernel_launches")}}
+                                                   "fused_used", "kernel_launches")},
+            "phases_ms": {"call_host_total": stats["ms_total"], "graph": stats["ms_gemm"],
+                          "prep_bounds": stats["ms_prep"], "fused": stats["ms_select"],
+                          "rerank": stats["ms_rerank"], "plain_problems": stats["ms_fallback"]}}
     # oracle on a few rows of a few problems
     import oracle
     sample = []
@@ -275,8 +278,10 @@ def run_select_only(args):
             "config": {"workload": f"select k={k} smallest of {args.q} rows x {args.cols} uniform FP32 values",
                        "Q": args.q, "n": args.cols, "k": k, "l2": "matrix > L2: no flush needed"},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": P["hbm_gbs"], "unit": "GB/s",
-                         "frac": gbs / P["hbm_gbs"], "traffic": None, "kernel": "select_rows_kernel",
-                         "peak_source": P["source"]},
+                         "frac": gbs / P["hbm_gbs"],
+                         "traffic": (recorded_traffic("select_rows_kernel", ["paper_1309_5478_gb300/csrc/select.cu"])
+                                     if (args.q, args.cols, k) == (16384, 65536, 64) else None),
+                         "kernel": "select_rows_kernel", "peak_source": P["source"]},
             "clocks": clk, "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 

@@ -15,6 +15,7 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -222,9 +223,14 @@ struct BatchWs {
 std::mutex g_bws_mu;
 std::map<int, BatchWs> g_bws;
 
+// Phase marks recorded inside a batch's graph: start, after prep and bounds, after the
+// fused launch, after the fused problems' re-rank, end (after the plain problems).
+constexpr int N_MARKS = 5;
+
 struct CachedGraph {
     cudaGraphExec_t exec = nullptr;
     uint64_t generation = 0;
+    cudaEvent_t marks[N_MARKS] = {};
 };
 std::map<std::string, CachedGraph> g_graphs;
 
@@ -414,24 +420,20 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
 }
 
 // Every launch of the batch (graph-capturable: no host synchronisation, no allocation).
-int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout& L, cudaStream_t st) {
+int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout& L, cudaStream_t st,
+                  cudaEvent_t* marks) {
+    // external record nodes when captured (a plain record would only order the graph)
+    auto mark = [&](int i) { return marks ? cudaEventRecordWithFlags(marks[i], st, cudaEventRecordExternal) : cudaSuccess; };
+    KNN_CK(mark(0));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
-    for (const BatchDev& b : L.dev) {
-        KNN_CK(cudaMemsetAsync(b.gq, 0, sizeof(PrepGlobals), st));
-        if (b.gc != b.gq) KNN_CK(cudaMemsetAsync(b.gc, 0, sizeof(PrepGlobals), st));
-    }
+    KNN_CK(launch_batch_init(L.d_dev, static_cast<int32_t>(L.dev.size()), st));
     if (!L.fused_ids.empty()) {
-        // NaN padding of the corpus norms past N (padded columns never pass a threshold)
-        for (int i : L.fused_ids) {
-            const BatchDev& b = L.dev[i];
-            const int64_t n_pad = (b.N + 255) / 256 * 256;
-            if (n_pad > b.N) KNN_CK(cudaMemsetAsync(b.cnorm2 + b.N, 0xff, (n_pad - b.N) * sizeof(float), st));
-        }
         KNN_CK(launch_prep_batched(L.d_dev, L.d_prep_segs, static_cast<int32_t>(L.prep_segs.size()), L.prep_rows, prec,
                                    st));
         KNN_CK(launch_bounds_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
                                      prec, st));
+        KNN_CK(mark(1));
         FusedParams fp{};
         fp.status = L.status;
         fp.scratch = L.scratch;
@@ -441,9 +443,14 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
         fp.problems = L.d_fprob;
         fp.work = L.d_work;
         KNN_CK(launch_fused_batched(fp, prec, L.grid, st));
+        KNN_CK(mark(2));
         KNN_CK(launch_rerank_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
                                      L.cap_max, L.counters, st));
+    } else {
+        KNN_CK(mark(1));
+        KNN_CK(mark(2));
     }
+    KNN_CK(mark(3));
     if (!L.plain_ids.empty()) {
         KNN_CK(launch_prep_batched(L.d_dev, L.d_plain_prep_segs, static_cast<int32_t>(L.plain_prep_segs.size()),
                                    L.plain_prep_rows, P_FP32, st));
@@ -496,6 +503,7 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
             }
         }
     }
+    KNN_CK(mark(4));
     return KNN_OK;
 }
 
@@ -520,6 +528,7 @@ std::string signature(const std::vector<Problem>& probs, const std::vector<int>&
 // first failure or KNN_OK.
 int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precision_req, ::knn_stats* stats,
               cudaStream_t st) {
+    const auto t_call = std::chrono::steady_clock::now();
     const int n = static_cast<int>(probs.size());
     std::vector<int> sched(n, SCHED_PLAIN);
     int prec = precision_req == KNN_FP8_E4M3 ? P_FP8 : P_BF16;
@@ -595,13 +604,15 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         cudaGraphExecDestroy(cg.exec);
         cg.exec = nullptr;
     }
+    if (!cg.marks[0])
+        for (auto& e : cg.marks) KNN_CK(cudaEventCreate(&e));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!cg.exec) {
         cudaStream_t cs = nullptr;
         KNN_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t g = nullptr;
         KNN_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue_batch(probs, prec, L, cs);
+        const int rc = enqueue_batch(probs, prec, L, cs, cg.marks);
         const cudaError_t ec = cudaStreamEndCapture(cs, &g);
         cudaStreamDestroy(cs);
         if (rc != KNN_OK) {
@@ -628,6 +639,12 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    float phase[N_MARKS - 1] = {};
+    for (int i = 0; i + 1 < N_MARKS; ++i)
+        if (cudaEventElapsedTime(&phase[i], cg.marks[i], cg.marks[i + 1]) != cudaSuccess) {
+            cudaGetLastError();
+            phase[i] = -1.f;
+        }
     if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the batched fused kernel stopped: a device-side wait timed out");
 
     // per problem: NaN/Inf inputs, then rows the batch could not certify
@@ -676,8 +693,14 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
         stats->rows_fallback = fallback_rows;
         stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
-        stats->ms_total = ms;
+        // device phases of the graph; ms_total is the whole call on the host, so
+        // ms_total - ms_gemm is the host work around the graph
+        stats->ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_call).count();
         stats->ms_gemm = ms;
+        stats->ms_prep = phase[0];
+        stats->ms_select = phase[1];
+        stats->ms_rerank = phase[2];
+        stats->ms_fallback = phase[3];
         stats->fused_used = static_cast<int32_t>(L.fused_ids.size());
         stats->list_capacity = L.cap_max;
         stats->precision_used = prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3;
@@ -686,7 +709,7 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         for (const Problem& p : probs) flops += 2.0 * double(p.M) * double(p.N) * double(p.d);
         stats->gemm_flops = flops;
         stats->kernel_launches =
-            (L.fused_ids.empty() ? 0 : 3 + rerank_launches(L.cap_max)) + (L.plain_ids.empty() ? 0 : 2);
+            1 + (L.fused_ids.empty() ? 0 : 3 + rerank_launches(L.cap_max)) + (L.plain_ids.empty() ? 0 : 2);
         for (int i : L.plain_ids) {
             const Problem& p = probs[i];
             const int64_t ldn = (p.N + 31) / 32 * 32;

@@ -543,43 +543,76 @@ __device__ __forceinline__ uint32_t select32(const uint32_t (&r)[32], int t) {
     return (t & 1) ? a[1] : a[0];
 }
 
-// Ranking value of column t of a chunk: v = |c_j|^2 - 2 acc (FP8: acc scaled back first).
-template <int P>
-__device__ __forceinline__ float chunk_value(uint32_t acc_bits, float cn, float cs, float qscale) {
-    float a = __uint_as_float(acc_bits);
-    if constexpr (P == P_FP8) a *= cs * qscale;
-    return fmaf(-2.f, a, cn);
+// Packed FP32 pairs (sm_100 and later): each half is rounded exactly like its scalar
+// counterpart, so results match fmaf / __fmul_rn bit for bit.
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1, float c0,
+                                     float c1) {
+    asm("{\n .reg .b64 A, B, C, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n mov.b64 C, {%6, %7};\n"
+        " fma.rn.f32x2 D, A, B, C;\n mov.b64 {%0, %1}, D;\n}\n"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+__device__ __forceinline__ void mul2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    asm("{\n .reg .b64 A, B, D;\n mov.b64 A, {%2, %3};\n mov.b64 B, {%4, %5};\n"
+        " mul.rn.f32x2 D, A, B;\n mov.b64 {%0, %1}, D;\n}\n"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+// Three-input minimum (a NaN operand is ignored, as with fminf).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
-// Filters one 32-column chunk of the accumulator into the row's candidate list: every
-// ranking value is compared with the row's float threshold; a lane's survivors (rare once
-// the threshold has settled) are then taken one per round, their value recomputed from
-// the accumulator register picked by a select tree, and appended to the lane's segment of
-// the row's list (slot base + dir * cnt). The warp runs as many rounds as its lane with
-// the most survivors.
+// Filters one 32-column chunk of the accumulator into the row's candidate list. The
+// ranking values v = |c_j|^2 - 2 acc (FP8: acc scaled back first) replace the accumulator
+// bits in r (packed pair arithmetic); a tree of three-input minimums gives the lane's
+// smallest value, and one warp vote ends the chunk when no lane has a value at or below
+// its row's threshold, the common case once thresholds have settled. Otherwise the lanes
+// build their survivor masks and take one survivor per round, its value picked from r
+// by a select tree, appending it to the lane's segment of the row's list (slot
+// base + dir * cnt); the warp runs as many rounds as its lane with the most survivors.
 template <int P>
-__device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
+__device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
                                              int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt,
                                              int base, int dir) {
-    uint32_t m8[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 c = reinterpret_cast<const float4*>(cn)[q];
-        const float cv[4] = {c.x, c.y, c.z, c.w};
-        float sv[4] = {1.f, 1.f, 1.f, 1.f};
+        float a0 = __uint_as_float(r[4 * q]), a1 = __uint_as_float(r[4 * q + 1]);
+        float a2 = __uint_as_float(r[4 * q + 2]), a3 = __uint_as_float(r[4 * q + 3]);
         if constexpr (P == P_FP8) {
             const float4 sc = reinterpret_cast<const float4*>(cs)[q];
-            sv[0] = sc.x;
-            sv[1] = sc.y;
-            sv[2] = sc.z;
-            sv[3] = sc.w;
+            float s0, s1, s2, s3;
+            mul2(s0, s1, sc.x, sc.y, qscale, qscale);
+            mul2(s2, s3, sc.z, sc.w, qscale, qscale);
+            mul2(a0, a1, a0, a1, s0, s1);
+            mul2(a2, a3, a2, a3, s2, s3);
         }
+        float v0, v1, v2, v3;
+        fma2(v0, v1, a0, a1, -2.f, -2.f, c.x, c.y);
+        fma2(v2, v3, a2, a3, -2.f, -2.f, c.z, c.w);
+        r[4 * q] = __float_as_uint(v0);
+        r[4 * q + 1] = __float_as_uint(v1);
+        r[4 * q + 2] = __float_as_uint(v2);
+        r[4 * q + 3] = __float_as_uint(v3);
+    }
+    // lane minimum over the 32 values: 10 + 4 + 1 + 1 three- and two-input minimums
+    float m[11];
+#pragma unroll
+    for (int i = 0; i < 10; ++i)
+        m[i] = min3f(__uint_as_float(r[3 * i]), __uint_as_float(r[3 * i + 1]), __uint_as_float(r[3 * i + 2]));
+    m[10] = fminf(__uint_as_float(r[30]), __uint_as_float(r[31]));
+    const float mn = fminf(min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
+                           fminf(m[9], m[10]));
+    if (!__any_sync(0xffffffffu, mn <= tau_f)) return;
+    uint32_t m8[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
         uint32_t mq = 0;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float v = chunk_value<P>(r[q * 4 + e], cv[e], sv[e], qscale);
-            mq |= (v <= tau_f) ? (1u << e) : 0u;
-        }
+        for (int e = 0; e < 4; ++e) mq |= (__uint_as_float(r[q * 4 + e]) <= tau_f) ? (1u << e) : 0u;
         m8[q] = mq << (4 * q);
     }
     uint32_t mask = ((m8[0] | m8[1]) | (m8[2] | m8[3])) | ((m8[4] | m8[5]) | (m8[6] | m8[7]));
@@ -591,7 +624,7 @@ __device__ __forceinline__ void filter_chunk(const uint32_t (&r)[32], const floa
         const int t = (__ffs(mask) - 1) & 31;
         const bool has = mask != 0u;
         mask &= mask - 1u;
-        const float v = chunk_value<P>(select32(r, t), cn[t], P == P_FP8 ? cs[t] : 1.f, qscale);
+        const float v = __uint_as_float(select32(r, t));
         if (has) {
             gbuf[base + dir * cnt] = make_key(v, jlo + static_cast<uint32_t>(t));
             ++cnt;

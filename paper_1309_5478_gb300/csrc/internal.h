@@ -146,6 +146,10 @@ struct BatchSeg {
     int32_t which;    // 0: corpus rows, 1: query rows
 };
 
+// Per-problem initialisation of a batch in one launch: the prep statistics zeroed, and
+// the corpus norms of the tensor-core problems (those with a reduced-precision copy)
+// padded past N to a multiple of 256 with NaN, so that padded columns never pass.
+cudaError_t launch_batch_init(const BatchDev* probs, int32_t n, cudaStream_t st);
 // Prep of every corpus (and non-graph query) row of the batch; segs sorted by row0.
 cudaError_t launch_prep_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
                                 int32_t precision, cudaStream_t st);

@@ -49,12 +49,32 @@ __device__ __forceinline__ float quantise(float x, float scale, void* xq, int64_
     }
 }
 
-// One warp prepares one row: norms, the reduced-precision copy and the row statistics.
+// Statistics of the rows a warp has prepared, flushed to a problem's PrepGlobals with one
+// set of atomics (values >= 0 compare as their bit patterns).
+struct RowStatsAcc {
+    float max_res = 0.f, max_tnorm = 0.f, max_norm2 = 0.f, max_abs = 0.f;
+    uint32_t nonfinite = 0, noninteger = 0;
+    __device__ __forceinline__ void flush(PrepGlobals* g, bool reduced) {
+        if (lane_id() != 0) return;
+        if (reduced) {
+            atomic_max_bits(&g->max_res, max_res);
+            atomic_max_bits(&g->max_tnorm, max_tnorm);
+        }
+        atomic_max_bits(&g->max_norm2, max_norm2);
+        atomic_max_bits(&g->max_abs, max_abs);
+        if (nonfinite) atomicAdd(&g->nonfinite, nonfinite);
+        if (noninteger) atomicAdd(&g->noninteger, noninteger);
+        *this = RowStatsAcc{};
+    }
+};
+
+// One warp prepares one row: norms, the reduced-precision copy, and the row's statistics
+// into acc (every lane holds the same values).
 template <int P>
 __device__ __forceinline__ void prep_row(const float* __restrict__ X, int64_t row, int32_t d,
                                          float* __restrict__ norm2, float* __restrict__ res,
                                          float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
-                                         float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
+                                         float* __restrict__ inv_scale, RowStatsAcc& acc) {
     const uint32_t lane = lane_id();
     const float* x = X + row * static_cast<int64_t>(d);
 
@@ -102,29 +122,32 @@ __device__ __forceinline__ void prep_row(const float* __restrict__ X, int64_t ro
             res[row] = rn;
             tnorm[row] = tn;
             if (inv_scale) inv_scale[row] = 1.f / scale;
-            atomic_max_bits(&g->max_res, rn);
-            atomic_max_bits(&g->max_tnorm, tn);
         }
+        acc.max_res = fmaxf(acc.max_res, rn);
+        acc.max_tnorm = fmaxf(acc.max_tnorm, tn);
     }
-    if (lane == 0) {
-        norm2[row] = s2;
-        if (!bad) {
-            atomic_max_bits(&g->max_norm2, s2);
-            atomic_max_bits(&g->max_abs, amax);
-        }
-        if (bad) atomicAdd(&g->nonfinite, 1u);
-        if (nonint) atomicAdd(&g->noninteger, 1u);
+    if (lane == 0) norm2[row] = s2;
+    if (!bad) {
+        acc.max_norm2 = fmaxf(acc.max_norm2, s2);
+        acc.max_abs = fmaxf(acc.max_abs, amax);
     }
+    acc.nonfinite += bad ? 1u : 0u;
+    acc.noninteger += nonint ? 1u : 0u;
 }
+
+constexpr int PREP_ROWS_PER_WARP = 16;
 
 template <int P>
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d,
                                                    float* __restrict__ norm2, float* __restrict__ res,
                                                    float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
                                                    float* __restrict__ inv_scale, PrepGlobals* __restrict__ g) {
-    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-    if (row >= rows) return;
-    prep_row<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
+    const int64_t r0 = (static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32) * PREP_ROWS_PER_WARP;
+    if (r0 >= rows) return;
+    const int64_t r1 = r0 + PREP_ROWS_PER_WARP < rows ? r0 + PREP_ROWS_PER_WARP : rows;
+    RowStatsAcc acc;
+    for (int64_t row = r0; row < r1; ++row) prep_row<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, acc);
+    acc.flush(g, P != P_FP32);
 }
 
 // Segment holding global row `row` (segs sorted by row0, segs[0].row0 == 0).
@@ -137,19 +160,47 @@ __device__ __forceinline__ int find_seg(const BatchSeg* segs, int32_t nseg, int6
     return lo;
 }
 
+__global__ void batch_init_kernel(const BatchDev* __restrict__ probs, int32_t n) {
+    const int32_t i = blockIdx.x;
+    if (i >= n) return;
+    const BatchDev& b = probs[i];
+    constexpr int W = static_cast<int>(sizeof(PrepGlobals) / 4);
+    if (threadIdx.x < W) {
+        reinterpret_cast<uint32_t*>(b.gq)[threadIdx.x] = 0u;
+        if (b.gc != b.gq) reinterpret_cast<uint32_t*>(b.gc)[threadIdx.x] = 0u;
+    }
+    if (b.xc) {
+        const int64_t n_pad = (b.N + 255) / 256 * 256;
+        for (int64_t j = b.N + threadIdx.x; j < n_pad; j += blockDim.x) b.cnorm2[j] = __uint_as_float(0xffffffffu);
+    }
+}
+
 template <int P>
 __global__ void __launch_bounds__(256) prep_batched_kernel(const BatchDev* __restrict__ probs,
                                                            const BatchSeg* __restrict__ segs, int32_t nseg,
                                                            int64_t rows) {
-    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
-    if (row >= rows) return;
-    const BatchSeg sg = segs[find_seg(segs, nseg, row)];
-    const BatchDev& b = probs[sg.problem];
-    const int64_t r = row - sg.row0;
-    if (sg.which == 0)
-        prep_row<P>(b.C, r, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, b.gc);
-    else
-        prep_row<P>(b.Q, r, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, b.gq);
+    const int64_t r0 = (static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32) * PREP_ROWS_PER_WARP;
+    if (r0 >= rows) return;
+    const int64_t r1 = r0 + PREP_ROWS_PER_WARP < rows ? r0 + PREP_ROWS_PER_WARP : rows;
+    // a warp's rows span at most a few segments: the statistics are flushed per segment
+    int64_t row = r0;
+    while (row < r1) {
+        const int si = find_seg(segs, nseg, row);
+        const BatchSeg sg = segs[si];
+        const int64_t seg_end = si + 1 < nseg ? segs[si + 1].row0 : rows;
+        const int64_t stop = seg_end < r1 ? seg_end : r1;
+        const BatchDev& b = probs[sg.problem];
+        RowStatsAcc acc;
+        if (sg.which == 0) {
+            for (; row < stop; ++row)
+                prep_row<P>(b.C, row - sg.row0, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, acc);
+            acc.flush(b.gc, P != P_FP32);
+        } else {
+            for (; row < stop; ++row)
+                prep_row<P>(b.Q, row - sg.row0, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, acc);
+            acc.flush(b.gq, P != P_FP32);
+        }
+    }
 }
 
 // Error bound of the ranking value d'_ij = |c_j|^2 - 2 q_i.c_j as computed by the
@@ -299,7 +350,7 @@ cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precisi
                         float* tnorm, void* xq, int32_t ldq, float* inv_scale, PrepGlobals* g, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     const int warps = 8;
-    const unsigned blocks = static_cast<unsigned>((rows + warps - 1) / warps);
+    const unsigned blocks = static_cast<unsigned>((rows + warps * PREP_ROWS_PER_WARP - 1) / (warps * PREP_ROWS_PER_WARP));
     switch (precision) {
         case P_FP32:
             prep_kernel<P_FP32><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
@@ -316,10 +367,16 @@ cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precisi
     return cudaGetLastError();
 }
 
+cudaError_t launch_batch_init(const BatchDev* probs, int32_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    batch_init_kernel<<<static_cast<unsigned>(n), 256, 0, st>>>(probs, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_prep_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
                                 int32_t precision, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
-    const unsigned blocks = static_cast<unsigned>((rows + 7) / 8);
+    const unsigned blocks = static_cast<unsigned>((rows + 8 * PREP_ROWS_PER_WARP - 1) / (8 * PREP_ROWS_PER_WARP));
     switch (precision) {
         case P_FP32: prep_batched_kernel<P_FP32><<<blocks, 256, 0, st>>>(probs, segs, nseg, rows); break;
         case P_BF16: prep_batched_kernel<P_BF16><<<blocks, 256, 0, st>>>(probs, segs, nseg, rows); break;
