@@ -205,6 +205,25 @@ def run_mlp(args):
     clocks.start()
     ms_with, st_with = timed(with_mlp)
     ms_without, st_without = timed(without_mlp)
+    # the method without any speculation (plain running thresholds), with and without the
+    # network: what the learned thresholds gain over the method alone
+    variants = {}
+    prev = os.environ.get("KNN_SPECULATE")
+    os.environ["KNN_SPECULATE"] = "0"
+    try:
+        for name, fn in (("running_threshold_only", without_mlp), ("learned_threshold_only", with_mlp)):
+            ms_v, st_v = timed(fn)
+            sv = st_v[-1]
+            variants[name] = {"ms_per_step": ms_v, "rows_per_s": n / (ms_v / 1e3), "ms_select": sv["ms_select"],
+                              "ms_rerank": sv["ms_rerank"], "ms_fallback": sv["ms_fallback"],
+                              "rows_fallback": int(sv["rows_fallback"])}
+    finally:
+        if prev is None:
+            os.environ.pop("KNN_SPECULATE", None)
+        else:
+            os.environ["KNN_SPECULATE"] = prev
+    variants["speculative_only"] = {"ms_per_step": ms_without, "ms_select": st_without[-1]["ms_select"]}
+    variants["speculative_and_learned"] = {"ms_per_step": ms_with, "ms_select": st_with[-1]["ms_select"]}
     clk = clocks.stop()
     identical = bool(torch.equal(oi, oi2) and torch.equal(od, od2))
     s1, s0 = st_with[-1], st_without[-1]
@@ -229,6 +248,9 @@ def run_mlp(args):
                          "threshold_misses": int(s1["threshold_misses"]),
                          "rows_uncertified": int(s1["rows_uncertified"]), "rows_fallback": int(s1["rows_fallback"])},
             "speedup_vs_without": ms_without / ms_with,
+            "variants": variants,
+            "learned_gain_over_running_threshold": (variants["running_threshold_only"]["ms_per_step"] /
+                                                    variants["learned_threshold_only"]["ms_per_step"]),
             "identical_to_without": identical,
             "pass_rate": 1.0 - (s1["rows_uncertified"] + s1["threshold_misses"]) / n,
             "proposal_log_ratio": {"median": float(lr.median()), "p01": float(torch.quantile(lr.float(), 0.01)),

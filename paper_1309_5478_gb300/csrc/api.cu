@@ -920,6 +920,31 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
 
 }  // namespace
 
+// Recomputes the given query rows of pb exactly (the plain FP32 form over gathered rows,
+// then FP64 for any it cannot certify), writing their output rows in place: the
+// fallback of the batched form for rows its re-rank could not certify.
+int recompute_rows(const Problem& pb, const std::vector<int32_t>& rows, cudaStream_t st) {
+    if (rows.empty()) return KNN_OK;
+    CommonLayout L;
+    {
+        Arena sz;
+        layout_common(pb, P_FP32, true, sz, L);
+        void* base = nullptr;
+        KNN_TRY(workspace_get(sz.used(), &base));
+        Arena ar(static_cast<char*>(base), sz.used());
+        L = CommonLayout{};
+        layout_common(pb, P_FP32, true, ar, L);
+    }
+    Timing tm;
+    KNN_TRY(prep_and_check(pb, P_FP32, L, st, nullptr, tm));
+    KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
+    int64_t n64 = 0;
+    KNN_TRY(plain_fallback(pb, L, rows, st, tm, &n64));
+    KNN_CK(cudaStreamSynchronize(st));
+    return KNN_OK;
+}
+
+
 int run_problem(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     int prec = pb.precision;
     const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));

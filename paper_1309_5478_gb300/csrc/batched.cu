@@ -669,15 +669,16 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
             rs.resize(static_cast<size_t>(b.M));
             KNN_CK(cudaMemcpyAsync(rs.data(), b.row_status, b.M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
             KNN_CK(cudaStreamSynchronize(st));
-            bool any = false;
-            for (uint32_t v : rs) any |= (v & ROW_UNCERTIFIED) != 0;
-            if (!any) continue;
-            // rare: recompute the whole problem with the plain form (exact, own workspace)
+            std::vector<int32_t> bad;
+            for (int64_t r = 0; r < b.M; ++r)
+                if (rs[static_cast<size_t>(r)] & ROW_UNCERTIFIED) bad.push_back(static_cast<int32_t>(r));
+            if (bad.empty()) continue;
+            // rare: recompute those rows exactly (plain FP32 form, then FP64)
             Problem q = probs[i];
             q.precision = KNN_FP32;
             q.fused = 0;
-            const int rc = run_problem(q, nullptr, st);
-            fallback_rows += q.M;
+            const int rc = recompute_rows(q, bad, st);
+            fallback_rows += static_cast<int64_t>(bad.size());
             if (rc != KNN_OK) {
                 status[i] = rc;
                 if (first == KNN_OK) first = rc;

@@ -104,6 +104,8 @@ cudaError_t launch_scatter_out(const int32_t* rows, int32_t n, int32_t k, const 
 
 // Runs one problem end to end (device pointers); fills stats when non-null.
 int run_problem(const Problem& pb, ::knn_stats* stats, cudaStream_t st);
+// Exact recomputation of the given query rows of pb in place (plain FP32 form, then FP64).
+int recompute_rows(const Problem& pb, const std::vector<int32_t>& rows, cudaStream_t st);
 
 // Runs independent problems (device pointers) as one batch: one CUDA graph holding a
 // persistent fused launch and the plain form's launches. status[i] receives each

@@ -454,13 +454,19 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
 }
 
 
-// Fast path of a mid-sweep shrink of row r (inline, compact code): the sampled threshold
-// search of shrink_row_k and the ballot compaction. Returns false, with the list and the
-// row state untouched, when no sample value passes or the threshold would keep more than
-// keep_max keys; the caller then runs shrink_row_k.
+// Fast path of a shrink of row r (inline, compact code): the sampled threshold search
+// of shrink_row_k and the ballot compaction. When the sampled band would keep more than
+// keep_max keys it is refined to the exact band edge by bisection; if that still keeps
+// too many (or no sample value reaches the ranks), the list is truncated instead at
+// the largest sample value that keeps at most keep_trunc keys, found by a binary search
+// over the sorted sample, and the row is marked truncated there (every key dropped is
+// above that value; the re-rank certificate decides). Returns false, with the list and
+// the row state untouched, when no such value exists (keep_trunc = 0 disables truncation);
+// the caller then runs shrink_row_k.
 template <int KPL>
 __device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es, const RowState& rs, int r,
-                                                int64_t grow, float window, int rk, int rkm, int keep_max) {
+                                                int64_t grow, float window, int rk, int rkm, int keep_max,
+                                                int keep_trunc) {
     const int lane = static_cast<int>(lane_id());
     const int n0 = rs.cnt[2 * r];
     const int n = n0 + rs.cnt[2 * r + 1];
@@ -483,11 +489,11 @@ __device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es
         int c = 0;
 #pragma unroll
         for (int q = 0; q < KPL; ++q) c += static_cast<uint32_t>(key[q] >> 32) <= x ? 1 : 0;  // padding is KEY_MAX
-        return __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(c));
+        return static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(c)));
     };
     auto passes = [&](uint32_t cand) {
-        if (count_le(cand) < static_cast<uint32_t>(rkm)) return false;
-        return window <= 0.f || count_le(float_to_ord(ord_to_float(cand) - window)) >= static_cast<uint32_t>(rk);
+        if (count_le(cand) < rkm) return false;
+        return window <= 0.f || count_le(float_to_ord(ord_to_float(cand) - window)) >= rk;
     };
     int s0 = (32 * rkm + n - 1) / n;
     s0 = s0 > 31 ? 31 : s0;
@@ -499,14 +505,51 @@ __device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es
         for (int s1 = s0 + 1; s1 < 32 && sel < 0; ++s1)
             if (passes(__shfl_sync(0xffffffffu, smp, s1))) sel = s1;
     }
-    if (sel < 0) return false;
-    const uint64_t band = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, sel)));
-    const uint64_t nt = band < t ? band : t;
-    int keep = 0;
+    uint64_t nt = t;
+    int keep = n + 1;
+    bool trunc = false;
+    if (sel >= 0) {
+        const uint64_t band = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, sel)));
+        nt = band < t ? band : t;
+        keep = 0;
 #pragma unroll
-    for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
-    keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
-    if (keep > keep_max) return false;
+        for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
+        keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
+    }
+    if (sel >= 0 && keep > keep_max) {
+        // the sample value overshoots the band by up to one sample gap: the exact band edge
+        // is the smallest value passing, found by bisection on the ordered values between
+        // the last failing sample value and the passing one
+        uint32_t lo_v = sel > 0 ? __shfl_sync(0xffffffffu, smp, sel - 1) : 0u;  // fails (or below all)
+        uint32_t hi_v = __shfl_sync(0xffffffffu, smp, sel);                       // passes
+        while (hi_v - lo_v > 1u) {
+            const uint32_t mid = lo_v + ((hi_v - lo_v) >> 1);
+            if (passes(mid)) hi_v = mid; else lo_v = mid;
+        }
+        const uint64_t band = key_ceiling(ord_to_float(hi_v));
+        nt = band < t ? band : t;
+        keep = 0;
+#pragma unroll
+        for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
+        keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
+    }
+    if (keep > keep_max) {
+        // the band does not fit: truncate at the largest sample value keeping <= keep_trunc
+        int lo = 0, hi = (sel >= 0 ? sel : 32) - 1, best = -1;
+        while (lo <= hi) {
+            const int mid = (lo + hi) >> 1;
+            if (count_le(__shfl_sync(0xffffffffu, smp, mid)) <= keep_trunc) {
+                best = mid;
+                lo = mid + 1;
+            } else {
+                hi = mid - 1;
+            }
+        }
+        if (best < 0) return false;
+        const uint64_t tt = key_ceiling(ord_to_float(__shfl_sync(0xffffffffu, smp, best)));
+        nt = tt < t ? tt : t;
+        trunc = true;
+    }
     const uint32_t lt_mask = lanemask_lt();
     int nn = 0;
 #pragma unroll
@@ -523,7 +566,7 @@ __device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es
         rs.cnt[2 * r + 1] = 0;
         rs.tau[r] = nt;
         rs.tauf[r] = tau_filter(nt);
-        if (speculated) rs.flags[r] |= RS_SPEC;
+        rs.flags[r] |= (speculated ? RS_SPEC : 0u) | (trunc ? RS_TRUNC : 0u);
     }
     __syncwarp();
     return true;
@@ -895,7 +938,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             need &= need - 1;
                             const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
                             const float w = __shfl_sync(0xffffffffu, my_window, owner);
-                            if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid))
+                            if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid,
+                                                      trunc_mid))
                                 shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, rk, rkm, keep_mid, trunc_mid);
                         }
                     }
@@ -908,8 +952,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // row block done: each row's list (both segments, every key <= its threshold)
             // goes to the re-rank, which reduces it to the band of the k-th and (k+m)-th.
             // Lists longer than RAW_LIST_MAX are trimmed here first (to a sampled band
-            // threshold, like a shrink with the ranks k and k + m), so that the re-rank
-            // sorts at most RAW_LIST_MAX keys per row.
+            // threshold, like a shrink with the ranks k and k + m, never truncating), so
+            // that the re-rank mostly sorts at most RAW_LIST_MAX keys per row.
             {
                 const int total = rs.cnt[2 * row_in_block] + rs.cnt[2 * row_in_block + 1];
                 uint32_t need = __ballot_sync(0xffffffffu, valid && total > RAW_LIST_MAX);
@@ -919,7 +963,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     need &= need - 1;
                     const int64_t g = static_cast<int64_t>(rb) * TC_BM + quarter * 32 + owner;
                     const float w = __shfl_sync(0xffffffffu, my_window, owner);
-                    if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, p.k, p.km, RAW_LIST_MAX))
+                    if (!shrink_mid_fast<KPL>(p, es, rs, quarter * 32 + owner, g, w, p.k, p.km, p.cap, 0))
                         shrink_row_k<KPL>(p, es, rs, quarter * 32 + owner, g, w, p.k, p.km, p.cap, p.cap);
                 }
                 pair_barrier(quarter);

@@ -114,3 +114,25 @@ def test_autotuner_writes_its_cache(monkeypatch, tmp_path):
     st = kb.knn_search_batched(probs)
     assert st == [0]
     check_all(probs, refs)
+
+
+def test_uncertified_rows_of_a_batch_are_recomputed():
+    # a crowded problem (points close together far from the origin: the reduced-precision
+    # bound dwarfs the distances, lists overflow and rows stay uncertified) next to an
+    # ordinary one; only the crowded problem's rows go through the fallback, and both are exact
+    rng = np.random.default_rng(81)
+    base = rng.standard_normal(64).astype(np.float32) * 30
+    C1 = (base + 0.05 * rng.standard_normal((3000, 64))).astype(np.float32)
+    Q1 = (base + 0.05 * rng.standard_normal((200, 64))).astype(np.float32)
+    C2 = inputs.gaussian_mixture(n=2500, d=64, components=4, seed=82)
+    Q2 = inputs.gaussian_mixture(n=150, d=64, components=4, seed=83)
+    probs, refs = [], []
+    for Q, C, k in ((Q1, C1, 10), (Q2, C2, 12)):
+        probs.append({"Q": torch.from_numpy(Q).cuda(), "C": torch.from_numpy(C).cuda(), "k": k,
+                      "out_idx": torch.empty((Q.shape[0], k), dtype=torch.int32, device="cuda"),
+                      "out_dist": torch.empty((Q.shape[0], k), dtype=torch.float32, device="cuda")})
+        refs.append((Q, C, k, False))
+    st, stats = kb.knn_search_batched(probs, precision="bf16", return_stats=True)
+    assert st == [0, 0]
+    assert 0 < stats["rows_fallback"] <= Q1.shape[0]
+    check_all(probs, refs, exact=False)
