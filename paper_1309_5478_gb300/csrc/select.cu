@@ -24,7 +24,8 @@
 namespace knn {
 namespace {
 
-constexpr int SEL_U = 4;  // 16-byte loads per lane per step
+constexpr int SEL_U = 8;                 // 16-byte loads per lane per step
+constexpr int STEP = 32 * 4 * SEL_U;     // values per warp and step
 
 struct RowBuffers {
     uint64_t* A;
@@ -37,54 +38,69 @@ __host__ __device__ constexpr size_t warp_smem_bytes(int bufk) {
     return static_cast<size_t>(bufk) * 16 + static_cast<size_t>(SEG_MAX) * 8;
 }
 
+// One step of a row into v (value 4u + c of a lane is column base + (32u + lane) 4 + c).
+// Full steps of 16-byte aligned rows take 16-byte streaming loads; the last step is
+// loaded value by value, NaN past the row end (NaN never passes a threshold compare).
 template <bool VEC>
-__device__ __forceinline__ void load_group(const float* rowp, int64_t N, int64_t idx4, float (&v)[4]) {
-    if (VEC && idx4 + 4 <= N) {
-        const float4 f = ldg_stream_f4(rowp + idx4);
-        v[0] = f.x;
-        v[1] = f.y;
-        v[2] = f.z;
-        v[3] = f.w;
-    } else {
-        // past the row end: NaN never passes a threshold compare
+__device__ __forceinline__ void load_step(const float* rowp, int64_t N, int64_t base, float (&v)[4 * SEL_U]) {
+    const uint32_t lane = lane_id();
+    if (VEC && base + STEP <= N) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) v[c] = (idx4 + c < N) ? rowp[idx4 + c] : __int_as_float(0x7fffffff);
+        for (int u = 0; u < SEL_U; ++u) {
+            const float4 f = ldg_stream_f4(rowp + base + (static_cast<int64_t>(u) * 32 + lane) * 4);
+            v[4 * u] = f.x;
+            v[4 * u + 1] = f.y;
+            v[4 * u + 2] = f.z;
+            v[4 * u + 3] = f.w;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < SEL_U; ++u)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int64_t idx = base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c;
+                v[4 * u + c] = idx < N ? rowp[idx] : __int_as_float(0x7fffffff);
+            }
     }
 }
 
-// Survivor bits (4 per float4 group, SEL_U groups) of one lane: value <= thr, where thr
-// is the float form of the running threshold (tau_filter). NaN (including the padding
-// past the row end) never passes.
-__device__ __forceinline__ uint32_t value_bits(const float (&v)[SEL_U][4], float thr) {
+// Three-input minimum (a NaN operand is ignored, as with fminf).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// v[t] for a lane-dependent t (0..31) by a 5-level select tree (no local memory).
+__device__ __forceinline__ float select32f(const float (&v)[32], int t) {
+    float a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = (t & 16) ? v[i + 16] : v[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (t & 8) ? a[i + 8] : a[i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = (t & 4) ? a[i + 4] : a[i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) a[i] = (t & 2) ? a[i + 2] : a[i];
+    return (t & 1) ? a[1] : a[0];
+}
+
+// Survivor bits of a lane's 32 values of a step (bit 4u + c), value <= thr, the
+// excluded self column cleared. NaN never passes.
+__device__ __forceinline__ uint32_t step_bits(const float (&v)[32], float thr, int64_t base, int64_t self_col) {
     uint32_t m = 0;
 #pragma unroll
-    for (int u = 0; u < SEL_U; ++u)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) m |= (v[u][c] <= thr) ? (1u << (u * 4 + c)) : 0u;
+    for (int i = 0; i < 32; ++i) m |= (v[i] <= thr) ? (1u << i) : 0u;
+    const uint64_t off = static_cast<uint64_t>(self_col - base);
+    if (off < static_cast<uint64_t>(STEP) && static_cast<uint32_t>((off & 127) >> 2) == lane_id())
+        m &= ~(1u << (((off >> 7) << 2) + (off & 3)));
     return m;
 }
 
-// Clears the bit of the excluded self column.
-__device__ __forceinline__ uint32_t clear_self(uint32_t m, int64_t base, int64_t self_col) {
-    if (self_col >= base && self_col < base + 32 * 4 * SEL_U) {
-        const int64_t off = self_col - base;
-        const int64_t q = off >> 2;
-        if ((q & 31) == lane_id()) m &= ~(1u << ((q >> 5) * 4 + (off & 3)));
-    }
-    return m;
-}
-
-template <bool VEC>
-__device__ __forceinline__ void load_step(const float* rowp, int64_t N, int64_t base, float (&v)[SEL_U][4]) {
-    const uint32_t lane = lane_id();
-#pragma unroll
-    for (int u = 0; u < SEL_U; ++u) load_group<VEC>(rowp, N, base + (static_cast<int64_t>(u) * 32 + lane) * 4, v[u]);
-}
-
-// Fast path of a mid-row shrink of A[0, n) (shared memory): a 32-key sample of the
-// values, sorted across the lanes, proposes thresholds; the smallest sample value with at
-// least rkm values at or below it and at least rk at or below it minus the window is
-// taken (so it is >= max(v_rkm, v_rk + window)), clamped by tau, and the keys above it are
+// Fast path of a shrink of A[0, n) (shared memory): a 32-key sample of the values,
+// sorted across the lanes, proposes thresholds; the smallest sample value with at least
+// rkm values at or below it and at least rk at or below it minus the window is taken (so
+// it is >= max(v_rkm, v_rk + window)), clamped by tau, and the keys above it are
 // compacted away in place with ballot/popc. Returns false, leaving A untouched, when no
 // sample value passes or more than keep_max keys would remain.
 __device__ __forceinline__ bool shrink_fast(uint64_t* A, int& n, uint64_t& tau, int rk, int rkm, float window,
@@ -135,12 +151,25 @@ __device__ __forceinline__ bool shrink_fast(uint64_t* A, int& n, uint64_t& tau, 
     return true;
 }
 
-// Streams one row, keeping keys <= tau in A (shrinking it when an insertion would
-// overflow). The next step's loads are issued before the current step is filtered;
-// survivors are inserted one per lane and round at ballot/popc offsets. With spec,
-// shrinks aim at speculative ranks (spec_rank) and spec_used records that one of them
-// lowered the threshold. Returns false on a reference-list overflow. n, tau, truncated
-// are updated in place.
+// The exact quick multi-select shrink (out of line: rare).
+__device__ __noinline__ bool shrink_exact(const RowBuffers& rb, int& n, uint64_t& tau, int rk, int rkm, float window,
+                                          int keep_mid, int trunc_mid, bool& truncated) {
+    __syncwarp();
+    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, rk, rkm, window, tau, keep_mid, trunc_mid);
+    if (!r.ok) return false;
+    n = r.n;
+    tau = r.tau;
+    truncated |= r.truncated;
+    return true;
+}
+
+// Streams one row, keeping keys <= tau in A. The next step's loads are issued before the
+// current step is filtered. Per step a lane takes the minimum of its 32 values and one
+// warp vote decides whether any lane may hold a survivor; only then are survivor bits
+// built and inserted, one per lane and round at ballot/popc offsets, the buffer shrunk
+// first whenever a round could overflow it (speculative ranks while only part of the
+// row has been seen). Returns false on a reference-list overflow. n, tau, truncated are
+// updated in place.
 template <bool VEC, bool CHECK_NAN>
 __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
                                          int bufk, int k, int km, float window, bool spec, int& n, uint64_t& tau,
@@ -149,72 +178,65 @@ __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t s
     const uint32_t lt = lanemask_lt();
     const int keep_mid = bufk - 160 > km ? bufk - 160 : km;
     const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
-    constexpr int STEP = 32 * 4 * SEL_U;
     float thr = tau_filter(tau);
-    float cur[SEL_U][4], nxt[SEL_U][4];
+    float cur[4 * SEL_U], nxt[4 * SEL_U];
     load_step<VEC>(rowp, N, 0, cur);
     for (int64_t base = 0; base < N; base += STEP) {
         if (base + STEP < N) load_step<VEC>(rowp, N, base + STEP, nxt);
         if (CHECK_NAN) {
+            bool bad = false;
+            if (base + STEP <= N) {
 #pragma unroll
-            for (int u = 0; u < SEL_U; ++u)
+                for (int i = 0; i < 32; ++i) bad |= cur[i] != cur[i];
+            } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    nan_seen |= (cur[u][c] != cur[u][c]) &&
-                                (base + (static_cast<int64_t>(u) * 32 + lane) * 4 + c < N);
+                for (int i = 0; i < 32; ++i)
+                    bad |= (cur[i] != cur[i]) && (base + ((i >> 2) * 32 + lane) * 4 + (i & 3) < N);
+            }
+            nan_seen |= bad;
         }
-        uint32_t m = clear_self(value_bits(cur, thr), base, self_col);
-        if (__any_sync(0xffffffffu, m != 0)) {
+        float m[11];
 #pragma unroll
-            for (int u = 0; u < SEL_U; ++u) {
-                uint32_t mu = (m >> (u * 4)) & 0xfu;
-                uint32_t tot = __reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mu)));
-                if (tot == 0) continue;
-                if (n + static_cast<int>(tot) > bufk) {
-                    // full: shrink (speculative ranks while only part of the row has been seen)
-                    const int64_t seen = base + static_cast<int64_t>(u) * 128;
-                    const int rk = spec ? spec_rank(k, seen, N) : k;
-                    const int rkm = spec ? spec_rank(km, seen, N) : km;
+        for (int i = 0; i < 10; ++i) m[i] = min3f(cur[3 * i], cur[3 * i + 1], cur[3 * i + 2]);
+        m[10] = fminf(cur[30], cur[31]);
+        const float mn = fminf(min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
+                               fminf(m[9], m[10]));
+        if (__any_sync(0xffffffffu, mn <= thr)) {
+            uint32_t mask = step_bits(cur, thr, base, self_col);
+            while (__any_sync(0xffffffffu, mask != 0u)) {
+                if (n + 32 > bufk) {
+                    // a round could overflow the buffer: shrink first
+                    const int rk = spec ? spec_rank(k, base, N) : k;
+                    const int rkm = spec ? spec_rank(km, base, N) : km;
                     const uint64_t before = tau;
-                    if (!shrink_fast(rb.A, n, tau, rk, rkm, window, keep_mid)) {
-                        __syncwarp();
-                        CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, rk, rkm, window, tau,
-                                                      keep_mid, trunc_mid);
-                        if (!r.ok) return false;
-                        n = r.n;
-                        tau = r.tau;
-                        truncated |= r.truncated;
-                    }
+                    if (!shrink_fast(rb.A, n, tau, rk, rkm, window, keep_mid) &&
+                        !shrink_exact(rb, n, tau, rk, rkm, window, keep_mid, trunc_mid, truncated))
+                        return false;
                     if ((rk < k || rkm < km) && tau < before) spec_used = true;
                     thr = tau_filter(tau);
-                    m = clear_self(value_bits(cur, thr), base, self_col);
-                    mu = (m >> (u * 4)) & 0xfu;
+                    mask &= step_bits(cur, thr, base, self_col);
+                    continue;
                 }
-                // insertion rounds: each lane with survivors left places one per round
-                const uint32_t rounds = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mu)));
-                const int64_t idx4 = base + (static_cast<int64_t>(u) * 32 + lane) * 4;
-                for (uint32_t r = 0; r < rounds; ++r) {
-                    const int e = (__ffs(mu) - 1) & 3;
-                    const bool has = mu != 0u;
-                    mu &= mu - 1u;
-                    const float v = (e & 2) ? ((e & 1) ? cur[u][3] : cur[u][2]) : ((e & 1) ? cur[u][1] : cur[u][0]);
-                    const uint32_t b = __ballot_sync(0xffffffffu, has);
-                    if (has) rb.A[n + __popc(b & lt)] = make_key(v, static_cast<uint32_t>(idx4 + e));
-                    n += __popc(b);
-                }
+                const int t = (__ffs(mask) - 1) & 31;
+                const bool has = mask != 0u;
+                mask &= mask - 1u;
+                const float v = select32f(cur, t);
+                const uint32_t b = __ballot_sync(0xffffffffu, has);
+                if (has)
+                    rb.A[n + __popc(b & lt)] =
+                        make_key(v, static_cast<uint32_t>(base + ((t >> 2) * 32 + lane) * 4 + (t & 3)));
+                n += __popc(b);
             }
         }
 #pragma unroll
-        for (int u = 0; u < SEL_U; ++u)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) cur[u][c] = nxt[u][c];
+        for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
     }
     __syncwarp();
     return true;
 }
 
 template <bool VEC, bool CHECK_NAN, bool TOPK>
-__global__ void __launch_bounds__(256, 3) select_rows_kernel(SelectParams p, int bufk, int64_t self_offset, int32_t* __restrict__ out_idx,
+__global__ void __launch_bounds__(256, 2) select_rows_kernel(SelectParams p, int bufk, int64_t self_offset, int32_t* __restrict__ out_idx,
                                    float* __restrict__ out_val) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = static_cast<int>(threadIdx.x / 32);
