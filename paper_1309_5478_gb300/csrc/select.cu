@@ -151,25 +151,15 @@ __device__ __forceinline__ bool shrink_fast(uint64_t* A, int& n, uint64_t& tau, 
     return true;
 }
 
-// The exact quick multi-select shrink (out of line: rare).
-__device__ __noinline__ bool shrink_exact(const RowBuffers& rb, int& n, uint64_t& tau, int rk, int rkm, float window,
-                                          int keep_mid, int trunc_mid, bool& truncated) {
-    __syncwarp();
-    CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, rk, rkm, window, tau, keep_mid, trunc_mid);
-    if (!r.ok) return false;
-    n = r.n;
-    tau = r.tau;
-    truncated |= r.truncated;
-    return true;
-}
-
 // Streams one row, keeping keys <= tau in A. The next step's loads are issued before the
 // current step is filtered. Per step a lane takes the minimum of its 32 values and one
 // warp vote decides whether any lane may hold a survivor; only then are survivor bits
 // built and inserted, one per lane and round at ballot/popc offsets, the buffer shrunk
 // first whenever a round could overflow it (speculative ranks while only part of the
-// row has been seen). Returns false on a reference-list overflow. n, tau, truncated are
-// updated in place.
+// row has been seen). When the sampled shrink cannot decide, the scan leaves its loop,
+// runs the exact quick multi-select and resumes the same step with the survivor bits it
+// had not inserted yet (the hot loop holds no call). Returns false on a reference-list
+// overflow. n, tau, truncated are updated in place.
 template <bool VEC, bool CHECK_NAN>
 __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t self_col, const RowBuffers& rb,
                                          int bufk, int k, int km, float window, bool spec, int& n, uint64_t& tau,
@@ -180,38 +170,52 @@ __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t s
     const int trunc_mid = (bufk / 2) > km ? bufk / 2 : km;
     float thr = tau_filter(tau);
     float cur[4 * SEL_U], nxt[4 * SEL_U];
-    load_step<VEC>(rowp, N, 0, cur);
-    for (int64_t base = 0; base < N; base += STEP) {
-        if (base + STEP < N) load_step<VEC>(rowp, N, base + STEP, nxt);
-        if (CHECK_NAN) {
-            bool bad = false;
-            if (base + STEP <= N) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) bad |= cur[i] != cur[i];
+    int64_t base = 0;
+    uint32_t pending = 0;  // survivor bits of step `base` left when the scan stopped for an exact shrink
+    bool resume = false;
+    while (base < N) {
+        bool need_exact = false;
+        int rk = k, rkm = km;
+        load_step<VEC>(rowp, N, base, cur);
+        for (; base < N; base += STEP) {
+            if (base + STEP < N) load_step<VEC>(rowp, N, base + STEP, nxt);
+            uint32_t mask;
+            if (resume) {
+                mask = pending & step_bits(cur, thr, base, self_col);
+                resume = false;
             } else {
+                if (CHECK_NAN) {
+                    bool bad = false;
+                    if (base + STEP <= N) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    bad |= (cur[i] != cur[i]) && (base + ((i >> 2) * 32 + lane) * 4 + (i & 3) < N);
+                        for (int i = 0; i < 32; ++i) bad |= cur[i] != cur[i];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            bad |= (cur[i] != cur[i]) && (base + ((i >> 2) * 32 + lane) * 4 + (i & 3) < N);
+                    }
+                    nan_seen |= bad;
+                }
+                float m[11];
+#pragma unroll
+                for (int i = 0; i < 10; ++i) m[i] = min3f(cur[3 * i], cur[3 * i + 1], cur[3 * i + 2]);
+                m[10] = fminf(cur[30], cur[31]);
+                const float mn = fminf(
+                    min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
+                    fminf(m[9], m[10]));
+                mask = __any_sync(0xffffffffu, mn <= thr) ? step_bits(cur, thr, base, self_col) : 0u;
             }
-            nan_seen |= bad;
-        }
-        float m[11];
-#pragma unroll
-        for (int i = 0; i < 10; ++i) m[i] = min3f(cur[3 * i], cur[3 * i + 1], cur[3 * i + 2]);
-        m[10] = fminf(cur[30], cur[31]);
-        const float mn = fminf(min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
-                               fminf(m[9], m[10]));
-        if (__any_sync(0xffffffffu, mn <= thr)) {
-            uint32_t mask = step_bits(cur, thr, base, self_col);
             while (__any_sync(0xffffffffu, mask != 0u)) {
                 if (n + 32 > bufk) {
                     // a round could overflow the buffer: shrink first
-                    const int rk = spec ? spec_rank(k, base, N) : k;
-                    const int rkm = spec ? spec_rank(km, base, N) : km;
+                    rk = spec ? spec_rank(k, base, N) : k;
+                    rkm = spec ? spec_rank(km, base, N) : km;
                     const uint64_t before = tau;
-                    if (!shrink_fast(rb.A, n, tau, rk, rkm, window, keep_mid) &&
-                        !shrink_exact(rb, n, tau, rk, rkm, window, keep_mid, trunc_mid, truncated))
-                        return false;
+                    if (!shrink_fast(rb.A, n, tau, rk, rkm, window, keep_mid)) {
+                        need_exact = true;
+                        pending = mask;
+                        break;
+                    }
                     if ((rk < k || rkm < km) && tau < before) spec_used = true;
                     thr = tau_filter(tau);
                     mask &= step_bits(cur, thr, base, self_col);
@@ -227,9 +231,22 @@ __device__ __forceinline__ bool scan_row(const float* rowp, int64_t N, int64_t s
                         make_key(v, static_cast<uint32_t>(base + ((t >> 2) * 32 + lane) * 4 + (t & 3)));
                 n += __popc(b);
             }
-        }
+            if (need_exact) break;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
+            for (int i = 0; i < 32; ++i) cur[i] = nxt[i];
+        }
+        if (!need_exact) break;
+        // exact quick multi-select shrink, then resume step `base` with the pending bits
+        __syncwarp();
+        const uint64_t before = tau;
+        CompactResult r = compact_row(rb.A, rb.B, rb.seg_s, rb.seg_e, n, rk, rkm, window, tau, keep_mid, trunc_mid);
+        if (!r.ok) return false;
+        n = r.n;
+        tau = r.tau;
+        truncated |= r.truncated;
+        if ((rk < k || rkm < km) && tau < before) spec_used = true;
+        thr = tau_filter(tau);
+        resume = true;
     }
     __syncwarp();
     return true;
