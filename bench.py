@@ -215,6 +215,7 @@ def run_mlp(args):
             ms_v, st_v = timed(fn)
             sv = st_v[-1]
             variants[name] = {"ms_per_step": ms_v, "rows_per_s": n / (ms_v / 1e3), "ms_select": sv["ms_select"],
+                              "inserted_per_row": sv["candidates_inserted"] / n,
                               "ms_rerank": sv["ms_rerank"], "ms_fallback": sv["ms_fallback"],
                               "rows_fallback": int(sv["rows_fallback"])}
     finally:
@@ -242,8 +243,10 @@ def run_mlp(args):
                        "l2": "input 1.6 GB > L2: no flush needed"},
             "without_mlp": {"rows_per_s": n / (ms_without / 1e3), "ms_per_step": ms_without,
                             "candidates_per_row": s0["candidates"] / n, "ms_select": s0["ms_select"],
+                            "inserted_per_row": s0["candidates_inserted"] / n,
                             "ms_rerank": s0["ms_rerank"]},
             "with_mlp": {"candidates_per_row": s1["candidates"] / n, "ms_select": s1["ms_select"],
+                         "inserted_per_row": s1["candidates_inserted"] / n,
                          "ms_rerank": s1["ms_rerank"], "ms_fallback": s1["ms_fallback"],
                          "threshold_misses": int(s1["threshold_misses"]),
                          "rows_uncertified": int(s1["rows_uncertified"]), "rows_fallback": int(s1["rows_fallback"])},
@@ -572,7 +575,8 @@ def main():
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "exactness": {"rows_uncertified": int(s0["rows_uncertified"]), "rows_fallback": int(s0["rows_fallback"]),
                           "rows_fp64_ties": int(s0["rows_fp64_ties"]), "rows_truncated": int(s0["rows_truncated"]),
-                          "candidates_per_row": s0["candidates"] / max(1, s0["rows"])},
+                          "candidates_per_row": s0["candidates"] / max(1, s0["rows"]),
+                          "inserted_per_row": s0["candidates_inserted"] / max(1, s0["rows"])},
             "phases_ms": {"prep": s0["ms_prep"], "gemm_select": s0["ms_select"], "rerank": s0["ms_rerank"],
                           "fallback": s0["ms_fallback"], "gemm": s0["ms_gemm"]}}
 

@@ -82,6 +82,8 @@ typedef struct knn_stats {
     int32_t fused_used;        /* 1 when the select ran inside the GEMM epilogue */
     int32_t exact_arithmetic;  /* 1 when the inputs made the GEMM exact (integer-valued, small) */
     int32_t list_capacity;     /* candidate-list capacity per row of the first pass (largest in a batch) */
+    int64_t candidates_inserted; /* fused form: keys the running thresholds let into candidate lists
+                                    during the sweep (the select's work), summed over rows */
 } knn_stats;
 
 typedef struct knn_options {

@@ -397,6 +397,7 @@ void fill_stats(knn_stats* stats, const Problem& pb, const RerankCounters& hc, i
     stats->rows_fallback = fallback;
     stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
     stats->threshold_misses = static_cast<int64_t>(hc.threshold_miss);
+    stats->candidates_inserted = static_cast<int64_t>(hc.inserted);
     stats->precision_used = prec;
     stats->fused_used = fused;
     stats->kernel_launches = tm.launches;
@@ -739,6 +740,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.flags = flags;
     fp.status = L.status;
     fp.scratch = scratch;
+    fp.inserted = &L.counters->inserted;
     fp.stages = stages;
     fp.cap_max = cap;
     fp.n_items = static_cast<int32_t>(nrb);

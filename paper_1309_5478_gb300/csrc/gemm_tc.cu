@@ -619,7 +619,7 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 template <int P>
 __device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
                                              int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt,
-                                             int base, int dir) {
+                                             int base, int dir, uint32_t& inserted) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 c = reinterpret_cast<const float4*>(cn)[q];
@@ -662,6 +662,7 @@ __device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn,
     const uint64_t ds = static_cast<uint64_t>(self - j0);
     if (ds < 32u) mask &= ~(1u << ds);
     const uint32_t rounds = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask)));
+    inserted += static_cast<uint32_t>(__popc(mask));
     const uint32_t jlo = static_cast<uint32_t>(j0);
     for (uint32_t it = 0; it < rounds; ++it) {
         const int t = (__ffs(mask) - 1) & 31;
@@ -847,6 +848,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         es.B = reinterpret_cast<uint32_t*>(es.scratch);
         int tile = 0;
         bool ok = true;
+        uint32_t inserted = 0;  // this lane's insertions (its rows)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item p = get_item<BATCHED>(params, &tmA, &tmB, it);
             const int rb = p.rb;
@@ -912,10 +914,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tmem_ld32(taddr + hs * 64, ra);
                     tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
                     filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf, my_cnt,
-                                    seg_base, seg_dir);
+                                    seg_base, seg_dir, inserted);
                     tmem_ld_wait();
                     filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self, tau_f,
-                                    gbuf, my_cnt, seg_base, seg_dir);
+                                    gbuf, my_cnt, seg_base, seg_dir, inserted);
                     if (hs == 1) {
                         // accumulator and staged norms of this tile no longer needed by this warp
                         tc_fence_before();
@@ -988,6 +990,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             pair_barrier(quarter);
         }
         if (!ok && lane == 0) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
+        if (params.inserted) {
+            const uint32_t w = __reduce_add_sync(0xffffffffu, inserted);
+            if (lane == 0 && w) atomicAdd(params.inserted, static_cast<unsigned long long>(w));
+        }
     }
 
     tc_fence_before();

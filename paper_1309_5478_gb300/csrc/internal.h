@@ -42,7 +42,8 @@ struct RerankCounters {
     unsigned long long uncertified;
     unsigned long long truncated;
     unsigned long long threshold_miss;
-    unsigned long long pad[3];
+    unsigned long long inserted;  // keys the fused sweep appended to candidate lists
+    unsigned long long pad[2];
 };
 
 // ---- prep / bounds (prep.cu) ----

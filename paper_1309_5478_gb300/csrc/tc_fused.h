@@ -54,6 +54,7 @@ struct FusedParams {
     uint32_t* flags;           // M
     int* status;               // device status word (0, or KNN_ETIMEOUT)
     uint64_t* scratch;         // fused_scratch_words(cap_max, grid) words of global scratch
+    unsigned long long* inserted;  // optional: keys appended to candidate lists, summed over rows
     int32_t stages;            // shared-memory pipeline depth (fused_stages)
     int32_t cap_max;           // largest list capacity of the launch (sizes shared memory)
     int32_t n_items;           // work items: row blocks of the problem, or entries of `work`

@@ -149,3 +149,21 @@ def test_threshold_below_the_answer_falls_back_exactly(precision):
     torch.cuda.synchronize()
     assert torch.equal(i0, i1) and torch.equal(d0, d1)
     assert s1["threshold_misses"] > 0
+
+
+def test_learned_threshold_cuts_the_select_work(monkeypatch):
+    # what the trained network gains over the method without it: with the plain running
+    # threshold (no speculation), the keys the fused sweep lets into candidate lists, with and
+    # without the learned per-row thresholds, on the same clustered points; answers identical
+    monkeypatch.setenv("KNN_SPECULATE", "0")
+    X = inputs.anisotropic_mixture(n=20000, d=128, components=16, seed=48)
+    k = 50
+    thr = _learned_thresholds(X, k, 4000, seed=49)
+    Xd = dev(X)
+    i0, d0, s0 = kb.knng_build(Xd, k, precision="bf16", fused=1, return_stats=True)
+    i1, d1, s1 = kb.knng_build(Xd, k, precision="bf16", fused=1, row_threshold=thr, return_stats=True)
+    torch.cuda.synchronize()
+    assert torch.equal(i0, i1) and torch.equal(d0, d1)
+    assert s0["candidates_inserted"] > 0
+    assert s1["candidates_inserted"] < 0.6 * s0["candidates_inserted"], (s0["candidates_inserted"],
+                                                                         s1["candidates_inserted"])
