@@ -137,7 +137,107 @@ __device__ __forceinline__ void prep_row(const float* __restrict__ X, int64_t ro
 
 constexpr int PREP_ROWS_PER_WARP = 16;
 
+// prep_row for rows of 16-byte aligned groups of four (d % 4 == 0, aligned X): 16-byte
+// loads and packed stores of the reduced-precision copy (8 bytes of BF16 or 4 of FP8 per
+// lane and group). BF16 needs no row scale, so one pass reads the row once; FP8 first
+// finds the row's largest magnitude. Same values and statistics as prep_row (sums in
+// another order).
 template <int P>
+__device__ __forceinline__ void prep_row_vec(const float* __restrict__ X, int64_t row, int32_t d,
+                                             float* __restrict__ norm2, float* __restrict__ res,
+                                             float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
+                                             float* __restrict__ inv_scale, RowStatsAcc& acc) {
+    const uint32_t lane = lane_id();
+    const float4* x4 = reinterpret_cast<const float4*>(X + row * static_cast<int64_t>(d));
+    const int32_t g = d / 4;                              // groups of the row
+    const int32_t gq = P == P_FP32 ? g : ldq / 4;         // groups of the padded copy
+    float s2 = 0.f, amax = 0.f, r2 = 0.f, t2 = 0.f;
+    bool bad = false, nonint = false;
+    auto stats = [&](const float4 v) {
+        const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            s2 = fmaf(e[c], e[c], s2);
+            amax = fmaxf(amax, fabsf(e[c]));
+            bad |= !isfinite(e[c]);
+            nonint |= (e[c] != rintf(e[c]));
+        }
+    };
+    if constexpr (P == P_BF16) {
+        uint2* out = reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(xq) + row * static_cast<int64_t>(ldq));
+        for (int32_t t = lane; t < gq; t += 32) {
+            const float4 v = t < g ? __ldg(x4 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            stats(v);
+            const float e[4] = {v.x, v.y, v.z, v.w};
+            uint32_t h[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const __nv_bfloat16 b = __float2bfloat16_rn(e[c]);
+                const float vq = __bfloat162float(b);
+                const float r = e[c] - vq;  // exact: vq is e rounded to fewer bits
+                r2 = fmaf(r, r, r2);
+                t2 = fmaf(vq, vq, t2);
+                h[c] = __bfloat16_as_ushort(b);
+            }
+            out[t] = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+        }
+    } else {
+        for (int32_t t = lane; t < g; t += 32) stats(__ldg(x4 + t));
+    }
+    s2 = warp_sum(s2);
+    amax = warp_maxf(amax);
+    bad = __any_sync(0xffffffffu, bad);
+    nonint = __any_sync(0xffffffffu, nonint);
+    float scale = 1.f;
+    if constexpr (P == P_FP8) {
+        // power-of-two scale putting the row's largest magnitude in (224, 448]
+        int e = 0;
+        if (amax > 0.f && isfinite(amax)) {
+            frexpf(amax / 448.f, &e);
+            e = -e;
+        }
+        scale = ldexpf(1.f, e);
+        uint32_t* out = reinterpret_cast<uint32_t*>(static_cast<unsigned char*>(xq) + row * static_cast<int64_t>(ldq));
+        for (int32_t t = lane; t < gq; t += 32) {
+            const float4 v = t < g ? __ldg(x4 + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float e4[4] = {v.x, v.y, v.z, v.w};
+            uint32_t word = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const __nv_fp8_e4m3 q(e4[c] * scale);  // saturating round-to-nearest-even
+                const float vq = static_cast<float>(q) / scale;  // scale is a power of two: exact
+                const float r = e4[c] - vq;
+                r2 = fmaf(r, r, r2);
+                t2 = fmaf(vq, vq, t2);
+                word |= static_cast<uint32_t>(q.__x) << (8 * c);
+            }
+            out[t] = word;
+        }
+    }
+    if constexpr (P != P_FP32) {
+        r2 = warp_sum(r2);
+        t2 = warp_sum(t2);
+        // upper bounds on the norms (FP32 sum and sqrt rounding absorbed by the factor)
+        const float inflate = 1.f + 0x1p-12f;
+        const float rn = sqrtf(r2) * inflate, tn = sqrtf(t2) * inflate;
+        if (lane == 0) {
+            res[row] = rn;
+            tnorm[row] = tn;
+            if (inv_scale) inv_scale[row] = 1.f / scale;
+        }
+        acc.max_res = fmaxf(acc.max_res, rn);
+        acc.max_tnorm = fmaxf(acc.max_tnorm, tn);
+    }
+    if (lane == 0) norm2[row] = s2;
+    if (!bad) {
+        acc.max_norm2 = fmaxf(acc.max_norm2, s2);
+        acc.max_abs = fmaxf(acc.max_abs, amax);
+    }
+    acc.nonfinite += bad ? 1u : 0u;
+    acc.noninteger += nonint ? 1u : 0u;
+}
+
+template <int P, bool VEC>
 __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d,
                                                    float* __restrict__ norm2, float* __restrict__ res,
                                                    float* __restrict__ tnorm, void* __restrict__ xq, int32_t ldq,
@@ -146,7 +246,12 @@ __global__ void __launch_bounds__(256) prep_kernel(const float* __restrict__ X, 
     if (r0 >= rows) return;
     const int64_t r1 = r0 + PREP_ROWS_PER_WARP < rows ? r0 + PREP_ROWS_PER_WARP : rows;
     RowStatsAcc acc;
-    for (int64_t row = r0; row < r1; ++row) prep_row<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, acc);
+    for (int64_t row = r0; row < r1; ++row) {
+        if constexpr (VEC)
+            prep_row_vec<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, acc);
+        else
+            prep_row<P>(X, row, d, norm2, res, tnorm, xq, ldq, inv_scale, acc);
+    }
     acc.flush(g, P != P_FP32);
 }
 
@@ -351,19 +456,20 @@ cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precisi
     if (rows <= 0) return cudaSuccess;
     const int warps = 8;
     const unsigned blocks = static_cast<unsigned>((rows + warps * PREP_ROWS_PER_WARP - 1) / (warps * PREP_ROWS_PER_WARP));
+    // 16-byte groups: rows of d % 4 == 0 floats from a 16-byte aligned base; the copy's rows
+    // (ldq a multiple of 64 BF16 or 128 FP8 values) are aligned for the packed stores
+    const bool vec = d % 4 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                     (precision == P_FP32 || (ldq % 4 == 0 && reinterpret_cast<uintptr_t>(xq) % 16 == 0));
+#define KNN_PREP_LAUNCH(PP)                                                                                       \
+    (vec ? prep_kernel<PP, true><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g) \
+         : prep_kernel<PP, false><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g))
     switch (precision) {
-        case P_FP32:
-            prep_kernel<P_FP32><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
-            break;
-        case P_BF16:
-            prep_kernel<P_BF16><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
-            break;
-        case P_FP8:
-            prep_kernel<P_FP8><<<blocks, warps * 32, 0, st>>>(X, rows, d, norm2, res, tnorm, xq, ldq, inv_scale, g);
-            break;
-        default:
-            return cudaErrorInvalidValue;
+        case P_FP32: KNN_PREP_LAUNCH(P_FP32); break;
+        case P_BF16: KNN_PREP_LAUNCH(P_BF16); break;
+        case P_FP8: KNN_PREP_LAUNCH(P_FP8); break;
+        default: return cudaErrorInvalidValue;
     }
+#undef KNN_PREP_LAUNCH
     return cudaGetLastError();
 }
 
