@@ -451,6 +451,23 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(value: float, world: int, device="cuda") -> float:
+    """The largest of every rank's value (the slowest rank's time); the value itself on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_rate(rows_per_rank: int, world: int, seconds_slowest: float) -> float:
+    """Whole-job rows/s of weak scaling: every rank answers rows_per_rank rows, the job ends with
+    the slowest rank."""
+    return world * rows_per_rank / seconds_slowest
+
+
 def workload_config(args, form: str) -> dict:
     return {"workload": f"k-NN graph, N={args.n} unit-norm Gaussian directions in d={args.d} with 1% exact "
                         f"duplicates, k={args.k}, squared Euclidean", "N": args.n, "d": args.d, "k": args.k,
@@ -527,13 +544,9 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms_total / args.steps
-    rows_per_s = world * args.n / (ms_step / 1000.0)
+    rows_per_s = weak_scaling_rate(args.n, world, ms_step / 1000.0)
 
     P = peaks()
     s0 = stats[-1]
@@ -604,12 +617,9 @@ def main():
         for _ in range(e_steps):
             kb.knng_build(Xh, k, out_idx=oih, out_dist=odh, precision=precision, fused=fused)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / e_steps
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        line["e2e"] = {"value": world * args.n / dt, "unit": "rows/s", "h2d_bytes_per_step": args.n * args.d * 4,
+        dt = max_over_ranks((time.perf_counter() - t0) / e_steps, world)
+        line["e2e"] = {"value": weak_scaling_rate(args.n, world, dt), "unit": "rows/s",
+                       "h2d_bytes_per_step": args.n * args.d * 4,
                        "d2h_bytes_per_step": args.n * k * 8}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
