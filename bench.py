@@ -268,7 +268,10 @@ def run_mlp(args):
             # prediction (2) kernels of every step
             "gpu_launches": int(sum(s["kernel_launches"] for s in st_with)) + args.steps * (4 + 2 * -(-n // 65536))}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample_rate(X, k, args.cpu_seconds, seed=505)
+        cb = oracle_sample_rate(X, k, args.cpu_seconds, seed=505)
+        rows, ri, rd = cb.pop("_rows"), cb.pop("_idx"), cb.pop("_dist")
+        line["cpu_baseline"] = cb
+        line["oracle_check"] = oracle_check(X, rows, oi.cpu().numpy()[rows], od.cpu().numpy()[rows], ri, rd)
     print(json.dumps(line), flush=True)
 
 
@@ -419,11 +422,38 @@ def oracle_sample_rate(X: np.ndarray, k: int, seconds: float, seed: int) -> dict
     want = max(threads, (want // threads) * threads)
     rows = inputs.sample_rows(n, want, seed=seed + 1)
     t0 = time.perf_counter()
-    oracle.knng(X, k, rows=rows)
+    ref_idx, ref_dist = oracle.knng(X, k, rows=rows)
     dt = time.perf_counter() - t0
     return {"value": len(rows) / dt, "unit": "rows/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(rows)} seeded rows of the same {n}-point graph (FP64 direct difference, qsort per row), "
-                      f"{dt:.1f} s"}
+                      f"{dt:.1f} s", "_rows": rows, "_idx": ref_idx, "_dist": ref_dist}
+
+
+def oracle_check(X: np.ndarray, rows, idx: np.ndarray, dist: np.ndarray, ref_idx, ref_dist, rel: float = 1e-5) -> dict:
+    """The engine's rows against the FP64 oracle's (same rows): distance error and the acceptance
+    rule (every oracle neighbour below tau (1 - rel) reported; every reported neighbour within
+    tau (1 + rel) in FP64; rows ascending; self absent)."""
+    max_err = 0.0
+    same = 0
+    ok = 0
+    for r, i in enumerate(rows):
+        gi, gd = idx[r].astype(np.int64), dist[r].astype(np.float64)
+        if np.array_equal(gi, ref_idx[r]):
+            same += 1
+            exact = ref_dist[r]
+        else:
+            diff = X[gi].astype(np.float64) - X[i].astype(np.float64)
+            exact = np.einsum("ij,ij->i", diff, diff)
+        err = np.abs(gd - exact) / np.maximum(exact, 1e-30)
+        err[exact == 0] = np.abs(gd[exact == 0])
+        max_err = max(max_err, float(err.max()))
+        tau = ref_dist[r, -1]
+        must = set(ref_idx[r][ref_dist[r] < tau * (1 - rel)].tolist())
+        good = (must <= set(gi.tolist()) and bool(np.all(exact <= tau * (1 + rel) + 1e-30)) and
+                bool(np.all(np.diff(gd) >= 0)) and i not in gi and float(err.max()) <= rel)
+        ok += 1 if good else 0
+    return {"rows": len(rows), "max_rel_dist_err": max_err, "rows_identical_indices": same,
+            "rows_pass_acceptance": ok}
 
 
 def run_reference(args, rank: int, world: int):
@@ -544,6 +574,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    fused_idx, fused_dist = oi.cpu().numpy(), od.cpu().numpy()
     ms_total = max_over_ranks(ev0.elapsed_time(ev1), world)
     ms_step = ms_total / args.steps
     rows_per_s = weak_scaling_rate(args.n, world, ms_step / 1000.0)
@@ -604,6 +635,23 @@ def main():
                               "single_step": True}
         line["fused_vs_plain"] = (args.n / dtp) and rows_per_s / world / (args.n / dtp)
 
+    # the FP8 e4m3 form on the same data: time, how many rows its first pass certified, fallback
+    fp8_out = None
+    if form == "fused" and not args.no_compare and rank == 0:
+        try:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s8 = step("fp8", 1)[2]
+            torch.cuda.synchronize()
+            dt8 = time.perf_counter() - t0
+            fp8_out = (oi.cpu().numpy(), od.cpu().numpy())
+            line["fp8"] = {"rows_per_s": args.n / dt8, "ms_per_step": dt8 * 1000.0, "ms_gemm": s8["ms_gemm"],
+                           "rows_certified_first_pass": int(args.n - s8["rows_uncertified"]),
+                           "rows_fallback": int(s8["rows_fallback"]), "candidates_per_row": s8["candidates"] / args.n,
+                           "single_step": True}
+        except kb.KnnError as e:
+            line["fp8"] = {"unavailable": str(e)}
+
     # end to end through the public API with host buffers (pinned)
     if not args.no_e2e:
         Xh = torch.from_numpy(X).pin_memory()
@@ -623,7 +671,13 @@ def main():
                        "d2h_bytes_per_step": args.n * k * 8}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample_rate(X, k, args.cpu_seconds, seed=77)
+        cb = oracle_sample_rate(X, k, args.cpu_seconds, seed=77)
+        rows, ri, rd = cb.pop("_rows"), cb.pop("_idx"), cb.pop("_dist")
+        line["cpu_baseline"] = cb
+        # the timed output against the FP64 oracle on the oracle's rows
+        line["oracle_check"] = oracle_check(X, rows, fused_idx[rows], fused_dist[rows], ri, rd)
+        if fp8_out is not None and "fp8" in line:
+            line["fp8"]["oracle_check"] = oracle_check(X, rows, fp8_out[0][rows], fp8_out[1][rows], ri, rd)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
