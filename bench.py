@@ -51,8 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--mode", choices=["knng", "select", "batch", "mlp"], default="knng",
+    ap.add_argument("--mode", choices=["knng", "select", "select_sweep", "batch", "mlp"], default="knng",
                     help="select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
+                         "select_sweep: the select alone over the paper's selection experiment shapes "
+                         "(n = 2^20 with Q 8..256; n Q = 2^27 with n/Q 2^-3..2^19; Q = 256 with n 2^16..2^20); "
                          "batch: 512 independent search problems of uneven shape in one graph; "
                          "mlp: k-NN graph of a 524288 x 768 anisotropic mixture, k=100, with learned per-row "
                          "thresholds against the same graph without them")
@@ -314,6 +316,76 @@ def run_select_only(args):
     print(json.dumps(line), flush=True)
 
 
+def select_sweep_shapes():
+    """(family, Q, n, k) of the paper's selection experiments: time per query against Q at
+    n = 2^20 (Fig. 8), a constant n Q = 2^27 with n / Q from 2^-3 to 2^19 (Fig. 6), and Q = 256
+    with n from 2^16 to 2^20 (Fig. 9)."""
+    out = []
+    for k in (16, 128, 1024):
+        for q in (8, 16, 32, 64, 128, 256):
+            out.append(("n=2^20", q, 1 << 20, k))
+    for k in (2, 32, 512):
+        for r in range(-3, 20, 2):
+            ln = (27 + r) // 2
+            out.append(("nQ=2^27", 1 << (27 - ln), 1 << ln, k))
+    for k in (2, 32, 1024):
+        for ln in (16, 18, 20):
+            out.append(("Q=256", 256, 1 << ln, k))
+    return out
+
+
+def run_select_sweep(args):
+    """The quick multi-select alone over the paper's selection experiment shapes, on uniform
+    random FP32 values; each call runs alone after an L2 flush (many of these matrices fit in
+    L2). ms is the device time of the select kernels (events inside the call, KNN_FLAG_TIMING),
+    ms_call the whole synchronous call from Python (launch and host overheads included). Row
+    0 of every shape is checked against a sort on the host."""
+    import torch
+    from paper_1309_5478_gb300 import binding as kb
+    P = peaks()
+    g = torch.Generator(device="cuda").manual_seed(20130906)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    clocks = ClockSampler(0)
+    clocks.start()
+    rows = []
+    for fam, q, n, k in select_sweep_shapes():
+        D = torch.rand((q, n), device="cuda", generator=g, dtype=torch.float32)
+        oi = torch.empty((q, k), dtype=torch.int32, device="cuda")
+        ov = torch.empty((q, k), dtype=torch.float32, device="cuda")
+        for _ in range(max(args.warmup, 1)):
+            kb.knn_select(D, k, out_idx=oi, out_val=ov)
+        times, dev_ms, launches = [], [], 0
+        for _ in range(max(args.steps, 3)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, st = kb.knn_select(D, k, out_idx=oi, out_val=ov, return_stats=True, timing=True)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            dev_ms.append(st["ms_select"])
+            launches = st["kernel_launches"]
+        ms_call = float(np.median(times))
+        ms = float(np.median(dev_ms))
+        r0 = D[0].cpu().numpy()
+        ref = np.lexsort((np.arange(n), r0))[:k]
+        ok = bool(np.array_equal(oi[0].cpu().numpy(), ref) and np.array_equal(ov[0].cpu().numpy(), r0[ref]))
+        gbs = (q * n * 4 + q * k * 8) / (ms / 1000.0) / 1e9
+        rows.append({"family": fam, "Q": q, "n": n, "k": k, "ms": round(ms, 4), "ms_call": round(ms_call, 4),
+                     "launches": launches,
+                     "us_per_query": round(ms * 1000.0 / q, 3), "GB_s": round(gbs, 1),
+                     "frac": round(gbs / P["hbm_gbs"], 3), "row0_exact": ok})
+        del D, oi, ov
+    clk = clocks.stop()
+    line = {"metric": "quick multi-select device time over the paper's selection shapes", "unit": "ms",
+            "higher_is_better": False, "dtype": "f32", "data": "synthetic uniform [0,1) FP32",
+            "config": {"workload": "select sweep (n=2^20 Q 8..256; nQ=2^27; Q=256 n 2^16..2^20)",
+                       "l2": "256 MB written before each timed call"},
+            "peak_hbm_gbs": P["hbm_gbs"], "peak_source": P["source"], "clocks": clk,
+            "all_row0_exact": all(r["row0_exact"] for r in rows), "shapes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -513,10 +585,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.mode in ("select", "batch", "mlp"):
+    if args.mode in ("select", "select_sweep", "batch", "mlp"):
         import torch
         torch.cuda.set_device(local)
-        {"select": run_select_only, "batch": run_batch, "mlp": run_mlp}[args.mode](args)
+        {"select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
+         "mlp": run_mlp}[args.mode](args)
         return
 
     import torch

@@ -126,6 +126,9 @@ int knn_search(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, 
  * smallest values of every row of the M x N FP32 matrix D (row stride ldd >= N
  * elements), ascending by (value, column), ties to the lower column. NaN entries
  * are rejected. out_idx (int32), out_val (FP32): M x k. Requires 1 <= k <= N.
+ * Few long rows are split into segments selected in parallel and merged (same
+ * result). opt->stats (optional): rows and kernel_launches; with KNN_FLAG_TIMING also
+ * ms_select (device time of the select kernels) and ms_total (the call's host time).
  */
 int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx, float* out_val,
                const knn_options* opt);

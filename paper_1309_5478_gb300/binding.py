@@ -213,17 +213,20 @@ def knn_search(Q, C, k: int, out_idx=None, out_dist=None, precision="auto", rera
     return (oi, od, st.as_dict()) if return_stats else (oi, od)
 
 
-def knn_select(D, k: int, n: int | None = None, out_idx=None, out_val=None, stream=None):
-    """The k smallest entries of every row of D (M x ldd; the first n columns): (idx, values)."""
+def knn_select(D, k: int, n: int | None = None, out_idx=None, out_val=None, stream=None,
+               return_stats: bool = False, timing: bool = False):
+    """The k smallest entries of every row of D (M x ldd; the first n columns): (idx, values)
+    (and the call's statistics with return_stats; timing fills ms_select and ms_total)."""
     lib = load()
     D = _as_f32(D)
     M, ldd = D.shape
     n = ldd if n is None else n
     oi = out_idx if out_idx is not None else _empty_like_out(D, (M, k), "i")
     ov = out_val if out_val is not None else _empty_like_out(D, (M, k), "f")
-    opt = make_options(stream=_stream_of(D, stream))
+    st = KnnStats() if return_stats else None
+    opt = make_options(flags=KNN_FLAG_TIMING if timing else 0, stream=_stream_of(D, stream), stats=st)
     _check(lib, lib.knn_select(_ptr(D), M, n, ldd, k, _ptr(oi), _ptr(ov), ctypes.byref(opt)))
-    return oi, ov
+    return (oi, ov, st.as_dict()) if return_stats else (oi, ov)
 
 
 def knn_select_noalloc(D, k: int, out_idx, out_val, n: int | None = None, stream=None):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -920,6 +921,66 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
     return KNN_OK;
 }
 
+// The k smallest of every row of D (M x N, row stride ldd) as sorted (index, value) pairs, and
+// each row's RowFlag bits in flags. Few long dense rows are split into S segments selected in
+// parallel (one warp per row would leave most SMs idle), whose S k answers are merged: by one
+// warp-wide sort when S k <= 1024, else by a select over their concatenation (itself split
+// again when it is long) and an index remap. With a sizing arena (ar.sizing()) only the
+// workspace is taken and nothing is launched.
+int select_rows(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* oi, float* ov,
+                uint32_t* flags, Arena& ar, cudaStream_t st, int64_t* launches) {
+    const bool run = !ar.sizing();
+    const int S = select_split_segments(M, N, ldd, k, D);
+    if (S == 1) {
+        if (!run) return KNN_OK;
+        SelectParams sp{};
+        sp.D = D;
+        sp.ldd = ldd;
+        sp.M = M;
+        sp.N = N;
+        sp.spec = select_spec(N);
+        sp.k = k;
+        sp.km = k;
+        sp.cap = k;
+        sp.flags = flags;
+        KNN_CK(launch_select_topk(sp, oi, ov, st));
+        ++*launches;
+        return KNN_OK;
+    }
+    const int64_t L = N / S, rows = M * S, width = static_cast<int64_t>(S) * k;
+    uint32_t* seg_flags = ar.take<uint32_t>(rows);
+    int32_t* seg_idx = ar.take<int32_t>(rows * k);
+    float* seg_val = ar.take<float>(rows * k);
+    int32_t* merged_col = width > 1024 ? ar.take<int32_t>(M * k) : nullptr;
+    if (run) {
+        SelectParams sp{};
+        sp.D = D;
+        sp.ldd = L;
+        sp.M = rows;
+        sp.N = L;
+        sp.spec = select_spec(L);
+        sp.k = k;
+        sp.km = k;
+        sp.cap = k;
+        sp.flags = seg_flags;
+        KNN_CK(launch_select_topk(sp, seg_idx, seg_val, st));
+        ++*launches;
+    }
+    if (width <= 1024) {
+        if (run) {
+            KNN_CK(launch_select_merge(seg_idx, seg_val, seg_flags, M, S, k, L, oi, ov, flags, st));
+            ++*launches;
+        }
+        return KNN_OK;
+    }
+    KNN_TRY(select_rows(seg_val, M, width, width, k, merged_col, ov, flags, ar, st, launches));
+    if (run) {
+        KNN_CK(launch_select_remap(merged_col, seg_idx, seg_flags, M, S, k, L, oi, flags, st));
+        ++*launches;
+    }
+    return KNN_OK;
+}
+
 }  // namespace
 
 // Recomputes the given query rows of pb exactly (the plain FP32 form over gathered rows,
@@ -1017,23 +1078,25 @@ int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int
     void *oi = nullptr, *ov = nullptr;
     KNN_TRY(sg.out(out_idx, static_cast<size_t>(M) * k * sizeof(int32_t), &oi));
     KNN_TRY(sg.out(out_val, static_cast<size_t>(M) * k * sizeof(float), &ov));
+    knn_stats* stats = opt ? opt->stats : nullptr;
+    const bool timing = stats && (opt->flags & KNN_FLAG_TIMING);
+    const auto t0 = std::chrono::steady_clock::now();
+    uint32_t* flags = nullptr;
+    int64_t launches = 0;
     Arena sz;
-    uint32_t* flags = sz.take<uint32_t>(M);
+    flags = sz.take<uint32_t>(M);
+    KNN_TRY(select_rows(static_cast<const float*>(Dd), M, N, ldd, k, nullptr, nullptr, flags, sz, st, &launches));
     void* base = nullptr;
     KNN_TRY(workspace_get(sz.used(), &base));
     Arena ar(static_cast<char*>(base), sz.used());
     flags = ar.take<uint32_t>(M);
-    SelectParams sp{};
-    sp.D = static_cast<const float*>(Dd);
-    sp.ldd = ldd;
-    sp.M = M;
-    sp.N = N;
-    sp.spec = select_spec(sp.N);
-    sp.k = k;
-    sp.km = k;
-    sp.cap = k;
-    sp.flags = flags;
-    KNN_CK(launch_select_topk(sp, static_cast<int32_t*>(oi), static_cast<float*>(ov), st));
+    Events ev;
+    KNN_TRY(ev.init(timing));
+    KNN_TRY(ev.rec(0, st));
+    launches = 0;
+    KNN_TRY(select_rows(static_cast<const float*>(Dd), M, N, ldd, k, static_cast<int32_t*>(oi), static_cast<float*>(ov),
+                        flags, ar, st, &launches));
+    KNN_TRY(ev.rec(1, st));
     std::vector<uint32_t> hf(static_cast<size_t>(M));
     KNN_CK(cudaMemcpyAsync(hf.data(), flags, M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
@@ -1041,6 +1104,16 @@ int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int
         if (hf[static_cast<size_t>(i)] & ROW_SELECT_ERROR)
             return set_error(KNN_EINVAL, "row %lld holds NaN (or the select gave up)", (long long)i);
     KNN_TRY(sg.copy_back(st));
+    if (stats) {
+        *stats = knn_stats{};
+        stats->rows = M;
+        stats->kernel_launches = launches;
+        if (timing) {
+            KNN_CK(cudaEventElapsedTime(&stats->ms_select, ev.ev[0], ev.ev[1]));
+            stats->ms_total =
+                std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
     return KNN_OK;
 }
 

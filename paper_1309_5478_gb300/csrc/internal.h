@@ -81,6 +81,21 @@ cudaError_t launch_select(const SelectParams& p, cudaStream_t st);
 // Whether rows of length N are selected with speculative thresholds (SelectParams::spec):
 // from 16384 columns on; KNN_SPECULATE=0/1 overrides.
 int select_spec(int64_t N);
+// Segments per row for a select of few long dense rows (1: no split): each row of length N is
+// selected as S rows of N / S columns, then merged by launch_select_merge.
+int select_split_segments(int64_t M, int64_t N, int64_t ldd, int32_t k, const void* D);
+// Row r's answer from its S segment answers (rows r S .. r S + S - 1 of seg_idx/seg_val, k
+// each, segment-local indices); flags[r] = OR of the segments' flags.
+cudaError_t launch_select_merge(const int32_t* seg_idx, const float* seg_val, const uint32_t* seg_flags, int64_t M,
+                                int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, float* out_val,
+                                uint32_t* flags, cudaStream_t st);
+
+// Row r's indices from a select over the concatenation of its S segment answers (M x S k
+// values): merged_col[r][i] is a column of that concatenation; out_idx[r][i] the row's global
+// column; flags[r] |= OR of the segments' flags.
+cudaError_t launch_select_remap(const int32_t* merged_col, const int32_t* seg_idx, const uint32_t* seg_flags,
+                                int64_t M, int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, uint32_t* flags,
+                                cudaStream_t st);
 
 // Select output written directly as sorted (index, value) pairs: the k smallest per row.
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st);

@@ -16,6 +16,7 @@
 // point whose exact distance can still be among the k smallest (the band argument
 // in the design notes). Output per row: the candidate keys, their count, tau
 // (every left-out key is > tau) and flags.
+#include <atomic>
 #include <cstdlib>
 
 #include "internal.h"
@@ -349,8 +350,16 @@ cudaError_t launch_variant(const SelectParams& p, int bufk, int64_t self_offset,
     if (warps < 1) warps = 1;
     const size_t smem = per_warp * warps;
     auto kern = select_rows_kernel<VEC, CHECK_NAN, TOPK>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    // the attribute is per device and only grows: set it when this device has not seen this size
+    static std::atomic<int> smem_set[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || static_cast<int>(smem) > smem_set[dev].load(std::memory_order_relaxed)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) smem_set[dev].store(static_cast<int>(smem), std::memory_order_relaxed);
+    }
     const int64_t blocks = (p.M + warps - 1) / warps;
     kern<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(p, bufk, self_offset, out_idx, out_val);
     return cudaGetLastError();
@@ -379,6 +388,110 @@ cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool ch
 }
 
 cudaError_t launch_select(const SelectParams& p, cudaStream_t st) { return launch_select_ex(p, -1, false, st); }
+
+namespace {
+// Merge of a row's S segment answers (k (value, segment-local index) pairs each) into the
+// row's k smallest: one warp per row sorts the S k keys (value, global index) in shared
+// memory; the order is the unsplit select's order.
+__global__ void select_merge_kernel(const int32_t* __restrict__ seg_idx, const float* __restrict__ seg_val,
+                                    const uint32_t* __restrict__ seg_flags, int64_t M, int32_t S, int32_t k,
+                                    int64_t seg_len, int32_t P, int32_t* __restrict__ out_idx,
+                                    float* __restrict__ out_val, uint32_t* __restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = static_cast<int>(threadIdx.x / 32);
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + warp;
+    if (row >= M) return;
+    const uint32_t lane = lane_id();
+    uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * P;
+    const int n = S * k;
+    uint32_t fl = 0;
+    for (int i = static_cast<int>(lane); i < P; i += 32) {
+        if (i < n) {
+            const int s = i / k;
+            const int64_t src = (row * S + s) * static_cast<int64_t>(k) + (i - s * k);
+            const int32_t j = seg_idx[src];
+            K[i] = j < 0 ? KEY_MAX : make_key(seg_val[src], static_cast<uint32_t>(j + s * seg_len));
+        } else {
+            K[i] = KEY_MAX;
+        }
+    }
+    for (int s = static_cast<int>(lane); s < S; s += 32) fl |= seg_flags[row * S + s];
+    fl = __reduce_or_sync(0xffffffffu, fl);
+    __syncwarp();
+    warp_bitonic_sort_smem(K, P);
+    for (int i = static_cast<int>(lane); i < k; i += 32) {
+        const bool have = K[i] != KEY_MAX;
+        out_idx[row * k + i] = have ? static_cast<int32_t>(key_idx(K[i])) : -1;
+        out_val[row * k + i] = have ? key_val(K[i]) : F_INF;
+    }
+    if (lane == 0) flags[row] = fl;
+}
+}  // namespace
+
+namespace {
+// Row r's answer from a select over the concatenation of its S segment answers: column c of
+// that concatenation is entry c mod k of segment c / k, whose segment-local index gets the
+// segment's offset. The concatenation keeps equal values in increasing global index order,
+// so the lower-index tie rule carries over.
+__global__ void select_remap_kernel(const int32_t* __restrict__ merged_col, const int32_t* __restrict__ seg_idx,
+                                    const uint32_t* __restrict__ seg_flags, int64_t M, int32_t S, int32_t k,
+                                    int64_t seg_len, int32_t* __restrict__ out_idx, uint32_t* __restrict__ flags) {
+    const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+    if (row >= M) return;
+    const uint32_t lane = lane_id();
+    for (int i = static_cast<int>(lane); i < k; i += 32) {
+        const int32_t c = merged_col[row * k + i];
+        int32_t j = -1;
+        if (c >= 0) {
+            const int32_t s = c / k;
+            const int32_t js = seg_idx[row * S * static_cast<int64_t>(k) + c];
+            j = js < 0 ? -1 : static_cast<int32_t>(js + s * seg_len);
+        }
+        out_idx[row * k + i] = j;
+    }
+    uint32_t fl = 0;
+    for (int s = static_cast<int>(lane); s < S; s += 32) fl |= seg_flags[row * S + s];
+    fl = __reduce_or_sync(0xffffffffu, fl);
+    if (lane == 0) flags[row] |= fl;
+}
+}  // namespace
+
+cudaError_t launch_select_remap(const int32_t* merged_col, const int32_t* seg_idx, const uint32_t* seg_flags,
+                                int64_t M, int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, uint32_t* flags,
+                                cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const int warps = 8;
+    select_remap_kernel<<<static_cast<unsigned>((M + warps - 1) / warps), warps * 32, 0, st>>>(
+        merged_col, seg_idx, seg_flags, M, S, k, seg_len, out_idx, flags);
+    return cudaGetLastError();
+}
+
+int select_split_segments(int64_t M, int64_t N, int64_t ldd, int32_t k, const void* D) {
+    // few rows: one warp per row would leave most of the GPU idle (the paper switches to a
+    // thread block per row for few queries); dense rows split into S equal segments
+    constexpr int64_t WARPS_WANTED = 152 * 16;
+    if (ldd != N || M * 4 >= WARPS_WANTED || reinterpret_cast<uintptr_t>(D) % 16 != 0) return 1;
+    int S = 1;
+    while (S < 64 && M * S * 2 <= WARPS_WANTED && N % (2 * S) == 0 && (N / (2 * S)) % 4 == 0 &&
+           N / (2 * S) >= 8192 && N / (2 * S) >= 8 * static_cast<int64_t>(k))
+        S *= 2;
+    return S;
+}
+
+cudaError_t launch_select_merge(const int32_t* seg_idx, const float* seg_val, const uint32_t* seg_flags, int64_t M,
+                                int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, float* out_val,
+                                uint32_t* flags, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    const int P = pow2_ceil(S * k > 32 ? S * k : 32);
+    const int warps = 4;
+    const size_t smem = static_cast<size_t>(warps) * P * 8;
+    cudaError_t e = cudaFuncSetAttribute(select_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    select_merge_kernel<<<static_cast<unsigned>((M + warps - 1) / warps), warps * 32, smem, st>>>(
+        seg_idx, seg_val, seg_flags, M, S, k, seg_len, P, out_idx, out_val, flags);
+    return cudaGetLastError();
+}
 
 int select_spec(int64_t N) {
     if (const char* e = std::getenv("KNN_SPECULATE")) return std::atoi(e) != 0 && N >= 2 * 32 * 4 * SEL_U ? 1 : 0;

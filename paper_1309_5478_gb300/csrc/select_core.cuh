@@ -96,6 +96,13 @@ __device__ __forceinline__ K warp_sort32(K v) {
     return v;
 }
 
+// Integer mixing (xorshift-multiply rounds) for pivot positions.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x = (x ^ (x >> 16)) * 0x7feb352du;
+    x = (x ^ (x >> 15)) * 0x846ca68bu;
+    return x ^ (x >> 16);
+}
+
 template <typename K>
 __device__ __forceinline__ K median3(K a, K b, K c) {
     K lo = a < b ? a : b, hi = a < b ? b : a;
@@ -147,7 +154,10 @@ __device__ K warp_rank_select(K* a, K* b, int n, int r) {
             v = warp_sort32(v);
             return shfl_key(v, r - lo);
         }
-        const K pivot = median3(src[lo], src[lo + len / 2], src[hi - 1]);
+        const uint32_t h0 = mix32(static_cast<uint32_t>(lo) * 0x9e3779b1u + static_cast<uint32_t>(hi) +
+                                  static_cast<uint32_t>(guard) * 0x85ebca6bu);
+        const uint32_t ul = static_cast<uint32_t>(len);
+        const K pivot = median3(src[lo + h0 % ul], src[lo + mix32(h0) % ul], src[lo + mix32(h0 ^ 0x5bd1e995u) % ul]);
         int nlt, neq;
         partition3(src, dst, lo, hi, pivot, nlt, neq);
         if (r < lo + nlt) {
@@ -222,7 +232,14 @@ __device__ __forceinline__ bool seg_rank(SegRefs& s, uint64_t* A, uint64_t* B, i
             return true;
         }
         if (s.count + 2 > SEG_MAX) return false;
-        const uint64_t pivot = median3(src[st], src[st + len / 2], src[en - 1]);
+        // median of three keys at hashed positions: fixed positions (first, middle, last) meet
+        // structured rows (sorted runs, sawtooth) with a pivot near the segment's minimum at
+        // every step, and the reference list overflows
+        const uint32_t h0 = mix32(static_cast<uint32_t>(st) * 0x9e3779b1u + static_cast<uint32_t>(en) +
+                                  static_cast<uint32_t>(guard) * 0x85ebca6bu);
+        const uint32_t h1 = mix32(h0), h2 = mix32(h0 ^ 0x5bd1e995u);
+        const uint32_t ul = static_cast<uint32_t>(len);
+        const uint64_t pivot = median3(src[st + h0 % ul], src[st + h1 % ul], src[st + h2 % ul]);
         int nlt, neq;
         partition3(src, dst, st, en, pivot, nlt, neq);  // neq == 1: keys are unique
         const uint32_t where = (ef & SEG_IN_B) ? 0u : SEG_IN_B;

@@ -145,12 +145,19 @@ def test_select_ties_and_ragged_ldd():
         assert np.array_equal(idx[r], order)
 
 
-@pytest.mark.parametrize("pattern", ["ascending", "descending", "constant", "sawtooth"])
+def _sorted_runs(n, run, seed):
+    # concatenated ascending runs of random values (the shape of merged per-segment answers)
+    v = inputs.uniform_matrix(1, n, seed=seed)[0]
+    return np.concatenate([np.sort(v[i:i + run]) for i in range(0, n, run)])
+
+
+@pytest.mark.parametrize("pattern", ["ascending", "descending", "constant", "sawtooth", "runs256", "runs2048"])
 def test_select_adversarial_orders(pattern):
     n = 20000
     base = np.arange(n, dtype=np.float32)
     row = {"ascending": base, "descending": base[::-1].copy(), "constant": np.zeros(n, np.float32),
-           "sawtooth": (base % 97).astype(np.float32)}[pattern]
+           "sawtooth": (base % 97).astype(np.float32), "runs256": _sorted_runs(n, 256, 46),
+           "runs2048": _sorted_runs(n, 2048, 47)}[pattern]
     D = np.stack([row, row[::-1].copy()])
     idx, val = kb.knn_select(dev(D), 300)
     idx = idx.cpu().numpy()
@@ -185,3 +192,44 @@ def test_select_speculation_on_off(spec, monkeypatch):
         for r in range(0, D.shape[0], 7):
             order = np.lexsort((np.arange(D.shape[1]), D[r]))[:64]
             assert np.array_equal(idx[r], order) and np.array_equal(val[r], D[r][order])
+
+
+def _check_rows_sorted(D, idx, val, k, rows):
+    for r in rows:
+        order = np.lexsort((np.arange(D.shape[1]), D[r]))[:k]
+        assert np.array_equal(idx[r], order) and np.array_equal(val[r], D[r][order]), r
+
+
+@pytest.mark.parametrize("m,n,k", [(8, 1 << 20, 64), (1, 1 << 20, 1), (37, 1 << 18, 256), (3, 65536 + 256, 16),
+                                   (120, 1 << 19, 8), (8, 1 << 20, 1024), (2, 1 << 20, 700), (256, 1 << 20, 1024),
+                                   (32, 1 << 20, 128), (64, 1 << 20, 128)])
+def test_select_few_long_rows(m, n, k):
+    # the paper's selection experiment shape: few rows of up to 2^20 uniform values; rows
+    # this few are split into segments selected in parallel and merged (a warp-wide sort for
+    # short merges, a select over the concatenated segment answers, split again, for long)
+    D = inputs.uniform_matrix(m, n, seed=40 + m)
+    idx, val, st = kb.knn_select(dev(D), k, return_stats=True, timing=True)
+    _check_rows_sorted(D, idx.cpu().numpy(), val.cpu().numpy(), k, range(0, m, max(1, m // 16)))
+    assert st["rows"] == m and st["kernel_launches"] >= 2 and st["ms_select"] > 0
+    oi = torch.empty((m, k), dtype=torch.int32, device="cuda")
+    ov = torch.empty((m, k), dtype=torch.float32, device="cuda")
+    kb.knn_select_noalloc(dev(D), k, oi, ov)
+    assert np.array_equal(oi.cpu().numpy(), idx.cpu().numpy())
+
+
+def test_select_few_long_rows_ties_across_segments():
+    # integer values 0..3 over 2^20 columns: the k smallest are all ties at 0, spread over
+    # every segment; the merge must keep the lowest column indices
+    m, n, k = 4, 1 << 20, 200
+    D = inputs.integer_lattice(n=m, d=n, lo=0, hi=3, seed=44)
+    D[2, :] = 5.0
+    D[2, n - 300:] = 1.0  # the answer sits in the last segment
+    idx, val = kb.knn_select(dev(D), k)
+    _check_rows_sorted(D, idx.cpu().numpy(), val.cpu().numpy(), k, range(m))
+
+
+def test_select_few_long_rows_nan_rejected():
+    D = inputs.uniform_matrix(2, 1 << 20, seed=45)
+    D[1, 700001] = np.nan
+    with pytest.raises(kb.KnnError):
+        kb.knn_select(dev(D), 4)
