@@ -97,6 +97,10 @@ cudaError_t launch_select_remap(const int32_t* merged_col, const int32_t* seg_id
                                 int64_t M, int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, uint32_t* flags,
                                 cudaStream_t st);
 
+// Smallest k whose sorted select (launch_select_topk) runs one CTA per row instead of one
+// warp (256; KNN_SELECT_BLOCK_K overrides, 0 = never).
+int select_block_k();
+
 // Select output written directly as sorted (index, value) pairs: the k smallest per row.
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st);
 

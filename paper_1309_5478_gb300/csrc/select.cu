@@ -470,9 +470,10 @@ int select_split_segments(int64_t M, int64_t N, int64_t ldd, int32_t k, const vo
     // few rows: one warp per row would leave most of the GPU idle (the paper switches to a
     // thread block per row for few queries); dense rows split into S equal segments
     constexpr int64_t WARPS_WANTED = 152 * 16;
-    if (ldd != N || M * 4 >= WARPS_WANTED || reinterpret_cast<uintptr_t>(D) % 16 != 0) return 1;
+    const int64_t wr = (select_block_k() > 0 && k >= select_block_k()) ? 8 : 1;  // warps per row
+    if (ldd != N || M * wr * 4 >= WARPS_WANTED || reinterpret_cast<uintptr_t>(D) % 16 != 0) return 1;
     int S = 1;
-    while (S < 64 && M * S * 2 <= WARPS_WANTED && N % (2 * S) == 0 && (N / (2 * S)) % 4 == 0 &&
+    while (S < 64 && M * wr * S * 2 <= WARPS_WANTED && N % (2 * S) == 0 && (N / (2 * S)) % 4 == 0 &&
            N / (2 * S) >= 8192 && N / (2 * S) >= 8 * static_cast<int64_t>(k))
         S *= 2;
     return S;
@@ -498,8 +499,317 @@ int select_spec(int64_t N) {
     return N >= 16384 ? 1 : 0;
 }
 
+namespace {
+// ---------------------------------------------------------------------------
+// Block-per-row select (the paper's variant for long rows and few queries): the
+// BW warps of a CTA share one candidate buffer, so a large k costs one buffer per
+// row instead of one per warp.
+// ---------------------------------------------------------------------------
+constexpr int BW = 8;          // warps per row
+constexpr int BSEG_MAX = 48;   // kept-part references before they are gathered back into A
+
+struct BlockShared {
+    int cnt[BW];               // per-warp counts (survivors, or keys < pivot in a partition)
+    int cnt2[BW];              // keys > pivot in a partition
+    int seg_lo[BSEG_MAX];      // kept position ranges whose keys live in B
+    int seg_hi[BSEG_MAX];
+    uint64_t key;              // broadcast of a selected key
+    uint32_t nan;
+};
+
+__host__ __device__ constexpr size_t block_smem_bytes(int bufk) {
+    return static_cast<size_t>(bufk) * 16 + sizeof(BlockShared);
+}
+
+int block_bufk(int k) {
+    int want = 2 * k + 288;
+    if (want < k + STEP) want = k + STEP;
+    return pow2_ceil(want);
+}
+
+// Gathers the kept ranges recorded in B back into A (positions unchanged).
+__device__ __forceinline__ void block_gather_segments(uint64_t* A, const uint64_t* B, BlockShared& sh, int nseg) {
+    for (int t = 0; t < nseg; ++t)
+        for (int i = sh.seg_lo[t] + static_cast<int>(threadIdx.x); i < sh.seg_hi[t]; i += blockDim.x) A[i] = B[i];
+}
+
+// Block-wide quick multi-select: afterwards A[0, r + 1) holds the r + 1 smallest keys of
+// A[0, n) (unique keys, any order); returns the largest of them (rank r). Each step
+// partitions the live range around a pivot into the other array: every warp counts the
+// keys below and above the pivot in its slice, an inter-warp prefix of the counts gives
+// each warp its write offsets, and the warp writes with ballot/popc (smaller keys from
+// the left end, larger from the right end). Recursion continues on the side holding
+// rank r; a left part that stays kept is recorded by reference, not copied. All threads
+// of the block call it.
+__device__ uint64_t block_select_prefix(uint64_t* A, uint64_t* B, int n, int r, BlockShared& sh) {
+    const int warp = static_cast<int>(threadIdx.x >> 5);
+    const uint32_t lane = lane_id();
+    const uint32_t lt_mask = lanemask_lt();
+    int lo = 0, hi = n, nseg = 0;
+    bool in_b = false;
+    uint64_t result = KEY_MAX;
+    for (int guard = 0; guard < 1 << 20; ++guard) {
+        const int len = hi - lo;
+        uint64_t* src = in_b ? B : A;
+        uint64_t* dst = in_b ? A : B;
+        if (len <= 32) {
+            if (warp == 0) {
+                uint64_t v = static_cast<int>(lane) < len ? src[lo + lane] : KEY_MAX;
+                v = warp_sort32(v);
+                if (static_cast<int>(lane) < len) src[lo + lane] = v;
+                const uint64_t kr = shfl_u64(v, r - lo);
+                if (lane == 0) sh.key = kr;
+            }
+            if (in_b && threadIdx.x == 0) {
+                sh.seg_lo[nseg] = lo;
+                sh.seg_hi[nseg] = r + 1;
+            }
+            nseg += in_b ? 1 : 0;
+            __syncthreads();
+            result = sh.key;
+            break;
+        }
+        const uint32_t h0 = mix32(static_cast<uint32_t>(lo) * 0x9e3779b1u + static_cast<uint32_t>(hi) +
+                                  static_cast<uint32_t>(guard) * 0x85ebca6bu);
+        const uint32_t ul = static_cast<uint32_t>(len);
+        const uint64_t pivot =
+            median3(src[lo + h0 % ul], src[lo + mix32(h0) % ul], src[lo + mix32(h0 ^ 0x5bd1e995u) % ul]);
+        const int cs = ((len + BW - 1) / BW + 31) & ~31;
+        const int w0 = lo + warp * cs;
+        const int w1 = min(hi, w0 + cs);
+        int nl = 0, ng = 0;
+        for (int i = w0 + static_cast<int>(lane); i < w1; i += 32) {
+            const uint64_t v = src[i];
+            nl += v < pivot ? 1 : 0;
+            ng += v > pivot ? 1 : 0;
+        }
+        nl = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(nl)));
+        ng = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(ng)));
+        if (lane == 0) {
+            sh.cnt[warp] = nl;
+            sh.cnt2[warp] = ng;
+        }
+        __syncthreads();
+        int off_l = 0, off_g = 0, tot_l = 0;
+#pragma unroll
+        for (int w = 0; w < BW; ++w) {
+            off_l += w < warp ? sh.cnt[w] : 0;
+            off_g += w < warp ? sh.cnt2[w] : 0;
+            tot_l += sh.cnt[w];
+        }
+        int wl = lo + off_l, wg = hi - 1 - off_g;
+        for (int i0 = w0; i0 < w1; i0 += 32) {
+            const int i = i0 + static_cast<int>(lane);
+            const uint64_t v = i < w1 ? src[i] : pivot;
+            const bool l = i < w1 && v < pivot;
+            const bool g = i < w1 && v > pivot;
+            const uint32_t bl = __ballot_sync(0xffffffffu, l);
+            const uint32_t bg = __ballot_sync(0xffffffffu, g);
+            if (l) dst[wl + __popc(bl & lt_mask)] = v;
+            if (g) dst[wg - __popc(bg & lt_mask)] = v;
+            if (i < w1 && v == pivot) dst[lo + tot_l] = v;
+            wl += __popc(bl);
+            wg -= __popc(bg);
+        }
+        __syncthreads();
+        const int m = lo + tot_l;  // the pivot's position (its rank)
+        if (r < m) {
+            hi = m;
+            in_b = !in_b;
+            continue;
+        }
+        // [lo, m] is kept; it lives in dst
+        if (!in_b) {  // dst is B
+            if (threadIdx.x == 0) {
+                sh.seg_lo[nseg] = lo;
+                sh.seg_hi[nseg] = m + 1;
+            }
+            ++nseg;
+        }
+        if (r == m) {
+            result = pivot;
+            break;
+        }
+        lo = m + 1;
+        in_b = !in_b;
+        if (nseg == BSEG_MAX) {
+            __syncthreads();
+            block_gather_segments(A, B, sh, nseg);
+            nseg = 0;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    block_gather_segments(A, B, sh, nseg);
+    __syncthreads();
+    return result;
+}
+
+// Ascending bitonic sort of A[0, P) by the whole block (P a power of two).
+__device__ __forceinline__ void block_bitonic_sort(uint64_t* A, int P) {
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = static_cast<int>(threadIdx.x); i < (P >> 1); i += blockDim.x) {
+                const int pos = 2 * i - (i & (stride - 1));
+                const int other = pos + stride;
+                const bool up = (pos & size) == 0;
+                const uint64_t a = A[pos], b = A[other];
+                if ((a > b) == up) {
+                    A[pos] = b;
+                    A[other] = a;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// Inserts a warp's survivor bits at A[at, ...) (ballot/popc offsets, one key per lane and round).
+__device__ __forceinline__ void block_insert(uint64_t* A, const float (&cur)[32], uint32_t mask, int at, int64_t base) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    while (__any_sync(0xffffffffu, mask != 0u)) {
+        const int t = (__ffs(mask) - 1) & 31;
+        const bool has = mask != 0u;
+        mask &= mask - 1u;
+        const float v = select32f(cur, t);
+        const uint32_t b = __ballot_sync(0xffffffffu, has);
+        if (has) A[at + __popc(b & lt)] = make_key(v, static_cast<uint32_t>(base + ((t >> 2) * 32 + lane) * 4 + (t & 3)));
+        at += __popc(b);
+    }
+}
+
+// The k smallest of each row as sorted (index, value) pairs; one CTA of BW warps per row.
+// A chunk of BW steps is filtered against the running threshold (the k-th smallest key
+// so far), all warps' survivors are inserted at once when they fit, else warp by warp
+// with a block-wide select in between; the row ends with a select of rank k - 1 and a
+// block bitonic sort. Later chunks only hold larger columns, as the threshold filter needs.
+template <bool VEC>
+__global__ void __launch_bounds__(BW * 32) select_block_rows_kernel(SelectParams p, int bufk, int32_t* __restrict__ out_idx,
+                                                                   float* __restrict__ out_val) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* A = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* B = A + bufk;
+    BlockShared& sh = *reinterpret_cast<BlockShared*>(B + bufk);
+    const int warp = static_cast<int>(threadIdx.x >> 5);
+    const uint32_t lane = lane_id();
+    const int64_t row = blockIdx.x;
+    const float* rowp = p.D + row * p.ldd;
+    const int64_t N = p.N;
+    const int k = p.k;
+    if (threadIdx.x == 0) sh.nan = 0;
+    int n = 0;
+    float thr = F_INF;
+    bool nan_seen = false;
+    for (int64_t cbase = 0; cbase < N; cbase += static_cast<int64_t>(BW) * STEP) {
+        const int64_t base = cbase + static_cast<int64_t>(warp) * STEP;
+        float cur[4 * SEL_U];
+        uint32_t mask = 0;
+        if (base < N) {
+            load_step<VEC>(rowp, N, base, cur);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+                nan_seen |= (cur[i] != cur[i]) && (base + ((i >> 2) * 32 + lane) * 4 + (i & 3) < N);
+            mask = step_bits(cur, thr, base, -1);
+        }
+        int c = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask))));
+        if (lane == 0) sh.cnt[warp] = c;
+        __syncthreads();
+        int total = 0;
+#pragma unroll
+        for (int w = 0; w < BW; ++w) total += sh.cnt[w];
+        if (n + total > bufk && n > k) {
+            // shrink first, then filter the chunk again with the tighter threshold
+            __syncthreads();  // every warp has read the counts the select overwrites
+            const uint64_t tau = block_select_prefix(A, B, n, k - 1, sh);
+            n = k;
+            thr = tau_filter(tau);
+            if (base < N) mask &= step_bits(cur, thr, base, -1);
+            c = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask))));
+            if (lane == 0) sh.cnt[warp] = c;
+            __syncthreads();
+            total = 0;
+#pragma unroll
+            for (int w = 0; w < BW; ++w) total += sh.cnt[w];
+        }
+        if (n + total <= bufk) {
+            int at = n;
+#pragma unroll
+            for (int w = 0; w < BW; ++w) at += w < warp ? sh.cnt[w] : 0;
+            block_insert(A, cur, mask, at, base);
+            n += total;
+        } else {
+            // a loose threshold (the row's first chunks): warp by warp, shrinking in between
+            for (int w = 0; w < BW; ++w) {
+                int cw = sh.cnt[w];
+                if (n + cw > bufk) {
+                    __syncthreads();
+                    const uint64_t tau = block_select_prefix(A, B, n, k - 1, sh);
+                    n = k;
+                    thr = tau_filter(tau);
+                    if (base < N) mask &= step_bits(cur, thr, base, -1);
+                    c = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask))));
+                    if (lane == 0 && warp >= w) sh.cnt[warp] = c;
+                    __syncthreads();
+                    cw = sh.cnt[w];
+                }
+                if (warp == w) {
+                    block_insert(A, cur, mask, n, base);
+                    mask = 0;
+                }
+                n += cw;
+            }
+        }
+        __syncthreads();
+    }
+    if (__any_sync(0xffffffffu, nan_seen) && lane == 0) atomicOr(&sh.nan, 1u);
+    if (n > k) {
+        block_select_prefix(A, B, n, k - 1, sh);
+        n = k;
+    }
+    const int P = pow2_ceil(n > 1 ? n : 1);
+    for (int i = n + static_cast<int>(threadIdx.x); i < P; i += blockDim.x) A[i] = KEY_MAX;
+    __syncthreads();
+    block_bitonic_sort(A, P);
+    for (int i = static_cast<int>(threadIdx.x); i < k; i += blockDim.x) {
+        const bool have = i < n;
+        out_idx[row * k + i] = have ? static_cast<int32_t>(key_idx(A[i])) : -1;
+        out_val[row * k + i] = have ? key_val(A[i]) : F_INF;
+    }
+    if (threadIdx.x == 0) p.flags[row] = sh.nan ? ROW_SELECT_ERROR : 0u;
+}
+
+template <bool VEC>
+cudaError_t launch_block_variant(const SelectParams& p, int bufk, int32_t* out_idx, float* out_val, cudaStream_t st) {
+    const size_t smem = block_smem_bytes(bufk);
+    auto kern = select_block_rows_kernel<VEC>;
+    static std::atomic<int> smem_set[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || static_cast<int>(smem) > smem_set[dev].load(std::memory_order_relaxed)) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) smem_set[dev].store(static_cast<int>(smem), std::memory_order_relaxed);
+    }
+    kern<<<static_cast<unsigned>(p.M), BW * 32, smem, st>>>(p, bufk, out_idx, out_val);
+    return cudaGetLastError();
+}
+}  // namespace
+
+int select_block_k() {
+    const char* e = std::getenv("KNN_SELECT_BLOCK_K");
+    return e ? std::atoi(e) : 256;
+}
+
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
+    const bool vec4 = (p.ldd % 4 == 0) && (reinterpret_cast<uintptr_t>(p.D) % 16 == 0);
+    const int bk = select_block_k();
+    if (bk > 0 && p.k >= bk && !p.E && !p.thr && !p.self_col && p.M <= 0x7fffffff) {
+        const int bufk = block_bufk(p.k);
+        return vec4 ? launch_block_variant<true>(p, bufk, out_idx, out_val, st)
+                    : launch_block_variant<false>(p, bufk, out_idx, out_val, st);
+    }
     const int bufk = choose_bufk(p.k, p.k);
     const bool vec = (p.ldd % 4 == 0) && (reinterpret_cast<uintptr_t>(p.D) % 16 == 0);
     return vec ? launch_variant<true, true, true>(p, bufk, -1, out_idx, out_val, st)
