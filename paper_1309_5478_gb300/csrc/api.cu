@@ -939,6 +939,7 @@ int select_rows(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, in
         sp.M = M;
         sp.N = N;
         sp.spec = select_spec(N);
+        sp.block = select_prefers_block(M, k) ? 1 : 0;
         sp.k = k;
         sp.km = k;
         sp.cap = k;
@@ -959,6 +960,7 @@ int select_rows(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, in
         sp.M = rows;
         sp.N = L;
         sp.spec = select_spec(L);
+        sp.block = select_prefers_block(M, k) ? 1 : 0;
         sp.k = k;
         sp.km = k;
         sp.cap = k;

@@ -76,6 +76,7 @@ struct SelectParams {
     uint32_t* flags;       // M: RowFlag bits
     const int32_t* self_col;  // per-row excluded column (or nullptr)
     int32_t spec;          // 1: speculative thresholds while streaming a row (rows they fail are redone)
+    int32_t block;         // 1: one CTA per row (sorted select only; see select_prefers_block)
 };
 cudaError_t launch_select(const SelectParams& p, cudaStream_t st);
 // Whether rows of length N are selected with speculative thresholds (SelectParams::spec):
@@ -97,9 +98,12 @@ cudaError_t launch_select_remap(const int32_t* merged_col, const int32_t* seg_id
                                 int64_t M, int32_t S, int32_t k, int64_t seg_len, int32_t* out_idx, uint32_t* flags,
                                 cudaStream_t st);
 
-// Smallest k whose sorted select (launch_select_topk) runs one CTA per row instead of one
-// warp (256; KNN_SELECT_BLOCK_K overrides, 0 = never).
+// Smallest k whose sorted select runs one CTA per row instead of one warp (128;
+// KNN_SELECT_BLOCK_K overrides: 0 = never, 1 = always).
 int select_block_k();
+// Whether a sorted select of M rows takes one CTA per row: for k >= select_block_k(), and
+// for at most 64 rows (one warp per row leaves the GPU idle there, even after a split).
+bool select_prefers_block(int64_t M, int32_t k);
 
 // Select output written directly as sorted (index, value) pairs: the k smallest per row.
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st);

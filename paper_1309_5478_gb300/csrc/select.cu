@@ -27,6 +27,7 @@ namespace {
 
 constexpr int SEL_U = 8;                 // 16-byte loads per lane per step
 constexpr int STEP = 32 * 4 * SEL_U;     // values per warp and step
+constexpr int BW = 8;                    // warps per row of the block-per-row select
 
 struct RowBuffers {
     uint64_t* A;
@@ -470,7 +471,7 @@ int select_split_segments(int64_t M, int64_t N, int64_t ldd, int32_t k, const vo
     // few rows: one warp per row would leave most of the GPU idle (the paper switches to a
     // thread block per row for few queries); dense rows split into S equal segments
     constexpr int64_t WARPS_WANTED = 152 * 16;
-    const int64_t wr = (select_block_k() > 0 && k >= select_block_k()) ? 8 : 1;  // warps per row
+    const int64_t wr = select_prefers_block(M, k) ? BW : 1;  // warps per row
     if (ldd != N || M * wr * 4 >= WARPS_WANTED || reinterpret_cast<uintptr_t>(D) % 16 != 0) return 1;
     int S = 1;
     while (S < 64 && M * wr * S * 2 <= WARPS_WANTED && N % (2 * S) == 0 && (N / (2 * S)) % 4 == 0 &&
@@ -505,7 +506,6 @@ namespace {
 // BW warps of a CTA share one candidate buffer, so a large k costs one buffer per
 // row instead of one per warp.
 // ---------------------------------------------------------------------------
-constexpr int BW = 8;          // warps per row
 constexpr int BSEG_MAX = 48;   // kept-part references before they are gathered back into A
 
 struct BlockShared {
@@ -798,14 +798,18 @@ cudaError_t launch_block_variant(const SelectParams& p, int bufk, int32_t* out_i
 
 int select_block_k() {
     const char* e = std::getenv("KNN_SELECT_BLOCK_K");
-    return e ? std::atoi(e) : 256;
+    return e ? std::atoi(e) : 128;
+}
+
+bool select_prefers_block(int64_t M, int32_t k) {
+    const int bk = select_block_k();
+    return bk > 0 && (k >= bk || M <= 64);
 }
 
 cudaError_t launch_select_topk(const SelectParams& p, int32_t* out_idx, float* out_val, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
     const bool vec4 = (p.ldd % 4 == 0) && (reinterpret_cast<uintptr_t>(p.D) % 16 == 0);
-    const int bk = select_block_k();
-    if (bk > 0 && p.k >= bk && !p.E && !p.thr && !p.self_col && p.M <= 0x7fffffff) {
+    if (p.block && !p.E && !p.thr && !p.self_col && p.M <= 0x7fffffff) {
         const int bufk = block_bufk(p.k);
         return vec4 ? launch_block_variant<true>(p, bufk, out_idx, out_val, st)
                     : launch_block_variant<false>(p, bufk, out_idx, out_val, st);

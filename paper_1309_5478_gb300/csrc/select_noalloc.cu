@@ -98,6 +98,7 @@ extern "C" int knn_select_noalloc(const float* D, int64_t M, int64_t N, int64_t 
     sp.M = M;
     sp.N = N;
     sp.spec = select_spec(sp.N);
+    sp.block = select_prefers_block(M, k) ? 1 : 0;
     sp.k = k;
     sp.km = k;
     sp.cap = k;
