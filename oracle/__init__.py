@@ -32,7 +32,7 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
         tmp = out + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, "-o", tmp, src], check=True)
+        subprocess.run(["gcc", *CFLAGS, "-o", tmp, src, "-lm"], check=True)
         os.replace(tmp, out)
     return out
 
@@ -51,6 +51,13 @@ def load(path: str | None = None):
         f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                       ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
                       ctypes.c_void_p]
+        g = lib.oracle_knn_sim_rows
+        g.restype = ctypes.c_int
+        g.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                      ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                      ctypes.c_void_p, ctypes.c_void_p]
+        lib.oracle_similarity.restype = ctypes.c_double
+        lib.oracle_similarity.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]
         lib.oracle_threads.restype = ctypes.c_int
         lib.oracle_sqdist.restype = ctypes.c_double
         lib.oracle_sqdist.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]
@@ -99,3 +106,44 @@ def sqdist(x: np.ndarray, y: np.ndarray) -> float:
     x = np.ascontiguousarray(x, dtype=np.float32)
     y = np.ascontiguousarray(y, dtype=np.float32)
     return float(load().oracle_sqdist(x.ctypes.data, y.ctypes.data, x.shape[0]))
+
+
+METRICS = {"cosine": 0, "pearson": 1}
+
+
+def knn_sim(Q: np.ndarray, C: np.ndarray, k: int, metric: str, rows=None, exclude_self: bool = False, lib=None):
+    """k most similar rows of ``C`` by cosine or Pearson similarity, for the query rows ``rows``.
+
+    Returns ``(idx, sim)``: int64 and float64 arrays of shape (len(rows), k), descending by
+    similarity, ties to the lower index. Raises ValueError on a zero-norm (centred) row.
+    """
+    lib = lib or load()
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    C = np.ascontiguousarray(C, dtype=np.float32)
+    assert Q.ndim == 2 and C.ndim == 2 and Q.shape[1] == C.shape[1]
+    M, d = Q.shape
+    N = C.shape[0]
+    if rows is None:
+        rows = np.arange(M, dtype=np.int64)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    idx = np.empty((len(rows), k), dtype=np.int64)
+    sim = np.empty((len(rows), k), dtype=np.float64)
+    rc = lib.oracle_knn_sim_rows(Q.ctypes.data, M, C.ctypes.data, N, d, k, METRICS[metric], rows.ctypes.data,
+                                 len(rows), 1 if exclude_self else 0, idx.ctypes.data, sim.ctypes.data)
+    if rc == -2:
+        raise ValueError("a row has zero norm (after centring): the similarity is undefined")
+    if rc != 0:
+        raise ValueError("oracle_knn_sim_rows rejected its arguments")
+    return idx, sim
+
+
+def knng_sim(X: np.ndarray, k: int, metric: str, rows=None, lib=None):
+    """Similarity graph rows: ``knn_sim(X, X, k, metric, rows, exclude_self=True)``."""
+    return knn_sim(X, X, k, metric, rows=rows, exclude_self=True, lib=lib)
+
+
+def similarity(x: np.ndarray, y: np.ndarray, metric: str) -> float:
+    """FP64 cosine or Pearson similarity of two FP32 vectors (NaN for a zero norm)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    return float(load().oracle_similarity(x.ctypes.data, y.ctypes.data, x.shape[0], METRICS[metric]))

@@ -195,8 +195,124 @@ def pin_pythagorean(lib):
     assert list(dist[0]) == [1.0, 25.0, 25.0, 169.0, 169.0, 289.0]
 
 
+SIM_GOLDEN = (("hand_cosine_search.txt", "cosine"), ("hand_pearson_search.txt", "pearson"))
+
+
+def pin_sim_hand_examples(lib):
+    """Hand-worked cosine and Pearson searches: exact order, similarities to 1e-15."""
+    for name, metric in SIM_GOLDEN:
+        g = read_golden(name)
+        idx, sim = oracle.knn_sim(g["queries"], g["points"], g["k"], metric, lib=lib)
+        assert np.array_equal(idx, g["idx"]), (name, idx, g["idx"])
+        assert np.allclose(sim, g["dist"], rtol=0, atol=1e-15), (name, sim, g["dist"])
+
+
+def _rational_key(q, c, centered):
+    """Exact order key of the cosine (centred: Pearson) of two integer vectors:
+    sign(dot) dot^2 / (|q|^2 |c|^2) as a Fraction (monotone in the similarity)."""
+    from fractions import Fraction
+    d = len(q)
+    if centered:
+        mq, mc = Fraction(sum(q), d), Fraction(sum(c), d)
+        q = [Fraction(v) - mq for v in q]
+        c = [Fraction(v) - mc for v in c]
+    dot = sum(Fraction(a) * b for a, b in zip(q, c))
+    nq = sum(Fraction(a) * a for a in q)
+    nc = sum(Fraction(b) * b for b in c)
+    return (1 if dot >= 0 else -1) * dot * dot / (nq * nc)
+
+
+def pin_sim_rational_bruteforce(lib):
+    """Integer inputs: the order of exact rational similarities. Where exact values tie, any
+    order of the tied points is right, so the pin checks the set of points above the k-th
+    value, that every reported point is at least the k-th value, and the similarity values."""
+    cases = [(14, 3, 5, 0), (19, 4, 7, 1), (25, 2, 9, 0), (11, 5, 10, 1), (30, 3, 12, 1)]
+    for case, (n, d, k, centered) in enumerate(cases):
+        X = inputs.integer_lattice(n=n, d=d, lo=-3, hi=4, seed=3000 + case)
+        metric = "pearson" if centered else "cosine"
+        Xi = [[int(v) for v in row] for row in X]
+        ok = [i for i in range(n) if (len(set(Xi[i])) > 1 if centered else any(Xi[i]))]
+        Xs = X[ok]
+        Xi = [Xi[i] for i in ok]
+        idx, sim = oracle.knng_sim(Xs, k, metric, lib=lib)
+        for i in range(len(Xi)):
+            keys = {j: _rational_key(Xi[i], Xi[j], centered) for j in range(len(Xi)) if j != i}
+            kth = sorted(keys.values(), reverse=True)[k - 1]
+            above = {j for j, v in keys.items() if v > kth}
+            got = set(idx[i].tolist())
+            assert i not in got, (case, i)
+            assert above <= got, (case, i, above - got)
+            assert all(keys[j] >= kth for j in got), (case, i)
+            for t, j in enumerate(idx[i]):
+                v = float(np.dot(np.array(Xi[i], float) - (np.mean(Xi[i]) if centered else 0),
+                                 np.array(Xi[j], float) - (np.mean(Xi[j]) if centered else 0)))
+                v /= (np.linalg.norm(np.array(Xi[i], float) - (np.mean(Xi[i]) if centered else 0)) *
+                      np.linalg.norm(np.array(Xi[j], float) - (np.mean(Xi[j]) if centered else 0)))
+                assert abs(sim[i, t] - v) <= 1e-14, (case, i, t, sim[i, t], v)
+            assert np.all(np.diff(sim[i]) <= 0)
+
+
+def pin_sim_library(lib):
+    """Float inputs: scipy's cdist with 'cosine' and 'correlation' (1 - similarity)."""
+    from scipy.spatial.distance import cdist
+    X = inputs.gaussian_mixture(n=203, d=17, components=5, seed=41)
+    Q = inputs.gaussian_mixture(n=9, d=17, components=3, seed=42)
+    k = 13
+    for metric, sp in (("cosine", "cosine"), ("pearson", "correlation")):
+        idx, sim = oracle.knn_sim(Q, X, k, metric, lib=lib)
+        S = 1.0 - cdist(Q.astype(np.float64), X.astype(np.float64), sp)
+        for i in range(Q.shape[0]):
+            order = np.lexsort((np.arange(X.shape[0]), -S[i]))[:k]
+            assert np.allclose(sim[i], S[i, order], rtol=0, atol=1e-12), (metric, i)
+            gaps = -np.diff(np.sort(S[i])[::-1][:k + 1])
+            if np.all(gaps > 1e-10):
+                assert np.array_equal(idx[i], order), (metric, i)
+
+
+def pin_sim_invariants(lib):
+    """Scaling a corpus row by a power of two changes no similarity (cosine and Pearson);
+    adding an integer to every entry of an integer row changes no Pearson similarity (d = 8,
+    where the row mean is exact);
+    negating the corpus negates every cosine; the graph never reports a point itself."""
+    X = inputs.integer_lattice(n=60, d=6, lo=-5, hi=5, seed=51).astype(np.float32)
+    X = X[[len(set(r.tolist())) > 1 for r in X]]
+    Q = X[:7]
+    n = X.shape[0]
+    for metric in ("cosine", "pearson"):
+        base_i, base_s = oracle.knn_sim(Q, X, n, metric, lib=lib)
+        Xs = X * np.where(np.arange(n) % 3 == 0, 4.0, 0.5).astype(np.float32)[:, None]
+        i2, s2 = oracle.knn_sim(Q, Xs, n, metric, lib=lib)
+        assert np.array_equal(i2, base_i) and np.array_equal(s2, base_s), metric
+        gi, gs = oracle.knng_sim(X, 5, metric, lib=lib)
+        for i in range(n):
+            assert i not in gi[i]
+            assert np.all(np.diff(gs[i]) <= 0)
+            for a in range(4):
+                assert gs[i, a] > gs[i, a + 1] or gi[i, a] < gi[i, a + 1]
+    # d = 8: the mean of an integer row is exact, so the shifted rows centre to the same values
+    X8 = inputs.integer_lattice(n=50, d=8, lo=-5, hi=5, seed=52).astype(np.float32)
+    X8 = X8[[len(set(r.tolist())) > 1 for r in X8]]
+    i3, s3 = oracle.knn_sim(X8[:6], X8 + np.float32(7), X8.shape[0], "pearson", lib=lib)
+    pi, ps = oracle.knn_sim(X8[:6], X8, X8.shape[0], "pearson", lib=lib)
+    assert np.array_equal(i3, pi) and np.array_equal(s3, ps)
+    ci, cs = oracle.knn_sim(Q, X, n, "cosine", lib=lib)
+    ni, ns = oracle.knn_sim(Q, -X, n, "cosine", lib=lib)
+    for i in range(Q.shape[0]):
+        assert np.array_equal(np.sort(ns[i]), np.sort(-cs[i]))
+        a = {int(j): v for j, v in zip(ci[i], cs[i])}
+        b = {int(j): v for j, v in zip(ni[i], ns[i])}
+        assert all(b[j] == -a[j] for j in a)
+    try:
+        oracle.knn_sim(Q, np.zeros((3, X.shape[1]), np.float32), 2, "cosine", lib=lib)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("a zero-norm corpus row was accepted")
+
+
 ALL_PINS = (pin_hand_examples, pin_lattice, pin_bruteforce, pin_row_subset, pin_library_cdist,
-            pin_invariants, pin_full_sort, pin_pythagorean)
+            pin_invariants, pin_full_sort, pin_pythagorean, pin_sim_hand_examples, pin_sim_rational_bruteforce,
+            pin_sim_library, pin_sim_invariants)
 
 
 def failing_pins(lib) -> list[str]:
@@ -204,6 +320,6 @@ def failing_pins(lib) -> list[str]:
     for pin in ALL_PINS:
         try:
             pin(lib)
-        except (AssertionError, ValueError, IndexError):
+        except (AssertionError, ValueError, LookupError):
             failed.append(pin.__name__)
     return failed

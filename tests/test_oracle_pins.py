@@ -32,6 +32,17 @@ MUTANTS = [
      "if (x->d < y->d) return 1;\n    if (x->d > y->d) return -1;"),
     ("output shifted by one", "out_idx[r * k + t] = t < n ? pairs[t].j", "out_idx[r * k + t] = t + 1 < n ? pairs[t + 1].j"),
     ("single-precision accumulation", "double s = 0.0;", "float s = 0.0f;"),
+    ("similarity: mean added instead of subtracted", "double c = (double)x[t] - m;", "double c = (double)x[t] + m;"),
+    ("similarity: centring skipped in the dot product", "((double)x[t] - mx) * ((double)y[t] - my)",
+     "((double)x[t]) * ((double)y[t])"),
+    ("similarity: mean not divided by d", "m /= (double)d;", "m /= 1.0;"),
+    ("similarity: squared norms instead of norms", "*norm = sqrt(ss);", "*norm = ss;"),
+    ("similarity: ascending order", "pairs[n].d = -sim_pair(", "pairs[n].d = sim_pair("),
+    ("similarity: self not excluded", "                if (exclude_self && j == i) continue;\n                /*",
+     "                if (0) continue;\n                /*"),
+    ("similarity: query norm dropped", "return dot / (nx * ny);", "return dot / ny;"),
+    ("similarity: corpus statistics of the wrong row", "C + (size_t)j * (size_t)d, cm[j], cn[j], d)",
+     "C + (size_t)j * (size_t)d, cm[0], cn[0], d)"),
 ]
 
 
