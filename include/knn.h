@@ -121,6 +121,34 @@ int knng_build_ex(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_
 int knn_search(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k,
                int32_t* out_idx, float* out_dist, const knn_options* opt);
 
+/* Metrics of the paper (Methods, "Distance calculation"). */
+typedef enum knn_metric {
+    KNN_METRIC_EUCLIDEAN = 0, /* squared Euclidean distance, ascending */
+    KNN_METRIC_COSINE = 1,    /* cosine similarity x.y / (|x| |y|), descending */
+    KNN_METRIC_PEARSON = 2    /* Pearson similarity: the cosine of rows centred on their own mean */
+} knn_metric;
+
+/*
+ * k-NN search by a metric of the paper: for KNN_METRIC_EUCLIDEAN exactly knn_search
+ * (out_val = squared distances, ascending). For KNN_METRIC_COSINE and
+ * KNN_METRIC_PEARSON, out_val holds the similarities (FP32 rounding of the FP64
+ * value), each row descending by similarity, ties to the lower index; the answer is
+ * exact in FP64 arithmetic: the nearest unit rows found by the engine are re-ranked by
+ * their FP64 similarity under a certificate, and rows it does not cover are recomputed
+ * over the whole corpus in FP64. A row of zero norm (Pearson: zero norm after
+ * centring) or with a non-finite value returns KNN_EINVAL. opt->row_threshold must be
+ * NULL for the similarity metrics. opt->stats: rows_uncertified counts the rows the
+ * similarity certificate did not cover; rows_fallback adds those rows to the rows the
+ * Euclidean pass over the unit rows recomputed. Pointers, ownership and sizes as
+ * knn_search; 1 <= k <= min(N, 1024).
+ */
+int knn_search_metric(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t metric,
+                      int32_t* out_idx, float* out_val, const knn_options* opt);
+
+/* The k-NN graph of X by a metric (a point is never its own neighbour); 1 <= k <= N - 1. */
+int knng_build_metric(const float* X, int64_t N, int32_t d, int32_t k, int32_t metric, int32_t* out_idx,
+                      float* out_val, const knn_options* opt);
+
 /*
  * Quick multi-select alone (Methods, "GPU-based quick multi-select"): the k
  * smallest values of every row of the M x N FP32 matrix D (row stride ldd >= N

@@ -91,6 +91,8 @@ def load(path: str | None = None):
         lib.knng_build.argtypes = [vp, i64, i32, i32, vp, vp]
         lib.knng_build_ex.argtypes = [vp, i64, i32, i32, vp, vp, opt_p]
         lib.knn_search.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, opt_p]
+        lib.knn_search_metric.argtypes = [vp, i64, vp, i64, i32, i32, i32, vp, vp, opt_p]
+        lib.knng_build_metric.argtypes = [vp, i64, i32, i32, i32, vp, vp, opt_p]
         lib.knn_select.argtypes = [vp, i64, i64, i64, i32, vp, vp, opt_p]
         lib.knn_distances.argtypes = [vp, i64, vp, i64, i32, vp, i64, i32, opt_p]
         lib.knn_search_batched.argtypes = [ctypes.POINTER(KnnProblem), i32, opt_p]
@@ -211,6 +213,42 @@ def knn_search(Q, C, k: int, out_idx=None, out_dist=None, precision="auto", rera
                        max_workspace_bytes)
     _check(lib, lib.knn_search(_ptr(Q), M, _ptr(C), N, d, k, _ptr(oi), _ptr(od), ctypes.byref(opt)))
     return (oi, od, st.as_dict()) if return_stats else (oi, od)
+
+
+METRICS = {"euclidean": 0, "cosine": 1, "pearson": 2}
+
+
+def knn_search_metric(Q, C, k: int, metric: str, out_idx=None, out_val=None, precision="auto",
+                      rerank_extra: int = 32, flags: int = KNN_FLAG_CHECK_FINITE, stream=None,
+                      return_stats: bool = False):
+    """k most similar rows of C for every row of Q by 'cosine' or 'pearson' similarity
+    (descending; 'euclidean' gives knn_search): (idx int32 M x k, value float32 M x k)."""
+    lib = load()
+    Q = _as_f32(Q)
+    C = _as_f32(C)
+    M, d = Q.shape
+    N = C.shape[0]
+    oi = out_idx if out_idx is not None else _empty_like_out(Q, (M, k), "i")
+    ov = out_val if out_val is not None else _empty_like_out(Q, (M, k), "f")
+    st = KnnStats()
+    opt = make_options(precision, rerank_extra, -1, flags, _stream_of(Q, stream), None, st)
+    _check(lib, lib.knn_search_metric(_ptr(Q), M, _ptr(C), N, d, k, METRICS[metric], _ptr(oi), _ptr(ov),
+                                      ctypes.byref(opt)))
+    return (oi, ov, st.as_dict()) if return_stats else (oi, ov)
+
+
+def knng_build_metric(X, k: int, metric: str, out_idx=None, out_val=None, precision="auto", rerank_extra: int = 32,
+                      flags: int = KNN_FLAG_CHECK_FINITE, stream=None, return_stats: bool = False):
+    """Similarity graph of the rows of X by 'cosine' or 'pearson' ('euclidean': knng_build)."""
+    lib = load()
+    X = _as_f32(X)
+    N, d = X.shape
+    oi = out_idx if out_idx is not None else _empty_like_out(X, (N, k), "i")
+    ov = out_val if out_val is not None else _empty_like_out(X, (N, k), "f")
+    st = KnnStats()
+    opt = make_options(precision, rerank_extra, -1, flags, _stream_of(X, stream), None, st)
+    _check(lib, lib.knng_build_metric(_ptr(X), N, d, k, METRICS[metric], _ptr(oi), _ptr(ov), ctypes.byref(opt)))
+    return (oi, ov, st.as_dict()) if return_stats else (oi, ov)
 
 
 def knn_select(D, k: int, n: int | None = None, out_idx=None, out_val=None, stream=None,

@@ -921,6 +921,171 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
     return KNN_OK;
 }
 
+// Device buffers owned by one call (released when the call returns; calls are synchronous).
+struct CallBuffers {
+    std::vector<void*> ptrs;
+    ~CallBuffers() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    int take(size_t n, T** out) {
+        void* p = nullptr;
+        const size_t bytes = std::max<size_t>(n * sizeof(T), 16);
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(KNN_ENOMEM, "similarity buffers (%zu bytes): %s", bytes, cudaGetErrorString(e));
+        }
+        ptrs.push_back(p);
+        *out = static_cast<T*>(p);
+        return KNN_OK;
+    }
+};
+
+// Cosine or Pearson similarity search / graph (Methods, "Distance calculation"): unit rows
+// in FP32, the k + m nearest unit rows by the Euclidean engine, the FP64 similarity of those
+// candidates from the original rows with a certificate, and FP64 over the whole corpus for
+// the rows the certificate does not cover.
+int metric_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t metric,
+                int32_t* out_idx, float* out_val, const knn_options* opt_in, bool graph) {
+    if (metric == KNN_METRIC_EUCLIDEAN) return search_impl(Q, M, C, N, d, k, out_idx, out_val, opt_in, graph);
+    g_last_error.clear();
+    if (metric != KNN_METRIC_COSINE && metric != KNN_METRIC_PEARSON)
+        return set_error(KNN_EINVAL, "unknown metric %d", metric);
+    const knn_options opt = opt_in ? *opt_in : defaults();
+    if (opt.row_threshold) return set_error(KNN_EINVAL, "row_threshold applies to the Euclidean metric only");
+    KNN_TRY(validate_args(Q, M, C, N, d, k, out_idx, out_val, opt, graph));
+    if (M == 0) return KNN_OK;
+    const int32_t centered = metric == KNN_METRIC_PEARSON ? 1 : 0;
+    cudaStream_t st = stream_of(&opt);
+    const auto t0 = std::chrono::steady_clock::now();
+    Staged sg;
+    const void *Qd = nullptr, *Cd = nullptr;
+    KNN_TRY(sg.in(C, static_cast<size_t>(N) * d * sizeof(float), st, &Cd));
+    if (graph) {
+        Qd = Cd;
+    } else {
+        KNN_TRY(sg.in(Q, static_cast<size_t>(M) * d * sizeof(float), st, &Qd));
+    }
+    void *oi = nullptr, *ov = nullptr;
+    KNN_TRY(sg.out(out_idx, static_cast<size_t>(M) * k * sizeof(int32_t), &oi));
+    KNN_TRY(sg.out(out_val, static_cast<size_t>(M) * k * sizeof(float), &ov));
+    const int64_t avail = N - (graph ? 1 : 0);
+    const int32_t extra = std::max(opt.rerank_extra, 16);
+    const int32_t kp = static_cast<int32_t>(std::min<int64_t>({static_cast<int64_t>(k) + extra, avail, MAX_K}));
+    CallBuffers cb;
+    float *Uc = nullptr, *Uq = nullptr, *cand_dist = nullptr;
+    double *cm = nullptr, *cn = nullptr, *qm = nullptr, *qn = nullptr;
+    int32_t *bad = nullptr, *cand_idx = nullptr;
+    uint32_t* unc = nullptr;
+    KNN_TRY(cb.take(static_cast<size_t>(N) * d, &Uc));
+    KNN_TRY(cb.take(static_cast<size_t>(N), &cm));
+    KNN_TRY(cb.take(static_cast<size_t>(N), &cn));
+    if (graph) {
+        Uq = Uc;
+        qm = cm;
+        qn = cn;
+    } else {
+        KNN_TRY(cb.take(static_cast<size_t>(M) * d, &Uq));
+        KNN_TRY(cb.take(static_cast<size_t>(M), &qm));
+        KNN_TRY(cb.take(static_cast<size_t>(M), &qn));
+    }
+    KNN_TRY(cb.take(1, &bad));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * kp, &cand_idx));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * kp, &cand_dist));
+    KNN_TRY(cb.take(static_cast<size_t>(M), &unc));
+    int64_t launches = 0;
+    KNN_CK(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    KNN_CK(launch_sim_prep(static_cast<const float*>(Cd), N, d, centered, Uc, cm, cn, bad, st));
+    ++launches;
+    if (!graph) {
+        KNN_CK(launch_sim_prep(static_cast<const float*>(Qd), M, d, centered, Uq, qm, qn, bad, st));
+        ++launches;
+    }
+    int32_t hbad = 0;
+    KNN_CK(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    if (hbad)
+        return set_error(KNN_EINVAL, "a row has zero norm%s or a non-finite value: its similarity is undefined",
+                         centered ? " after centring" : "");
+    // the nearest unit rows
+    Problem pb{};
+    pb.Q = Uq;
+    pb.C = Uc;
+    pb.M = M;
+    pb.N = N;
+    pb.d = d;
+    pb.k = kp;
+    pb.m = opt.rerank_extra;
+    pb.graph = graph;
+    pb.out_idx = cand_idx;
+    pb.out_dist = cand_dist;
+    pb.slab_bytes = opt.max_workspace_bytes > 0 ? opt.max_workspace_bytes / 2 : 0;
+    pb.precision = opt.precision;
+    pb.fused = opt.fused;
+    pb.flags = opt.flags & ~KNN_FLAG_TIMING;
+    knn_stats local{};
+    knn_stats* stats = opt.stats ? opt.stats : &local;
+    std::memset(stats, 0, sizeof(*stats));
+    KNN_TRY(run_problem(pb, stats, st));
+    launches += stats->kernel_launches;
+    // FP64 similarity of the candidates, certificate
+    SimRerankParams rp{};
+    rp.Q = static_cast<const float*>(Qd);
+    rp.C = static_cast<const float*>(Cd);
+    rp.qmean = qm;
+    rp.qnorm = qn;
+    rp.cmean = cm;
+    rp.cnorm = cn;
+    rp.cand_idx = cand_idx;
+    rp.cand_dist = cand_dist;
+    rp.M = M;
+    rp.d = d;
+    rp.k = k;
+    rp.kp = kp;
+    rp.P = 32;
+    while (rp.P < kp) rp.P *= 2;
+    rp.all_candidates = kp == avail ? 1 : 0;
+    rp.margin = sim_margin(d);
+    rp.out_idx = static_cast<int32_t*>(oi);
+    rp.out_val = static_cast<float*>(ov);
+    rp.uncertified = unc;
+    KNN_CK(launch_sim_rerank(rp, centered, st));
+    ++launches;
+    std::vector<uint32_t> hu(static_cast<size_t>(M));
+    KNN_CK(cudaMemcpyAsync(hu.data(), unc, M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaStreamSynchronize(st));
+    std::vector<int32_t> rows;
+    for (int64_t i = 0; i < M; ++i)
+        if (hu[static_cast<size_t>(i)]) rows.push_back(static_cast<int32_t>(i));
+    stats->rows_uncertified = static_cast<int64_t>(rows.size());
+    if (!rows.empty() && !(opt.flags & KNN_FLAG_NO_FALLBACK)) {
+        // FP64 over the whole corpus, in batches whose scratch stays within 1 GiB
+        const int64_t per = std::max<int64_t>(1, std::min<int64_t>(static_cast<int64_t>(rows.size()),
+                                                                   (int64_t(1) << 27) / N));
+        int32_t* drows = nullptr;
+        double* scratch = nullptr;
+        KNN_TRY(cb.take(rows.size(), &drows));
+        KNN_TRY(cb.take(static_cast<size_t>(per) * N, &scratch));
+        KNN_CK(cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        for (int64_t r0 = 0; r0 < static_cast<int64_t>(rows.size()); r0 += per) {
+            const int32_t nb = static_cast<int32_t>(std::min<int64_t>(per, static_cast<int64_t>(rows.size()) - r0));
+            KNN_CK(launch_exact_rows_sim_fp64(static_cast<const float*>(Qd), static_cast<const float*>(Cd), N, d, k,
+                                              graph ? 1 : 0, centered, qm, qn, cm, cn, drows + r0, nb, scratch,
+                                              static_cast<int32_t*>(oi), static_cast<float*>(ov), st));
+            ++launches;
+        }
+        stats->rows_fallback += static_cast<int64_t>(rows.size());
+    }
+    KNN_TRY(sg.copy_back(st));
+    KNN_CK(cudaStreamSynchronize(st));
+    stats->rows = M;
+    stats->kernel_launches = launches;
+    if (opt.flags & KNN_FLAG_TIMING)
+        stats->ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return KNN_OK;
+}
+
 // The k smallest of every row of D (M x N, row stride ldd) as sorted (index, value) pairs, and
 // each row's RowFlag bits in flags. Few long dense rows are split into S segments selected in
 // parallel (one warp per row would leave most SMs idle), whose S k answers are merged: by one
@@ -1060,6 +1225,16 @@ int knng_build_ex(const float* X, int64_t N, int32_t d, int32_t k, int32_t* out_
 int knn_search(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t* out_idx,
                float* out_dist, const knn_options* opt) {
     return knn::search_impl(Q, M, C, N, d, k, out_idx, out_dist, opt, false);
+}
+
+int knn_search_metric(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t metric,
+                      int32_t* out_idx, float* out_val, const knn_options* opt) {
+    return knn::metric_impl(Q, M, C, N, d, k, metric, out_idx, out_val, opt, false);
+}
+
+int knng_build_metric(const float* X, int64_t N, int32_t d, int32_t k, int32_t metric, int32_t* out_idx,
+                      float* out_val, const knn_options* opt) {
+    return knn::metric_impl(X, N, X, N, d, k, metric, out_idx, out_val, opt, true);
 }
 
 int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx, float* out_val,

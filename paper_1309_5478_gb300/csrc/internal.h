@@ -184,9 +184,42 @@ cudaError_t launch_bounds_batched(const BatchDev* probs, const BatchSeg* segs, i
 cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
                                   int32_t cap_max, RerankCounters* counters, cudaStream_t st);
 
+// ---- cosine and Pearson similarity (metric.cu) ----
+// Per row: FP64 mean (centered) and norm of the centred row, and the FP32 unit row
+// (x - mean) / norm; *bad |= 1 for a zero, NaN or infinite norm.
+cudaError_t launch_sim_prep(const float* X, int64_t rows, int32_t d, int32_t centered, float* U, double* mean,
+                            double* norm, int32_t* bad, cudaStream_t st);
+struct SimRerankParams {
+    const float* Q;            // M x d original queries
+    const float* C;            // N x d original corpus
+    const double* qmean;
+    const double* qnorm;
+    const double* cmean;
+    const double* cnorm;
+    const int32_t* cand_idx;   // M x kp, nearest unit rows first
+    const float* cand_dist;    // M x kp, their squared distances in the unit rows
+    int64_t M;
+    int32_t d, k, kp, P;       // P = power of two >= kp
+    int32_t all_candidates;    // 1: the candidates are every point (nothing to certify)
+    double margin;             // sim_margin(d)
+    int32_t* out_idx;          // M x k
+    float* out_val;            // M x k similarities
+    uint32_t* uncertified;     // M
+};
+// Distance margin of the similarity certificate for dimension d.
+double sim_margin(int32_t d);
+cudaError_t launch_sim_rerank(const SimRerankParams& p, int32_t centered, cudaStream_t st);
+
 // Exact FP64 answer for a list of rows (last-resort path; slow, used for rows no other path certifies).
 cudaError_t launch_exact_rows_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,
                                    int32_t exclude_self, const int32_t* rows, int32_t nrows, double* scratch,
                                    int32_t* out_idx, float* out_dist, cudaStream_t st);
+// The same for cosine (centered = 0) or Pearson (centered = 1) similarity, the k most similar
+// (descending, ties to the lower index), with the means and norms of launch_sim_prep.
+cudaError_t launch_exact_rows_sim_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,
+                                       int32_t exclude_self, int32_t centered, const double* qmean,
+                                       const double* qnorm, const double* cmean, const double* cnorm,
+                                       const int32_t* rows, int32_t nrows, double* scratch, int32_t* out_idx,
+                                       float* out_val, cudaStream_t st);
 
 }  // namespace knn

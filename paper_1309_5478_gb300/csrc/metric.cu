@@ -1,0 +1,161 @@
+// Cosine and Pearson similarity (Methods, "Distance calculation": the cosine metric
+// x.y / (|x| |y|); the Pearson metric, the cosine of rows centred on their own mean).
+//
+// The k most similar points are found with the Euclidean engine: for unit vectors
+// |u - v|^2 = 2 - 2 cos(u, v), so the nearest unit rows are the most similar rows.
+//   1. sim_prep_kernel: per row, the FP64 mean (Pearson) and norm of the centred row,
+//      and the unit row u = (x - mean) / norm rounded to FP32;
+//   2. the Euclidean engine on the unit rows: the k' = k + m nearest (exact in the unit
+//      rows' arithmetic);
+//   3. sim_rerank_kernel: the FP64 similarity of every candidate from the original rows,
+//      sorted by (similarity descending, index ascending); the k best are the answer when
+//      the certificate below holds;
+//   4. rows it does not certify are recomputed over the whole corpus in FP64.
+//
+// Certificate. Let s be the FP64 similarity computed from the same means and norms as
+// the unit rows. Each unit entry carries a relative error of at most 2^-24 + 3 2^-53
+// against (x - mean) / norm, which bounds |d2(u_i, u_j) - (2 - 2 s_ij)| by
+// eta = 9 2^-24 + (4 d + 64) 2^-53. The engine reports d2 of its k'-th candidate in FP32
+// (within 2^-18 of the value it ranked by), and every other point lies at least that far.
+// So when 2 - 2 s_(k) < d2_(k') - 2^-18 - eta, no point outside the candidates can reach
+// the k-th similarity, and the answer is exact in FP64.
+#include "common.cuh"
+#include "internal.h"
+
+namespace knn {
+namespace {
+
+constexpr int RR_THREADS = 128;
+
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per row.
+__global__ void sim_prep_kernel(const float* __restrict__ X, int64_t rows, int32_t d, int32_t centered,
+                                float* __restrict__ U, double* __restrict__ mean, double* __restrict__ norm,
+                                int32_t* __restrict__ bad) {
+    const int64_t row = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (row >= rows) return;
+    const int lane = static_cast<int>(threadIdx.x & 31u);
+    const float* x = X + row * d;
+    double m = 0.0;
+    if (centered) {
+        double s = 0.0;
+        for (int t = lane; t < d; t += 32) s += static_cast<double>(x[t]);
+        m = warp_sum_f64(s) / static_cast<double>(d);
+    }
+    double ss = 0.0;
+    for (int t = lane; t < d; t += 32) {
+        const double c = static_cast<double>(x[t]) - m;
+        ss = fma(c, c, ss);
+    }
+    const double n = sqrt(warp_sum_f64(ss));
+    const bool ok = n > 0.0 && n <= 1.7976931348623157e308;  // zero norm, NaN or Inf: undefined
+    if (!ok) {
+        if (lane == 0) atomicOr(bad, 1);
+        return;
+    }
+    float* u = U + row * d;
+    for (int t = lane; t < d; t += 32) u[t] = static_cast<float>((static_cast<double>(x[t]) - m) / n);
+    if (lane == 0) {
+        mean[row] = m;
+        norm[row] = n;
+    }
+}
+
+// One block per query row: FP64 similarity of the kp candidates, sort, certificate, output.
+template <bool CENTERED>
+__global__ void __launch_bounds__(RR_THREADS) sim_rerank_kernel(SimRerankParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* S = reinterpret_cast<double*>(smem_raw);
+    int32_t* I = reinterpret_cast<int32_t*>(S + p.P);
+    const int64_t i = blockIdx.x;
+    const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31u);
+    const int nw = RR_THREADS / 32;
+    const float* q = p.Q + i * p.d;
+    const double mi = CENTERED ? p.qmean[i] : 0.0;
+    const double ni = p.qnorm[i];
+    for (int c = warp; c < p.P; c += nw) {
+        const int32_t j = c < p.kp ? p.cand_idx[i * p.kp + c] : -1;
+        double s = -__longlong_as_double(0x7ff0000000000000ll);  // -inf: no candidate
+        if (j >= 0) {
+            const float* y = p.C + static_cast<int64_t>(j) * p.d;
+            const double mj = CENTERED ? p.cmean[j] : 0.0;
+            double dot = 0.0;
+            for (int t = lane; t < p.d; t += 32) {
+                const double a = static_cast<double>(q[t]) - mi;
+                const double b = static_cast<double>(y[t]) - mj;
+                dot = fma(a, b, dot);
+            }
+            dot = warp_sum_f64(dot);
+            s = dot / (ni * p.cnorm[j]);
+        }
+        if (lane == 0) {
+            S[c] = s;
+            I[c] = j >= 0 ? j : 0x7fffffff;
+        }
+    }
+    __syncthreads();
+    // bitonic sort by (similarity descending, index ascending)
+    for (int size = 2; size <= p.P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = static_cast<int>(threadIdx.x); t < (p.P >> 1); t += RR_THREADS) {
+                const int a = 2 * t - (t & (stride - 1));
+                const int b = a + stride;
+                const bool up = (a & size) == 0;
+                const double sa = S[a], sb = S[b];
+                const int32_t ia = I[a], ib = I[b];
+                const bool a_after_b = sa < sb || (sa == sb && ia > ib);
+                if (a_after_b == up) {
+                    S[a] = sb;
+                    S[b] = sa;
+                    I[a] = ib;
+                    I[b] = ia;
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = static_cast<int>(threadIdx.x); t < p.k; t += RR_THREADS) {
+        p.out_idx[i * p.k + t] = I[t] == 0x7fffffff ? -1 : I[t];
+        p.out_val[i * p.k + t] = static_cast<float>(S[t]);
+    }
+    if (threadIdx.x == 0) {
+        bool cert = p.all_candidates != 0;
+        if (!cert) {
+            const double edge = static_cast<double>(p.cand_dist[i * p.kp + p.kp - 1]) - p.margin;
+            cert = 2.0 - 2.0 * S[p.k - 1] < edge;
+        }
+        p.uncertified[i] = cert ? 0u : 1u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sim_prep(const float* X, int64_t rows, int32_t d, int32_t centered, float* U, double* mean,
+                            double* norm, int32_t* bad, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t blocks = (rows * 32 + threads - 1) / threads;
+    sim_prep_kernel<<<static_cast<unsigned>(blocks), threads, 0, st>>>(X, rows, d, centered, U, mean, norm, bad);
+    return cudaGetLastError();
+}
+
+double sim_margin(int32_t d) {
+    // 2^-18 for the FP32 distance the engine reports, plus eta (see the header comment)
+    return 0x1p-18 + 9.0 * 0x1p-24 + (4.0 * d + 64.0) * 0x1p-53;
+}
+
+cudaError_t launch_sim_rerank(const SimRerankParams& p, int32_t centered, cudaStream_t st) {
+    if (p.M <= 0) return cudaSuccess;
+    const size_t smem = static_cast<size_t>(p.P) * (sizeof(double) + sizeof(int32_t));
+    auto kern = centered ? sim_rerank_kernel<true> : sim_rerank_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<static_cast<unsigned>(p.M), RR_THREADS, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace knn
