@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--mode", choices=["knng", "select", "select_sweep", "batch", "mlp"], default="knng",
+    ap.add_argument("--mode", choices=["knng", "select", "select_sweep", "batch", "mlp", "metric"], default="knng",
                     help="select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
+                         "metric: the cosine and Pearson similarity graphs of the headline data; "
                          "select_sweep: the select alone over the paper's selection experiment shapes "
                          "(n = 2^20 with Q 8..256; n Q = 2^27 with n/Q 2^-3..2^19; Q = 256 with n 2^16..2^20); "
                          "batch: 512 independent search problems of uneven shape in one graph; "
@@ -313,6 +314,76 @@ def run_select_only(args):
                                      if (args.q, args.cols, k) == (16384, 65536, 64) else None),
                          "kernel": "select_rows_kernel", "peak_source": P["source"]},
             "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+
+
+def run_metric(args):
+    """Cosine and Pearson similarity graphs (k most similar, FP64-exact) of the headline data,
+    timed like the Euclidean step; beside each, the Euclidean graph of the same rows already
+    normalised (the engine part of the similarity path), and a sampled check of the similarity
+    rows against the FP64 oracle."""
+    import torch
+    import oracle
+    from paper_1309_5478_gb300 import binding as kb
+    from paper_1309_5478_gb300 import inputs
+    X = workload(args.n, args.d)
+    k = args.k
+    Xd = torch.from_numpy(X).cuda()
+    oi = torch.empty((args.n, k), dtype=torch.int32, device="cuda")
+    ov = torch.empty((args.n, k), dtype=torch.float32, device="cuda")
+    out = {}
+    for metric in ("cosine", "pearson"):
+        for _ in range(args.warmup):
+            kb.knng_build_metric(Xd, k, metric, out_idx=oi, out_val=ov)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            _, _, st = kb.knng_build_metric(Xd, k, metric, out_idx=oi, out_val=ov, return_stats=True)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        clk = clocks.stop()
+        # the Euclidean graph of the unit rows alone (the same engine work)
+        Xc = X.astype(np.float64)
+        if metric == "pearson":
+            Xc = Xc - Xc.mean(axis=1, keepdims=True)
+        U = torch.from_numpy((Xc / np.linalg.norm(Xc, axis=1, keepdims=True)).astype(np.float32)).cuda()
+        kb.knng_build(U, k + 32, rerank_extra=32)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            kb.knng_build(U, k + 32, rerank_extra=32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms_unit = e0.elapsed_time(e1) / args.steps
+        del U
+        rows = inputs.sample_rows(args.n, 64, seed=606)
+        t0 = time.perf_counter()
+        ref_idx, ref_sim = oracle.knng_sim(X, k, metric, rows=rows)
+        dt = time.perf_counter() - t0
+        gi, gv = oi.cpu().numpy()[rows], ov.cpu().numpy()[rows]
+        same = int(sum(np.array_equal(gi[r].astype(np.int64), ref_idx[r]) for r in range(len(rows))))
+        max_ulps = float(max((np.max(np.abs(gv[r].astype(np.float64) - ref_sim[r]) /
+                                     np.spacing(np.abs(ref_sim[r]).astype(np.float32)).astype(np.float64))
+                              for r in range(len(rows)) if np.array_equal(gi[r].astype(np.int64), ref_idx[r])),
+                             default=float("nan")))
+        out[metric] = {"ms_per_step": ms, "rows_per_s": args.n / (ms / 1e3), "ms_euclidean_unit_rows": ms_unit,
+                       "ms_similarity_overhead": ms - ms_unit, "rows_uncertified": st["rows_uncertified"],
+                       "rows_fallback": st["rows_fallback"], "precision_used": st["precision_used"],
+                       "oracle_check": {"rows": len(rows), "rows_identical_indices": same,
+                                        "max_value_error_fp32_ulps": max_ulps},
+                       "cpu_baseline": {"value": len(rows) / dt, "unit": "rows/s", "cores": oracle.threads(),
+                                        "kind": "oracle", "sample": f"{len(rows)} seeded rows, {dt:.1f} s"},
+                       "clocks": clk}
+    line = {"metric": "exact cosine / Pearson k-NN graph rows/s", "value": out["cosine"]["rows_per_s"],
+            "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["cosine"]["ms_per_step"], "higher_is_better": True, "dtype": "bf16+f64",
+            "data": "synthetic", "config": {"workload": f"similarity graph N={args.n} d={args.d} k={k}, unit "
+                                                        "directions + 1% duplicates", "N": args.n, "d": args.d,
+                                            "k": k}, "metrics": out}
     print(json.dumps(line), flush=True)
 
 
@@ -585,11 +656,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.mode in ("select", "select_sweep", "batch", "mlp"):
+    if args.mode in ("select", "select_sweep", "batch", "mlp", "metric"):
         import torch
         torch.cuda.set_device(local)
         {"select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
-         "mlp": run_mlp}[args.mode](args)
+         "mlp": run_mlp, "metric": run_metric}[args.mode](args)
         return
 
     import torch

@@ -66,28 +66,39 @@ __global__ void sim_prep_kernel(const float* __restrict__ X, int64_t rows, int32
     }
 }
 
-// One block per query row: FP64 similarity of the kp candidates, sort, certificate, output.
-template <bool CENTERED>
+// One block per query row: FP64 similarity of the candidates, sort, certificate, output.
+// The (centred) query row is staged in shared memory as FP64 when it fits (STAGED). Each
+// reported unit-row distance is within margin of 2 - 2 s, so the k nearest candidates all
+// have s >= 1 - (d2_(k) + margin) / 2; a later candidate with d2 > d2_(k) + 2 margin has a
+// smaller s than that and cannot enter the answer: its FP64 similarity is skipped.
+template <bool CENTERED, bool STAGED>
 __global__ void __launch_bounds__(RR_THREADS) sim_rerank_kernel(SimRerankParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* S = reinterpret_cast<double*>(smem_raw);
     int32_t* I = reinterpret_cast<int32_t*>(S + p.P);
+    double* Qs = reinterpret_cast<double*>(I + p.P + (p.P & 1));
     const int64_t i = blockIdx.x;
     const int warp = static_cast<int>(threadIdx.x >> 5), lane = static_cast<int>(threadIdx.x & 31u);
     const int nw = RR_THREADS / 32;
     const float* q = p.Q + i * p.d;
     const double mi = CENTERED ? p.qmean[i] : 0.0;
     const double ni = p.qnorm[i];
+    if (STAGED) {
+        for (int t = static_cast<int>(threadIdx.x); t < p.d; t += RR_THREADS) Qs[t] = static_cast<double>(q[t]) - mi;
+        __syncthreads();
+    }
+    const double skip_above = static_cast<double>(p.cand_dist[i * p.kp + p.k - 1]) + 2.0 * p.margin;
     for (int c = warp; c < p.P; c += nw) {
-        const int32_t j = c < p.kp ? p.cand_idx[i * p.kp + c] : -1;
+        int32_t j = c < p.kp ? p.cand_idx[i * p.kp + c] : -1;
+        if (j >= 0 && c >= p.k && static_cast<double>(p.cand_dist[i * p.kp + c]) > skip_above) j = -1;
         double s = -__longlong_as_double(0x7ff0000000000000ll);  // -inf: no candidate
         if (j >= 0) {
             const float* y = p.C + static_cast<int64_t>(j) * p.d;
             const double mj = CENTERED ? p.cmean[j] : 0.0;
             double dot = 0.0;
             for (int t = lane; t < p.d; t += 32) {
-                const double a = static_cast<double>(q[t]) - mi;
-                const double b = static_cast<double>(y[t]) - mj;
+                const double a = STAGED ? Qs[t] : static_cast<double>(q[t]) - mi;
+                const double b = CENTERED ? static_cast<double>(y[t]) - mj : static_cast<double>(y[t]);
                 dot = fma(a, b, dot);
             }
             dot = warp_sum_f64(dot);
@@ -150,8 +161,12 @@ double sim_margin(int32_t d) {
 
 cudaError_t launch_sim_rerank(const SimRerankParams& p, int32_t centered, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
-    const size_t smem = static_cast<size_t>(p.P) * (sizeof(double) + sizeof(int32_t));
-    auto kern = centered ? sim_rerank_kernel<true> : sim_rerank_kernel<false>;
+    const size_t base = static_cast<size_t>(p.P) * (sizeof(double) + sizeof(int32_t)) + (p.P & 1) * sizeof(int32_t);
+    const size_t staged = base + static_cast<size_t>(p.d) * sizeof(double);
+    const bool stage = staged <= 160 * 1024;
+    const size_t smem = stage ? staged : base;
+    auto kern = centered ? (stage ? sim_rerank_kernel<true, true> : sim_rerank_kernel<true, false>)
+                         : (stage ? sim_rerank_kernel<false, true> : sim_rerank_kernel<false, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(p.M), RR_THREADS, smem, st>>>(p);
