@@ -145,6 +145,23 @@ typedef enum knn_metric {
 int knn_search_metric(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int32_t metric,
                       int32_t* out_idx, float* out_val, const knn_options* opt);
 
+/*
+ * k-NN search against a corpus larger than device memory (the paper's Discussion names
+ * corpora beyond the GPU's memory as future work). C (N x d) is read in chunks of
+ * chunk_rows rows (0: two chunks fit in a quarter of the free device memory); each chunk is
+ * searched on the device like knn_search and its answer merged into the running answer
+ * by (FP64 direct-difference distance, global index). The indices equal knn_search over
+ * the whole corpus; out_dist holds the FP32 rounding of each pair's FP64 distance (a
+ * value of the pair alone, whatever the chunking; knn_search reports its FP32 re-rank
+ * value, which can differ from it in the last bit). C may be host memory
+ * (page-locked memory lets the copy of the next chunk overlap the search of the current
+ * one) or device memory; Q and the outputs follow knn_search and must fit on the device.
+ * opt->row_threshold must be NULL. opt->stats: counters summed over the chunks
+ * (gemm_launches = chunks). Synchronous.
+ */
+int knn_search_streamed(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k,
+                        int64_t chunk_rows, int32_t* out_idx, float* out_dist, const knn_options* opt);
+
 /* The k-NN graph of X by a metric (a point is never its own neighbour); 1 <= k <= N - 1. */
 int knng_build_metric(const float* X, int64_t N, int32_t d, int32_t k, int32_t metric, int32_t* out_idx,
                       float* out_val, const knn_options* opt);

@@ -93,6 +93,7 @@ def load(path: str | None = None):
         lib.knn_search.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, opt_p]
         lib.knn_search_metric.argtypes = [vp, i64, vp, i64, i32, i32, i32, vp, vp, opt_p]
         lib.knng_build_metric.argtypes = [vp, i64, i32, i32, i32, vp, vp, opt_p]
+        lib.knn_search_streamed.argtypes = [vp, i64, vp, i64, i32, i32, i64, vp, vp, opt_p]
         lib.knn_select.argtypes = [vp, i64, i64, i64, i32, vp, vp, opt_p]
         lib.knn_distances.argtypes = [vp, i64, vp, i64, i32, vp, i64, i32, opt_p]
         lib.knn_search_batched.argtypes = [ctypes.POINTER(KnnProblem), i32, opt_p]
@@ -235,6 +236,24 @@ def knn_search_metric(Q, C, k: int, metric: str, out_idx=None, out_val=None, pre
     _check(lib, lib.knn_search_metric(_ptr(Q), M, _ptr(C), N, d, k, METRICS[metric], _ptr(oi), _ptr(ov),
                                       ctypes.byref(opt)))
     return (oi, ov, st.as_dict()) if return_stats else (oi, ov)
+
+
+def knn_search_streamed(Q, C, k: int, chunk_rows: int = 0, out_idx=None, out_dist=None, precision="auto",
+                        rerank_extra: int = 32, flags: int = KNN_FLAG_CHECK_FINITE, stream=None,
+                        return_stats: bool = False):
+    """knn_search with the corpus C read in chunks of chunk_rows rows (C may stay in host memory)."""
+    lib = load()
+    Q = _as_f32(Q)
+    C = _as_f32(C)
+    M, d = Q.shape
+    N = C.shape[0]
+    oi = out_idx if out_idx is not None else _empty_like_out(Q, (M, k), "i")
+    od = out_dist if out_dist is not None else _empty_like_out(Q, (M, k), "f")
+    st = KnnStats()
+    opt = make_options(precision, rerank_extra, -1, flags, _stream_of(Q, stream), None, st)
+    _check(lib, lib.knn_search_streamed(_ptr(Q), M, _ptr(C), N, d, k, int(chunk_rows), _ptr(oi), _ptr(od),
+                                        ctypes.byref(opt)))
+    return (oi, od, st.as_dict()) if return_stats else (oi, od)
 
 
 def knng_build_metric(X, k: int, metric: str, out_idx=None, out_val=None, precision="auto", rerank_extra: int = 32,

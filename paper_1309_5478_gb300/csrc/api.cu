@@ -1086,6 +1086,143 @@ int metric_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
     return KNN_OK;
 }
 
+// k-NN search against a corpus read in chunks (out-of-core): chunk c + 1 is copied on a second
+// stream while chunk c is searched; each chunk's exact answer is merged into the running
+// answer by (FP64 distance, global index) while the chunk is resident, and the reported
+// distances are the FP32 rounding of those FP64 distances.
+int stream_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k, int64_t chunk_rows,
+                int32_t* out_idx, float* out_dist, const knn_options* opt_in) {
+    g_last_error.clear();
+    const knn_options opt = opt_in ? *opt_in : defaults();
+    if (opt.row_threshold) return set_error(KNN_EINVAL, "row_threshold is not supported with a streamed corpus");
+    KNN_TRY(validate_args(Q, M, C, N, d, k, out_idx, out_dist, opt, false));
+    if (chunk_rows < 0) return set_error(KNN_EINVAL, "chunk_rows must be >= 0");
+    if (M == 0) return KNN_OK;
+    cudaStream_t st = stream_of(&opt);
+    const auto t0 = std::chrono::steady_clock::now();
+    Staged sg;
+    const void* Qd = nullptr;
+    KNN_TRY(sg.in(Q, static_cast<size_t>(M) * d * sizeof(float), st, &Qd));
+    void *oi = nullptr, *od = nullptr;
+    KNN_TRY(sg.out(out_idx, static_cast<size_t>(M) * k * sizeof(int32_t), &oi));
+    KNN_TRY(sg.out(out_dist, static_cast<size_t>(M) * k * sizeof(float), &od));
+    if (chunk_rows == 0) {
+        // two chunk buffers in a quarter of the free device memory
+        size_t free_b = 0, total_b = 0;
+        KNN_CK(cudaMemGetInfo(&free_b, &total_b));
+        chunk_rows = static_cast<int64_t>(free_b / 4) / (2 * static_cast<int64_t>(d) * 4);
+    }
+    chunk_rows = std::max<int64_t>(1, std::min(chunk_rows, N));
+    const int32_t kc_max = static_cast<int32_t>(std::min<int64_t>(k, chunk_rows));
+    CallBuffers cb;
+    float* buf[2] = {nullptr, nullptr};
+    KNN_TRY(cb.take(static_cast<size_t>(chunk_rows) * d, &buf[0]));
+    if (chunk_rows < N) KNN_TRY(cb.take(static_cast<size_t>(chunk_rows) * d, &buf[1]));
+    int32_t *run_idx = nullptr, *cidx = nullptr;
+    double* run_d64 = nullptr;
+    float *run_f32 = nullptr, *cdist = nullptr;
+    KNN_TRY(cb.take(static_cast<size_t>(M) * k, &run_idx));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * k, &run_d64));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * k, &run_f32));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * kc_max, &cidx));
+    KNN_TRY(cb.take(static_cast<size_t>(M) * kc_max, &cdist));
+    struct StreamEvents {
+        cudaStream_t cs = nullptr;
+        cudaEvent_t copied[2] = {nullptr, nullptr}, merged[2] = {nullptr, nullptr};
+        ~StreamEvents() {
+            if (cs) cudaStreamSynchronize(cs);
+            for (auto e : copied)
+                if (e) cudaEventDestroy(e);
+            for (auto e : merged)
+                if (e) cudaEventDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } se;
+    KNN_CK(cudaStreamCreateWithFlags(&se.cs, cudaStreamNonBlocking));
+    for (int b = 0; b < 2; ++b) {
+        KNN_CK(cudaEventCreateWithFlags(&se.copied[b], cudaEventDisableTiming));
+        KNN_CK(cudaEventCreateWithFlags(&se.merged[b], cudaEventDisableTiming));
+    }
+    KNN_CK(launch_stream_init(M * k, run_idx, run_d64, run_f32, st));
+    int64_t launches = 1;
+    // the copy into a buffer waits for the merge that last read it
+    auto issue_copy = [&](int64_t c0, int b) -> int {
+        const int64_t n = std::min(chunk_rows, N - c0);
+        KNN_CK(cudaStreamWaitEvent(se.cs, se.merged[b], 0));
+        KNN_CK(cudaMemcpyAsync(buf[b], C + c0 * d, static_cast<size_t>(n) * d * sizeof(float), cudaMemcpyDefault,
+                               se.cs));
+        KNN_CK(cudaEventRecord(se.copied[b], se.cs));
+        return KNN_OK;
+    };
+    knn_stats* stats = opt.stats;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    KNN_TRY(issue_copy(0, 0));
+    int64_t ci = 0;
+    for (int64_t c0 = 0; c0 < N; c0 += chunk_rows, ++ci) {
+        const int b = static_cast<int>(ci & 1);
+        const int64_t n = std::min(chunk_rows, N - c0);
+        KNN_CK(cudaStreamWaitEvent(st, se.copied[b], 0));
+        if (c0 + chunk_rows < N) KNN_TRY(issue_copy(c0 + chunk_rows, b ^ 1));
+        const int32_t kcc = static_cast<int32_t>(std::min<int64_t>(k, n));
+        Problem pb{};
+        pb.Q = static_cast<const float*>(Qd);
+        pb.C = buf[b];
+        pb.M = M;
+        pb.N = n;
+        pb.d = d;
+        pb.k = kcc;
+        pb.m = opt.rerank_extra;
+        pb.graph = false;
+        pb.out_idx = cidx;
+        pb.out_dist = cdist;
+        pb.slab_bytes = opt.max_workspace_bytes > 0 ? opt.max_workspace_bytes / 2 : 0;
+        pb.precision = opt.precision;
+        pb.fused = opt.fused;
+        pb.flags = opt.flags & ~KNN_FLAG_TIMING;
+        knn_stats cs_stats{};
+        KNN_TRY(run_problem(pb, &cs_stats, st));
+        StreamMergeParams mp{};
+        mp.Q = static_cast<const float*>(Qd);
+        mp.chunk = buf[b];
+        mp.chunk_row0 = c0;
+        mp.chunk_idx = cidx;
+        mp.M = M;
+        mp.d = d;
+        mp.k = k;
+        mp.kc = kcc;
+        mp.P = 32;
+        while (mp.P < k + kcc) mp.P *= 2;
+        mp.run_idx = run_idx;
+        mp.run_d64 = run_d64;
+        mp.run_f32 = run_f32;
+        KNN_CK(launch_stream_merge(mp, st));
+        KNN_CK(cudaEventRecord(se.merged[b], st));
+        launches += cs_stats.kernel_launches + 1;
+        if (stats) {
+            stats->candidates += cs_stats.candidates;
+            stats->rows_truncated += cs_stats.rows_truncated;
+            stats->rows_uncertified += cs_stats.rows_uncertified;
+            stats->rows_fallback += cs_stats.rows_fallback;
+            stats->rows_fp64_ties += cs_stats.rows_fp64_ties;
+            stats->gemm_flops += cs_stats.gemm_flops;
+            stats->precision_used = cs_stats.precision_used;
+            stats->fused_used = cs_stats.fused_used;
+        }
+    }
+    KNN_CK(cudaMemcpyAsync(oi, run_idx, static_cast<size_t>(M) * k * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    KNN_CK(cudaMemcpyAsync(od, run_f32, static_cast<size_t>(M) * k * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    KNN_TRY(sg.copy_back(st));
+    KNN_CK(cudaStreamSynchronize(st));
+    if (stats) {
+        stats->rows = M;
+        stats->kernel_launches = launches;
+        stats->gemm_launches = static_cast<int32_t>(ci);
+        if (opt.flags & KNN_FLAG_TIMING)
+            stats->ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return KNN_OK;
+}
+
 // The k smallest of every row of D (M x N, row stride ldd) as sorted (index, value) pairs, and
 // each row's RowFlag bits in flags. Few long dense rows are split into S segments selected in
 // parallel (one warp per row would leave most SMs idle), whose S k answers are merged: by one
@@ -1235,6 +1372,11 @@ int knn_search_metric(const float* Q, int64_t M, const float* C, int64_t N, int3
 int knng_build_metric(const float* X, int64_t N, int32_t d, int32_t k, int32_t metric, int32_t* out_idx,
                       float* out_val, const knn_options* opt) {
     return knn::metric_impl(X, N, X, N, d, k, metric, out_idx, out_val, opt, true);
+}
+
+int knn_search_streamed(const float* Q, int64_t M, const float* C, int64_t N, int32_t d, int32_t k,
+                        int64_t chunk_rows, int32_t* out_idx, float* out_dist, const knn_options* opt) {
+    return knn::stream_impl(Q, M, C, N, d, k, chunk_rows, out_idx, out_dist, opt);
 }
 
 int knn_select(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx, float* out_val,

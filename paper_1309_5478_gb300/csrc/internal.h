@@ -210,6 +210,21 @@ struct SimRerankParams {
 double sim_margin(int32_t d);
 cudaError_t launch_sim_rerank(const SimRerankParams& p, int32_t centered, cudaStream_t st);
 
+// ---- out-of-core corpus (stream.cu) ----
+struct StreamMergeParams {
+    const float* Q;            // M x d queries
+    const float* chunk;        // the resident chunk: rows chunk_row0 .. of the corpus
+    int64_t chunk_row0;
+    const int32_t* chunk_idx;  // M x kc chunk-local indices (the chunk's answer)
+    int64_t M;
+    int32_t d, k, kc, P;       // P = power of two >= k + kc
+    int32_t* run_idx;          // M x k running answer (global indices, -1 = empty)
+    double* run_d64;           // M x k their FP64 direct-difference distances
+    float* run_f32;            // M x k the FP32 rounding of run_d64 (the reported distances)
+};
+cudaError_t launch_stream_init(int64_t n, int32_t* idx, double* d64, float* f32, cudaStream_t st);
+cudaError_t launch_stream_merge(const StreamMergeParams& p, cudaStream_t st);
+
 // Exact FP64 answer for a list of rows (last-resort path; slow, used for rows no other path certifies).
 cudaError_t launch_exact_rows_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,
                                    int32_t exclude_self, const int32_t* rows, int32_t nrows, double* scratch,
