@@ -484,7 +484,7 @@ int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
 
 // Sampled rows of the band probe and the smallest problem it runs on (M N pairs).
 constexpr int PROBE_ROWS = 64;
-constexpr double PROBE_MIN_PAIRS = 17179869184.0;  // 2^34
+constexpr double PROBE_MIN_PAIRS = 1073741824.0;  // 2^30
 
 struct ProbeBuffers {
     int32_t* rows = nullptr;   // PROBE_ROWS sampled query rows
@@ -494,7 +494,7 @@ struct ProbeBuffers {
     int32_t* oi = nullptr;     // PROBE_ROWS x km
     float* ov = nullptr;
     uint32_t* fl = nullptr;
-    int32_t* cnt = nullptr;
+    int32_t* cnt = nullptr;    // 2 x PROBE_ROWS: band counts with 2E, then with 4E
     float* edge = nullptr;     // band edges of the sampled rows as squared distances
 };
 
@@ -527,11 +527,12 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
     sp.self_col = pb.graph ? pr.rows : nullptr;
     KNN_CK(launch_select_topk(sp, pr.oi, pr.ov, st));
     KNN_CK(launch_band_count(pr.D, PROBE_ROWS, pb.N, pb.N, pr.ov, pb.k, km, pr.Es, sp.self_col, L.ps.qnorm2,
-                             pr.rows, pr.cnt, pr.edge, st));
+                             pr.rows, pr.cnt, pr.cnt + PROBE_ROWS, pr.edge, st));
     tm.launches += 4;
-    std::vector<int32_t> cnt(PROBE_ROWS);
+    std::vector<int32_t> cnt(PROBE_ROWS), cnt4(PROBE_ROWS);
     std::vector<float> edge(PROBE_ROWS);
     KNN_CK(cudaMemcpyAsync(cnt.data(), pr.cnt, PROBE_ROWS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaMemcpyAsync(cnt4.data(), pr.cnt + PROBE_ROWS, PROBE_ROWS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaMemcpyAsync(edge.data(), pr.edge, PROBE_ROWS * sizeof(float), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
     if (spec_d2) {
@@ -541,8 +542,14 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
         *spec_d2 = std::isfinite(t) ? t : __builtin_huge_valf();
     }
     std::sort(cnt.begin(), cnt.end());
+    std::sort(cnt4.begin(), cnt4.end());
     const int band = cnt[(PROBE_ROWS * 9) / 10];
+    const int band4 = cnt4[(PROBE_ROWS * 9) / 10];
     int cap = (band + band / 4 + 160 + 31) / 32 * 32;
+    // a truncating shrink in the sweep keeps cap / 2 keys: keep that above the band the lists
+    // can reach on approximate values (exact v_k + 4E), or rows with dense neighbourhoods are
+    // truncated inside their band and end uncertified
+    cap = std::max(cap, (2 * band4 + 31) / 32 * 32);
     cap = std::max(cap, fused_cap(pb.k, km));
     *cap_out = std::min(cap, FUSED_CAP_WIDE);
     return KNN_OK;
@@ -691,7 +698,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
             pr.oi = ar.take<int32_t>(static_cast<size_t>(PROBE_ROWS) * km);
             pr.ov = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * km);
             pr.fl = ar.take<uint32_t>(PROBE_ROWS);
-            pr.cnt = ar.take<int32_t>(PROBE_ROWS);
+            pr.cnt = ar.take<int32_t>(2 * PROBE_ROWS);
             pr.edge = ar.take<float>(PROBE_ROWS);
         }
     };

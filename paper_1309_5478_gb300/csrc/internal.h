@@ -132,11 +132,13 @@ inline int rerank_launches(int cap) { return cap > 1024 ? 3 : (cap > 512 ? 2 : 1
 
 // ---- band probe (probe.cu) ----
 // out_count[i] = #{ j != self_col[i] : D[i][j] <= max(vals[i][km-1], vals[i][k-1] + 2 E[i]) },
-// vals[i] holding row i's km smallest values in ascending order; out_edge[i] (optional) =
-// that band edge plus qnorm2[row_ids[i]], a squared distance.
+// vals[i] holding row i's km smallest values in ascending order; out_count4[i] (optional) the
+// same with 4 E (the reach of a band taken on approximate values); out_edge[i] (optional) =
+// the 2 E band edge plus qnorm2[row_ids[i]], a squared distance.
 cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
                               int32_t km, const float* E, const int32_t* self_col, const float* qnorm2,
-                              const int32_t* row_ids, int32_t* out_count, float* out_edge, cudaStream_t st);
+                              const int32_t* row_ids, int32_t* out_count, int32_t* out_count4, float* out_edge,
+                              cudaStream_t st);
 
 // ---- batched problems (batched.cu, with batched kernels in prep.cu / rerank.cu) ----
 // Device-side description of one problem of a batch and of its buffers.

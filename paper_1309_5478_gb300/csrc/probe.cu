@@ -19,22 +19,35 @@ __global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_
                                   int32_t k, int32_t km, const float* __restrict__ E,
                                   const int32_t* __restrict__ self_col, const float* __restrict__ qnorm2,
                                   const int32_t* __restrict__ rows, int32_t* __restrict__ out_count,
-                                  float* __restrict__ out_edge) {
+                                  int32_t* __restrict__ out_count4, float* __restrict__ out_edge) {
     const int64_t i = blockIdx.x;
     const float* v = vals + i * km;
     const float T = fmaxf(v[km - 1], v[k - 1] + 2.f * E[i]);
+    // a list built on approximate values (each within E) keeps keys up to exact v_k + 4E
+    const float T4 = fmaxf(v[km - 1], v[k - 1] + 4.f * E[i]);
     const float* row = D + i * ldd;
     const int64_t self = self_col ? self_col[i] : -1;
-    int c = 0;
-    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) c += (row[j] <= T && j != self) ? 1 : 0;
+    int c = 0, c4 = 0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        c += (row[j] <= T && j != self) ? 1 : 0;
+        c4 += (row[j] <= T4 && j != self) ? 1 : 0;
+    }
     c = __reduce_add_sync(0xffffffffu, c);
-    __shared__ int part[32];
-    if ((threadIdx.x & 31u) == 0) part[threadIdx.x / 32] = c;
+    c4 = __reduce_add_sync(0xffffffffu, c4);
+    __shared__ int part[32], part4[32];
+    if ((threadIdx.x & 31u) == 0) {
+        part[threadIdx.x / 32] = c;
+        part4[threadIdx.x / 32] = c4;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int s = 0;
-        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += part[w];
+        int s = 0, s4 = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) {
+            s += part[w];
+            s4 += part4[w];
+        }
         out_count[i] = s;
+        if (out_count4) out_count4[i] = s4;
         if (out_edge) out_edge[i] = T + qnorm2[rows[i]];
     }
 }
@@ -43,10 +56,11 @@ __global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_
 
 cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
                               int32_t km, const float* E, const int32_t* self_col, const float* qnorm2,
-                              const int32_t* row_ids, int32_t* out_count, float* out_edge, cudaStream_t st) {
+                              const int32_t* row_ids, int32_t* out_count, int32_t* out_count4, float* out_edge,
+                              cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
     band_count_kernel<<<static_cast<unsigned>(rows), 512, 0, st>>>(D, N, ldd, vals, k, km, E, self_col, qnorm2,
-                                                                   row_ids, out_count, out_edge);
+                                                                   row_ids, out_count, out_count4, out_edge);
     return cudaGetLastError();
 }
 
