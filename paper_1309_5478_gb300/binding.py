@@ -54,7 +54,8 @@ class KnnProblem(ctypes.Structure):
 EXPORTS = ("knn_options_init", "knng_build", "knng_build_ex", "knn_search", "knn_select", "knn_distances",
            "knn_search_batched", "knn_status_string", "knn_last_error", "knn_shutdown", "knn_version",
            "knn_select_noalloc", "knn_mlp_param_count", "knn_mlp_features", "knn_mlp_loss_grad", "knn_mlp_train",
-           "knn_mlp_predict", "knn_mlp_save", "knn_mlp_load")
+           "knn_mlp_predict", "knn_mlp_save", "knn_mlp_load", "knn_search_metric", "knng_build_metric",
+           "knn_search_streamed")
 MLP_FEATURES, MLP_HIDDEN = 257, 128
 MLP_TRAINED = MLP_HIDDEN * MLP_FEATURES + 2 * MLP_HIDDEN + 1
 

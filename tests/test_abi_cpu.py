@@ -65,6 +65,21 @@ def test_argument_checks_need_no_device(lib):
     lib.knn_options_init(ctypes.byref(opt))
     assert opt.rerank_extra == 32 and opt.precision == binding.KNN_AUTO and opt.fused == -1
     assert lib.knn_search(p, 10, p, 10, 4, 11, oi.ctypes.data, od.ctypes.data, ctypes.byref(opt)) == binding.KNN_EINVAL
+    # similarity metrics and the streamed corpus check their arguments before any device work
+    assert lib.knn_search_metric(p, 10, p, 10, 4, 3, 7, oi.ctypes.data, od.ctypes.data,
+                                 ctypes.byref(opt)) == binding.KNN_EINVAL
+    assert b"unknown metric" in lib.knn_last_error()
+    assert lib.knng_build_metric(p, 10, 4, 10, binding.METRICS["cosine"], oi.ctypes.data, od.ctypes.data,
+                                 ctypes.byref(opt)) == binding.KNN_EINVAL
+    thr = np.ones(10, dtype=np.float32)
+    opt_t = binding.make_options(row_threshold=thr)
+    assert lib.knn_search_metric(p, 10, p, 10, 4, 3, binding.METRICS["pearson"], oi.ctypes.data, od.ctypes.data,
+                                 ctypes.byref(opt_t)) == binding.KNN_EINVAL
+    assert b"row_threshold" in lib.knn_last_error()
+    assert lib.knn_search_streamed(p, 10, p, 10, 4, 3, -1, oi.ctypes.data, od.ctypes.data,
+                                   ctypes.byref(opt)) == binding.KNN_EINVAL
+    assert lib.knn_search_streamed(p, 10, p, 10, 4, 0, 5, oi.ctypes.data, od.ctypes.data,
+                                   ctypes.byref(opt)) == binding.KNN_EINVAL
 
 
 def test_library_is_built_for_sm_103a():
