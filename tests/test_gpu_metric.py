@@ -132,3 +132,17 @@ def test_cosine_graph_65536x128_sampled_rows():
     print("cosine 65536x128 stats:", {kk: st[kk] for kk in ("rows_uncertified", "rows_fallback", "candidates",
                                                            "rows_truncated", "precision_used", "list_capacity")})
     assert st["rows_uncertified"] < len(X) // 100
+
+
+def test_host_arrays_are_staged():
+    # numpy inputs and outputs: the library stages them through device memory
+    X = nonzero_rows(inputs.integer_lattice(n=800, d=10, lo=-4, hi=4, seed=78), True)
+    Q = X[:50]
+    for metric in ("cosine", "pearson"):
+        idx, val = kb.knn_search_metric(Q, X, 9, metric)
+        assert isinstance(idx, np.ndarray) and isinstance(val, np.ndarray)
+        ref_idx, ref_sim = oracle.knn_sim(Q, X, 9, metric)
+        if metric == "cosine":
+            check_sim_exact(idx, val, ref_idx, ref_sim)
+        else:
+            check_sim_float(Q, X, range(len(Q)), idx, val, ref_idx, ref_sim, metric, False)

@@ -12,7 +12,8 @@ torch = pytest.importorskip("torch")
 
 
 def test_noalloc_select_matches_select_on_two_calls():
-    for call, (rows, cols, k, seed) in enumerate([(777, 5003, 64, 5), (300, 20000, 17, 6)]):
+    # the second and third shapes take the block-per-row select (k >= 128, and few rows)
+    for call, (rows, cols, k, seed) in enumerate([(777, 5003, 64, 5), (300, 20000, 300, 6), (12, 70000, 17, 7)]):
         D = torch.from_numpy(inputs.uniform_matrix(rows, cols, seed=seed)).cuda()
         ref_i, ref_v = kb.knn_select(D, k)
         oi = torch.empty((rows, k), dtype=torch.int32, device="cuda")
