@@ -507,7 +507,7 @@ struct ProbeBuffers {
 // its final threshold; a row whose band lies beyond it is caught at the end of the
 // sweep (truncated, re-rank certificate, second pass). Where the edges spread widely
 // the proposal is loose and costs nothing.
-int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffers& pr, cudaStream_t st,
+int probe_cap(const Problem& pb, int prec, int km, const CommonLayout& L, const ProbeBuffers& pr, cudaStream_t st,
               Timing& tm, int* cap_out, float* spec_d2) {
     std::vector<int32_t> rows(PROBE_ROWS);
     for (int i = 0; i < PROBE_ROWS; ++i) rows[i] = static_cast<int32_t>((pb.M * (2 * i + 1)) / (2 * PROBE_ROWS));
@@ -545,13 +545,15 @@ int probe_cap(const Problem& pb, int km, const CommonLayout& L, const ProbeBuffe
     std::sort(cnt4.begin(), cnt4.end());
     const int band = cnt[(PROBE_ROWS * 9) / 10];
     const int band4 = cnt4[(PROBE_ROWS * 9) / 10];
-    int cap = (band + band / 4 + 160 + 31) / 32 * 32;
+    const int base = std::min(std::max((band + band / 4 + 160 + 31) / 32 * 32, fused_cap(pb.k, km)), FUSED_CAP_WIDE);
     // a truncating shrink in the sweep keeps cap / 2 keys: keep that above the band the lists
     // can reach on approximate values (exact v_k + 4E), or rows with dense neighbourhoods are
-    // truncated inside their band and end uncertified
-    cap = std::max(cap, (2 * band4 + 31) / 32 * 32);
-    cap = std::max(cap, fused_cap(pb.k, km));
-    *cap_out = std::min(cap, FUSED_CAP_WIDE);
+    // truncated inside their band and end uncertified -- but never at the price of a stage of
+    // the GEMM's operand pipeline (the lists share its shared memory)
+    int cap = std::min(std::max(base, (2 * band4 + 31) / 32 * 32), FUSED_CAP_WIDE);
+    const int stages = fused_stages(base, prec);
+    while (cap > base && fused_stages(cap, prec) < stages) cap -= 32;
+    *cap_out = cap;
     return KNN_OK;
 }
 
@@ -721,7 +723,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
     float spec_d2 = __builtin_huge_valf();
     const bool spec = speculate(pb);
-    if (probe) KNN_TRY(probe_cap(pb, km, L, pr, st, tm, &cap, spec && spec_start() ? &spec_d2 : nullptr));
+    if (probe) KNN_TRY(probe_cap(pb, prec, km, L, pr, st, tm, &cap, spec && spec_start() ? &spec_d2 : nullptr));
     if (cap_env > 0) cap = cap_env;
     const int stages = fused_stages(cap, prec);
     if (stages == 0) return set_error(KNN_EINTERNAL, "fused list capacity %d does not fit", cap);
