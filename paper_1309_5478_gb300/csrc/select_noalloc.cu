@@ -1,20 +1,25 @@
 // knn_select_noalloc: the quick multi-select for callers that must not allocate.
 //
-// Some callers cannot let a library call cudaMalloc: code that runs while a CUDA
-// graph is being captured (allocation is not a capturable operation), applications
-// whose device memory is all owned by their own caching allocator or memory pool
-// reserved at start-up, and latency-critical paths that cannot pay cudaMalloc's
-// implicit synchronisation. This entry point serves them: it uses no library
-// workspace and stages nothing, so it calls no cudaMalloc, cudaFree or other
+// Some callers cannot let a library call cudaMalloc: applications whose device memory
+// is all owned by their own caching allocator or by a pool reserved at start-up (a
+// library allocation there can fail, or fragment memory the application has already
+// planned), and latency-critical paths that cannot pay cudaMalloc's implicit device
+// synchronisation in the middle of their work. This entry point serves them: it uses
+// no library workspace and stages nothing, so it calls no cudaMalloc, cudaFree or other
 // allocating routine. Its only scratch -- one status word per row plus an error
 // summary -- is a file-scope device array of fixed size, which every GPU that loads
 // the library holds until the process exits.
 //
 // Set-up: the first call on a device looks up the array's device address with
-// cudaGetSymbolAddress (with that device current) and caches it; make that first call
-// before any stream capture begins. Every later call reuses the same array, so calls
-// that overlap on the GPU (different streams, or host threads without ordering) race
-// on it and must be serialised by the caller.
+// cudaGetSymbolAddress (with that device current) and caches it. Every later call
+// reuses the same array, so calls that overlap on the GPU (different streams, or host
+// threads without ordering) race on it and must be serialised by the caller. Like the
+// library's other calls it is synchronous: it ends by copying the error summary to a
+// host variable and synchronising the stream.
+//
+// Few long rows are not split into segments here (knn_select does that, with workspace
+// for the segment answers): for at most 64 rows the select takes one CTA per row, which
+// is slower than knn_select's split when the rows are very long.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -76,6 +81,7 @@ __global__ void noalloc_error_summary(int64_t M) {
 extern "C" int knn_select_noalloc(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx,
                                   float* out_val, void* stream) {
     using namespace knn;
+    g_last_error.clear();
     if (!D || !out_idx || !out_val) return set_error(KNN_EINVAL, "NULL pointer argument");
     if (N < 1 || N >= (int64_t(1) << 31)) return set_error(KNN_EINVAL, "N must be in [1, 2^31)");
     if (ldd < N) return set_error(KNN_EINVAL, "ldd (%lld) must be >= N (%lld)", (long long)ldd, (long long)N);

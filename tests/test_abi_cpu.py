@@ -109,3 +109,15 @@ def test_mlp_parameter_file_round_trip_on_host(lib, tmp_path):
         binding.mlp_load(bad, q)
     with pytest.raises(binding.KnnError):
         binding.mlp_load(tmp_path / "missing.bin", q)
+
+
+def test_noalloc_select_row_limit_is_checked_before_any_device_work(lib):
+    from paper_1309_5478_gb300 import binding
+    buf = np.zeros(16, dtype=np.float32)
+    oi = np.zeros(16, dtype=np.int32)
+    p = buf.ctypes.data
+    # 2^20 + 1 rows: rejected by the argument checks, before the pointers are looked at
+    assert lib.knn_select_noalloc(p, (1 << 20) + 1, 4, 4, 2, oi.ctypes.data, p, None) == binding.KNN_EINVAL
+    assert b"at most 1048576 rows" in lib.knn_last_error()
+    assert lib.knn_select_noalloc(p, 4, 4, 3, 2, oi.ctypes.data, p, None) == binding.KNN_EINVAL  # ldd < N
+    assert b"ldd" in lib.knn_last_error()

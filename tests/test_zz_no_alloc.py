@@ -35,3 +35,16 @@ def test_noalloc_select_rejects_what_it_cannot_do():
         kb.knn_select_noalloc(D, 2, oi, ov)
     D[2, 5] = 0.0
     kb.knn_select_noalloc(D, 2, oi, ov)  # the error word is cleared per call
+
+
+def test_noalloc_select_on_a_column_slice():
+    # ldd > N: the first 3001 columns of a 5000-column matrix; every row's status word
+    # must still be covered by the fixed array
+    D = torch.from_numpy(inputs.uniform_matrix(901, 5000, seed=8)).cuda()
+    ref_i, ref_v = kb.knn_select(D, 40, n=3001)
+    oi = torch.empty((901, 40), dtype=torch.int32, device="cuda")
+    ov = torch.empty((901, 40), dtype=torch.float32, device="cuda")
+    kb.knn_select_noalloc(D, 40, oi, ov, n=3001)
+    torch.cuda.synchronize()
+    assert torch.equal(oi, ref_i) and torch.equal(ov, ref_v)
+    assert int(oi.max()) < 3001
