@@ -73,7 +73,9 @@ typedef struct knn_stats {
     int64_t rows_fp64_ties;    /* rows where FP64 decided a near tie */
     int64_t threshold_misses;  /* rows where a supplied threshold kept fewer than k candidates */
     float max_error_bound;     /* largest per-row bound on |approximate - exact| squared distance */
-    float ms_total, ms_prep, ms_select, ms_rerank, ms_fallback; /* with KNN_FLAG_TIMING */
+    float ms_total, ms_prep, ms_select, ms_rerank, ms_fallback; /* with KNN_FLAG_TIMING; in the plain
+                                  form ms_select and ms_rerank are the device times of the select and
+                                  re-rank launches alone (the slabs interleave them with the GEMM) */
     float ms_gemm;             /* with KNN_FLAG_TIMING: device time of the distance kernel (fused: GEMM + select) */
     int32_t gemm_launches;     /* launches of that kernel */
     int64_t kernel_launches;   /* every kernel the call launched */
@@ -84,6 +86,11 @@ typedef struct knn_stats {
     int32_t list_capacity;     /* candidate-list capacity per row of the first pass (largest in a batch) */
     int64_t candidates_inserted; /* fused form: keys the running thresholds let into candidate lists
                                     during the sweep (the select's work), summed over rows */
+    float max_error_ratio;     /* largest |approximate - exact| / E_i over the candidates the re-rank
+                                  evaluated, where E_i is the row's proven error bound of the GEMM's
+                                  ranking value (exactness rests on this ratio staying <= 1) */
+    int64_t rows_reranked_in_sweep; /* fused form: rows re-ranked by the fused kernel while it swept
+                                       later row blocks (the rest by the re-rank launch after it) */
 } knn_stats;
 
 typedef struct knn_options {
@@ -96,7 +103,9 @@ typedef struct knn_options {
                                    threshold proposal that pre-filters candidates; rows where fewer
                                    than k candidates pass are recomputed without it */
     knn_stats* stats;           /* optional output */
-    int64_t max_workspace_bytes;/* 0 = no cap; otherwise the distance-matrix slab is sized to fit */
+    int64_t max_workspace_bytes;/* 0 = no cap; otherwise the call's device workspace is kept within it
+                                   (distance-matrix slabs and FP64 scratch shrink to fit), and a call
+                                   whose workspace cannot fit returns KNN_ENOMEM */
 } knn_options;
 
 /* Fill *opt with defaults: KNN_AUTO, m = 32, fused auto, finite check on. */
@@ -188,16 +197,18 @@ int knn_distances(const float* Q, int64_t M, const float* C, int64_t N, int32_t 
 
 /*
  * knn_select without any allocation (the paper has no counterpart: this is for
- * callers that cannot let the library allocate -- code running inside CUDA graph
- * capture, applications whose device memory is all owned by their own pool, and
- * latency-critical paths that cannot pay cudaMalloc's implicit synchronisation).
+ * callers that cannot let the library allocate -- applications whose device memory
+ * is all owned by their own caching allocator or pool, and latency-critical paths
+ * that cannot pay cudaMalloc's implicit synchronisation).
  * Same result as knn_select. D, out_idx and out_val must be DEVICE pointers (nothing
  * is staged); stream is a cudaStream_t (NULL = legacy default stream). At most
  * 1048576 rows per call (larger M returns KNN_EINVAL). The only scratch is a fixed
- * 4 MiB device array inside the library, held by every GPU that loads it until exit.
- * The first call on a device looks up that array's address (cudaGetSymbolAddress):
- * make it before any stream capture. All calls share the array: calls that overlap
- * on the GPU race and must be serialised by the caller. Synchronous like every call.
+ * 4 MiB device array inside the library, held by every GPU that loads it until exit;
+ * the first call on a device looks up that array's address (cudaGetSymbolAddress).
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. Synchronous like every call: it ends by copying a status
+ * word to the host and synchronising the stream. Up to 64 long rows take one CTA per
+ * row (knn_select splits them into segments instead, which needs workspace).
  */
 int knn_select_noalloc(const float* D, int64_t M, int64_t N, int64_t ldd, int32_t k, int32_t* out_idx,
                        float* out_val, void* stream);

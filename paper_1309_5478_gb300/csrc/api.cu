@@ -44,9 +44,16 @@ struct DevWs {
 };
 std::mutex g_ws_mu;
 std::unordered_map<int, DevWs> g_ws;
+thread_local int64_t g_ws_cap = 0;  // knn_options.max_workspace_bytes of the running call (0: none)
 }  // namespace
 
+WorkspaceCap::WorkspaceCap(int64_t bytes) : prev_(g_ws_cap) { g_ws_cap = bytes > 0 ? bytes : 0; }
+WorkspaceCap::~WorkspaceCap() { g_ws_cap = prev_; }
+
 int workspace_get(size_t bytes, void** out) {
+    if (g_ws_cap > 0 && bytes > static_cast<size_t>(g_ws_cap))
+        return set_error(KNN_ENOMEM, "the call needs %zu bytes of workspace, above max_workspace_bytes = %lld", bytes,
+                         static_cast<long long>(g_ws_cap));
     int dev = 0;
     KNN_CK(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_ws_mu);
@@ -116,28 +123,38 @@ namespace {
 struct Timing {
     bool on = false;
     std::vector<cudaEvent_t> gemm;  // pairs around each distance-kernel launch
+    std::vector<cudaEvent_t> sel;   // pairs around each unfused select (plain form)
+    std::vector<cudaEvent_t> rr;    // pairs around each re-rank launch of the plain form
     int64_t launches = 0;
     int32_t gemm_launches = 0;
-    int record_gemm(cudaStream_t st, bool begin) {
+    static int record(std::vector<cudaEvent_t>& v, bool on, cudaStream_t st) {
         if (!on) return KNN_OK;
         cudaEvent_t e;
         KNN_CK(cudaEventCreate(&e));
-        gemm.push_back(e);
+        v.push_back(e);
         KNN_CK(cudaEventRecord(e, st));
-        (void)begin;
         return KNN_OK;
     }
-    float gemm_ms() const {
+    int record_gemm(cudaStream_t st, bool begin) {
+        (void)begin;
+        return record(gemm, on, st);
+    }
+    int record_sel(cudaStream_t st) { return record(sel, on, st); }
+    int record_rr(cudaStream_t st) { return record(rr, on, st); }
+    static float sum_ms(const std::vector<cudaEvent_t>& v) {
         float g = 0.f;
-        for (size_t i = 0; i + 1 < gemm.size(); i += 2) {
+        for (size_t i = 0; i + 1 < v.size(); i += 2) {
             float t = 0.f;
-            cudaEventElapsedTime(&t, gemm[i], gemm[i + 1]);
+            cudaEventElapsedTime(&t, v[i], v[i + 1]);
             g += t;
         }
         return g;
     }
+    float gemm_ms() const { return sum_ms(gemm); }
     ~Timing() {
         for (auto& e : gemm) cudaEventDestroy(e);
+        for (auto& e : sel) cudaEventDestroy(e);
+        for (auto& e : rr) cudaEventDestroy(e);
     }
 };
 
@@ -195,7 +212,9 @@ int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* 
         sp.bound = B.bound;
         sp.flags = B.flags;
         sp.self_col = self_col ? self_col + r0 : nullptr;
+        KNN_TRY(tm.record_sel(st));
         KNN_CK(launch_select_ex(sp, self_offset >= 0 ? self_offset + r0 : -1, false, st));
+        KNN_TRY(tm.record_sel(st));
         RerankParams rp{};
         rp.Q = Q + r0 * pb.d;
         rp.C = pb.C;
@@ -214,7 +233,9 @@ int plain_pipeline(const Problem& pb, const float* Q, int64_t M, const int32_t* 
         rp.out_dist = out_dist + r0 * pb.k;
         rp.row_status = row_status + r0;
         rp.counters = counters;
+        KNN_TRY(tm.record_rr(st));
         KNN_CK(launch_rerank(rp, st));
+        KNN_TRY(tm.record_rr(st));
         tm.launches += 2 + rerank_launches(B.cap);
         tm.gemm_launches += 1;
     }
@@ -281,7 +302,9 @@ void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena&
     L.counters = ar.take<RerankCounters>(1);
     L.status = ar.take<int>(1);
     L.fb_rows = ar.take<int32_t>(pb.M);
-    L.fp64_chunk = std::max<int64_t>(1, std::min<int64_t>(pb.M, (int64_t(1) << 30) / (pb.N * 8)));
+    // FP64 fallback scratch: rows of N doubles, up to 1 GiB (a quarter of a workspace cap)
+    const int64_t fp64_budget = pb.slab_bytes > 0 ? pb.slab_bytes / 2 : (int64_t(1) << 30);
+    L.fp64_chunk = std::max<int64_t>(1, std::min<int64_t>(pb.M, fp64_budget / (pb.N * 8)));
     L.fp64_scratch = ar.take<double>(static_cast<size_t>(L.fp64_chunk) * pb.N);
     if (with_fallback_plain) {
         L.fb_rows_max = std::min<int64_t>(pb.M, 16384);
@@ -399,6 +422,13 @@ void fill_stats(knn_stats* stats, const Problem& pb, const RerankCounters& hc, i
     stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
     stats->threshold_misses = static_cast<int64_t>(hc.threshold_miss);
     stats->candidates_inserted = static_cast<int64_t>(hc.inserted);
+    {
+        const uint32_t bits = static_cast<uint32_t>(hc.max_err_ratio);
+        float r;
+        std::memcpy(&r, &bits, sizeof(r));
+        stats->max_error_ratio = r;
+    }
+    stats->rows_reranked_in_sweep = static_cast<int64_t>(hc.rows_in_sweep);
     stats->precision_used = prec;
     stats->fused_used = fused;
     stats->kernel_launches = tm.launches;
@@ -478,7 +508,14 @@ int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     KNN_TRY(ev.rec(4, st));
     KNN_CK(cudaStreamSynchronize(st));
     fill_stats(stats, pb, hc, fallback, KNN_FP32, 0, tm, ev.ev);
-    if (stats) stats->list_capacity = B.cap;
+    if (stats) {
+        stats->list_capacity = B.cap;
+        if (tm.on) {
+            // the slabs interleave GEMM, select and re-rank: report each kernel's own device time
+            stats->ms_select = Timing::sum_ms(tm.sel);
+            stats->ms_rerank = Timing::sum_ms(tm.rr);
+        }
+    }
     return KNN_OK;
 }
 
@@ -551,8 +588,10 @@ int probe_cap(const Problem& pb, int prec, int km, const CommonLayout& L, const 
     // truncated inside their band and end uncertified -- but never at the price of a stage of
     // the GEMM's operand pipeline (the lists share its shared memory)
     int cap = std::min(std::max(base, (2 * band4 + 31) / 32 * 32), FUSED_CAP_WIDE);
-    const int stages = fused_stages(base, prec);
-    while (cap > base && fused_stages(cap, prec) < stages) cap -= 32;
+    // nor at the price of the re-rank warps' buffers, where they fit at the base capacity
+    const bool rr = fused_stages(base, prec, true) == fused_stages(base, prec, false);
+    const int stages = fused_stages(base, prec, rr);
+    while (cap > base && fused_stages(cap, prec, rr) < stages) cap -= 32;
     *cap_out = cap;
     return KNN_OK;
 }
@@ -581,6 +620,7 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
         KNN_CK(launch_gather_qrows(L.ps.xq, row_bytes, prec == P_FP8 ? L.ps.qscale : nullptr, L.fb_rows, n, L.fb_xq,
                                    L.fb_qscale, st));
         FusedParams fp = first;
+        fp.rr_on = 0;  // the second pass re-ranks its gathered rows after the kernel
         fp.xq = L.fb_xq;
         fp.M = n;
         fp.cap = cap2;
@@ -660,6 +700,25 @@ int tile_stride(int64_t n) {
     for (int64_t a = static_cast<int64_t>(0.6180339887 * static_cast<double>(n)) | 1; a > 1; a -= 2)
         if (gcd(a, n) == 1) return static_cast<int>(a);
     return 1;
+}
+
+// Polls of a bounded device-side wait before a kernel gives up (0: the kernel's default).
+// KNN_WAIT_LIMIT overrides it, so that the give-up path can be exercised.
+long long wait_limit() {
+    const char* e = std::getenv("KNN_WAIT_LIMIT");
+    return e ? std::max(1ll, std::atoll(e)) : 0ll;
+}
+
+// Whether the fused kernel's re-rank warps take the rows of finished row blocks during the
+// sweep: they need 16-byte aligned rows with d % 4 == 0, at least two row blocks per CTA
+// (the last one is always left to the re-rank launch), and shared memory that costs the
+// GEMM no pipeline stage. KNN_RERANK_IN_SWEEP=0 turns it off.
+bool rerank_in_sweep(const Problem& pb, int prec, int cap, int64_t nrb, int grid) {
+    if (const char* e = std::getenv("KNN_RERANK_IN_SWEEP"))
+        if (std::atoi(e) == 0) return false;
+    const bool vec = pb.d % 4 == 0 && reinterpret_cast<uintptr_t>(pb.Q) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(pb.C) % 16 == 0;
+    return vec && nrb >= 2 * static_cast<int64_t>(grid) && fused_stages(cap, prec, true) == fused_stages(cap, prec, false);
 }
 
 int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
@@ -758,16 +817,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.perm_a = fp.spec && !L.maybe_exact ? tile_stride((pb.N + 255) / 256) : 1;
     fp.qnorm2 = L.ps.qnorm2;
     fp.spec_d2 = spec_d2;
-    KNN_TRY(tm.record_gemm(st, true));
-    KNN_CK(launch_fused(fp, prec, grid, st));
-    KNN_TRY(tm.record_gemm(st, false));
-    ++tm.launches;
-    ++tm.gemm_launches;
-    KNN_TRY(ev.rec(2, st));
-    int hstatus = 0;
-    KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    KNN_CK(cudaStreamSynchronize(st));
-    if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the fused kernel stopped: a device-side wait timed out");
+    fp.wait_limit = wait_limit();
 
     RerankParams rp{};
     rp.Q = pb.Q;
@@ -787,12 +837,28 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     rp.out_dist = pb.out_dist;
     rp.row_status = L.row_status;
     rp.counters = L.counters;
+    rp.status = L.status;  // nothing is re-ranked after the fused kernel gave up
+    // the re-rank of finished row blocks overlaps the sweep of later ones; the launch after
+    // the kernel takes the rows the sweep's re-rank warps did not
+    fp.rr_on = rerank_in_sweep(pb, prec, cap, nrb, grid) ? 1 : 0;
+    fp.rr = rp;
+    rp.skip_done = fp.rr_on;
+    if (fp.rr_on) KNN_CK(cudaMemsetAsync(L.row_status, 0, static_cast<size_t>(pb.M) * sizeof(uint32_t), st));
+    KNN_TRY(tm.record_gemm(st, true));
+    KNN_CK(launch_fused(fp, prec, grid, st));
+    KNN_TRY(tm.record_gemm(st, false));
+    ++tm.launches;
+    ++tm.gemm_launches;
+    KNN_TRY(ev.rec(2, st));
     KNN_CK(launch_rerank(rp, st));
     tm.launches += rerank_launches(cap);
     KNN_TRY(ev.rec(3, st));
+    int hstatus = 0;
     RerankCounters hc{};
+    KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
+    if (hstatus != 0) return set_error(KNN_ETIMEOUT, "the fused kernel stopped: a device-side wait timed out");
     int64_t fallback = 0;
     if (hc.uncertified > 0 && !(pb.flags & KNN_FLAG_NO_FALLBACK)) {
         std::vector<int32_t> rows;
@@ -893,6 +959,7 @@ int search_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
     const knn_options opt = opt_in ? *opt_in : defaults();
     KNN_TRY(validate_args(Q, M, C, N, d, k, out_idx, out_dist, opt, graph));
     if (M == 0) return KNN_OK;
+    const WorkspaceCap cap_guard(opt.max_workspace_bytes);
     cudaStream_t st = stream_of(&opt);
     Staged sg;
     const void *Qd = nullptr, *Cd = nullptr, *Td = nullptr;
@@ -1208,6 +1275,8 @@ int stream_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
         KNN_CK(cudaEventRecord(se.merged[b], st));
         launches += cs_stats.kernel_launches + 1;
         if (stats) {
+            stats->max_error_ratio = std::max(stats->max_error_ratio, cs_stats.max_error_ratio);
+            stats->rows_reranked_in_sweep += cs_stats.rows_reranked_in_sweep;
             stats->candidates += cs_stats.candidates;
             stats->rows_truncated += cs_stats.rows_truncated;
             stats->rows_uncertified += cs_stats.rows_uncertified;

@@ -694,6 +694,10 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         stats->rows_uncertified = static_cast<int64_t>(hc.uncertified);
         stats->rows_fallback = fallback_rows;
         stats->rows_fp64_ties = static_cast<int64_t>(hc.fp64_rows);
+        {
+            const uint32_t bits = static_cast<uint32_t>(hc.max_err_ratio);
+            std::memcpy(&stats->max_error_ratio, &bits, sizeof(float));
+        }
         // device phases of the graph; ms_total is the whole call on the host, so
         // ms_total - ms_gemm is the host work around the graph
         stats->ms_total = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t_call).count();

@@ -86,7 +86,18 @@ struct PrepState {
     int32_t d_pad;
 };
 
+// The library's cached device workspace (grow-only). A call running under a
+// WorkspaceCap fails with KNN_ENOMEM instead of growing it past the cap.
 int workspace_get(size_t bytes, void** out);
+struct WorkspaceCap {
+    explicit WorkspaceCap(int64_t bytes);  // 0: no cap
+    ~WorkspaceCap();
+    WorkspaceCap(const WorkspaceCap&) = delete;
+    WorkspaceCap& operator=(const WorkspaceCap&) = delete;
+
+   private:
+    int64_t prev_;
+};
 void workspace_release_all();
 bool is_device_pointer(const void* p);
 int pick_cap(int k, int km);

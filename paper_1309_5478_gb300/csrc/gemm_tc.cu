@@ -22,11 +22,16 @@
 //              max(v_(k+m), v_(k) + 2E_i) (speculatively to lower ranks while only part
 //              of the corpus has been swept), so the list always holds every point whose
 //              exact distance can still be among the row's k smallest.
+//   warps 10-11 exact re-rank (rerank_core.cuh) of the row blocks this CTA has finished,
+//              while the other warps sweep the next one: the re-rank gathers FP32 corpus
+//              rows from HBM while the tensor cores are busy, so the two overlap. They stop
+//              once the epilogue has finished the CTA's last row block; the rows they have
+//              not reached by then are left to the re-rank launch that follows the kernel.
 // Work: row blocks of 128 queries; each CTA sweeps all corpus tiles of a row block
 // (the candidate state of a row lives in one CTA), then hands the rows' lists to the
 // re-rank (which reduces them to the band) and takes the next row block.
-// Every mbarrier wait is bounded; on expiry the kernel records KNN_ETIMEOUT in a status
-// word, stops issuing work, waits (bounded) for its own copies and frees its TMEM.
+// Every wait is bounded (p.wait_limit polls); on expiry the kernel records KNN_ETIMEOUT in
+// a status word, stops issuing work, waits (bounded) for its own copies and frees its TMEM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -34,6 +39,7 @@
 #include "common.cuh"
 #include "engine.h"
 #include "internal.h"
+#include "rerank_core.cuh"
 #include "select_core.cuh"
 #include "tc_fused.h"
 
@@ -44,12 +50,11 @@ constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK_BYTES = 128;  // one 128-byte swizzle row per stage: 64 BF16 or 128 FP8 values
 constexpr int TC_STAGES = 4;
-constexpr int TC_THREADS = 320;  // producer, MMA issuer, 8 epilogue warps
+constexpr int TC_THREADS = 384;  // producer, MMA issuer, 8 epilogue warps, 2 re-rank warps
 constexpr int A_BYTES = TC_BM * TC_BK_BYTES;  // 16 KB
 constexpr int B_BYTES = TC_BN * TC_BK_BYTES;  // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr long long WAIT_LIMIT = 1ll << 26;  // try_wait polls before a wait is declared stuck
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -76,12 +81,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: false when the limit expired or another warp already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    for (long long i = 0; i < WAIT_LIMIT; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, long long limit) {
+    for (long long i = 0; i < limit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((i & 255) == 255 && *abort_flag) return false;
     }
     *abort_flag = 1;
+    return false;
+}
+
+// The same wait taken by a whole warp: every lane observes the phase, and all lanes
+// return the same answer (a warp that gives up leaves together).
+__device__ __forceinline__ bool mbar_wait_all(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                              long long limit) {
+    for (long long i = 0; i < limit; ++i) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if ((i & 255) == 255 && __any_sync(0xffffffffu, *abort_flag != 0)) return false;
+    }
+    if (lane_id() == 0) *abort_flag = 1;
     return false;
 }
 
@@ -171,6 +188,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
 constexpr int MAX_STAGES = 4;
 
 constexpr int EPI_WARPS = 8;   // two per TMEM lane quarter; each takes half of every tile's columns
+constexpr int RR_WARPS = 2;    // re-rank warps (warps 2 + EPI_WARPS ...)
+constexpr int RR_P = 512;      // keys per re-rank warp buffer: longer lists are left to the re-rank launch
 constexpr int RAW_LIST_MAX = 512;  // longest list handed to the re-rank without a trim
 constexpr int HIST_WORDS = 36; // histogram of the sampled select (33 buckets used)
 
@@ -205,9 +224,14 @@ constexpr size_t ROWSTATE_BYTES = 128 * (4 + 8 + 4 + 4);
 
 __host__ __device__ constexpr size_t cn_bytes(int precision) { return (precision == P_FP8 ? 2 : 1) * 2 * TC_BN * 4; }
 
-__host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision) {
+// Re-rank warps' shared memory: a key buffer and an FP64 tie buffer each, and counters.
+constexpr size_t RR_BYTES = RR_WARPS * (static_cast<size_t>(RR_P + TIE_MAX) * 8 + RC_COUNT * 8);
+// mbarriers, TMEM address, abort flag, completion count, and the epilogue pairs' wait results
+constexpr size_t BAR_BYTES = 192;
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision, bool rr) {
     return 1024 /* alignment slack */ + static_cast<size_t>(stages) * STAGE_BYTES + EPI_WARPS * epi_warp_bytes(cap) +
-           cn_bytes(precision) + ROWSTATE_BYTES + 128;
+           cn_bytes(precision) + ROWSTATE_BYTES + BAR_BYTES + (rr ? RR_BYTES : 0);
 }
 
 __host__ __device__ constexpr size_t scratch_words_per_warp(int cap) {
@@ -681,6 +705,32 @@ __device__ __forceinline__ void pair_barrier(int quarter) {
     asm volatile("bar.sync %0, 64;" ::"r"(1 + quarter) : "memory");
 }
 
+// Waits (bounded) until the epilogue warps' completion count reaches `target` (each
+// epilogue warp adds one per finished row block). Called by the whole warp; lane 0 polls.
+// False when the kernel is giving up.
+__device__ __forceinline__ bool wait_epilogue(const volatile int* ep_done, int target, volatile int* abort_flag,
+                                              long long limit) {
+    int ok = 0;
+    if (lane_id() == 0) {
+        for (long long i = 0;; ++i) {
+            if (*ep_done >= target) {
+                __threadfence_block();  // the lists, counts and flags written before the count was raised
+                ok = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            if (i >= limit) {
+                *abort_flag = 1;
+                break;
+            }
+            __nanosleep(256);
+        }
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+
 template <int P, bool BATCHED, int KPL>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     fused_gemm_select_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -704,8 +754,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     uint64_t* empty = bars + MAX_STAGES;          // [MAX_STAGES]
     uint64_t* acc_full = bars + 2 * MAX_STAGES;   // [2]
     uint64_t* acc_empty = acc_full + 2;           // [2]
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acc_empty + 2);
+    uint64_t* drain = acc_empty + 2;              // [1]: completion of every MMA issued
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    int* ep_done = reinterpret_cast<int*>(tmem_holder + 2);  // epilogue warps' finished row blocks
+    volatile int* pair_ok = reinterpret_cast<volatile int*>(reinterpret_cast<unsigned char*>(bars) + 128);  // [8]
+    unsigned char* rr_base = reinterpret_cast<unsigned char*>(bars) + BAR_BYTES;  // RR_BYTES when p.rr_on
+    const long long wait_limit = p.wait_limit > 0 ? p.wait_limit : (1ll << 26);
 
     const int warp = static_cast<int>(threadIdx.x / 32);
     const uint32_t lane = lane_id();
@@ -721,7 +776,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(&acc_full[a], 2);  // the norms' copy (arrive + bytes) and the MMA commit
             mbar_init(&acc_empty[a], EPI_WARPS);
         }
+        mbar_init(drain, 1);
         *abort_flag = 0;
+        *ep_done = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -746,7 +803,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
                 for (int ct = 0; ct < im.nct && ok; ++ct) {
                     for (int ks = 0; ks < im.nk; ++ks) {
-                        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+                        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, wait_limit)) {
                             ok = false;
                             break;
                         }
@@ -764,7 +821,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (ok) {
                 // drain: every stage filled has been consumed
                 for (int i = 0; i < nst; ++i) {
-                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+                    if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, wait_limit)) break;
                     if (++s == nst) {
                         s = 0;
                         ph ^= 1u;
@@ -790,19 +847,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ph = 0;
             int tile = 0;
             bool ok = true;
+            int copy_acc = -1;  // accumulator whose norms copy is in flight without its commit
+            uint32_t copy_ph = 0;
             const int k_per_mma = 32;  // bytes of K per instruction: 16 BF16 or 32 FP8 values
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
                 for (int ct = 0; ct < im.nct && ok; ++ct, ++tile) {
                     const int acc = tile & 1;
                     const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
-                    if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1u, abort_flag)) {
+                    if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1u, abort_flag, wait_limit)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     // stage this tile's corpus norms (and FP8 scales) for the epilogue
                     mbar_expect_tx(&acc_full[acc], CN_TX);
+                    copy_acc = acc;
+                    copy_ph = acc_ph;
                     const int64_t cphys = static_cast<int64_t>(tile_at(im, ct)) * TC_BN;
                     bulk_copy_g2s(cn_smem + acc * TC_BN, im.cnorm2 + cphys, TC_BN * 4, &acc_full[acc]);
                     if constexpr (P == P_FP8)
@@ -810,7 +871,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                       &acc_full[acc]);
                     const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
                     for (int ks = 0; ks < im.nk; ++ks) {
-                        if (!mbar_wait(&full[s], ph, abort_flag)) {
+                        if (!mbar_wait(&full[s], ph, abort_flag, wait_limit)) {
                             ok = false;
                             break;
                         }
@@ -828,12 +889,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             ph ^= 1u;
                         }
                     }
-                    if (ok) umma_commit(&acc_full[acc]);
+                    if (ok) {
+                        umma_commit(&acc_full[acc]);
+                        copy_acc = -1;
+                    }
                 }
             }
+            if (!ok && copy_acc >= 0) {
+                // gave up after staging a tile's norms: arrive in place of the missing commit
+                // and let the copy land before the CTA exits
+                mbar_arrive(&acc_full[copy_acc]);
+                for (int spin = 0; spin < (1 << 20); ++spin)
+                    if (mbar_try_wait(&acc_full[copy_acc], copy_ph)) break;
+            }
+            // every MMA issued completes before the TMEM is freed
+            umma_commit(drain);
+            for (int spin = 0; spin < (1 << 20); ++spin)
+                if (mbar_try_wait(drain, 0)) break;
         }
         __syncwarp();
-    } else {
+    } else if (warp < 2 + EPI_WARPS) {
         // ------------------------------ epilogue ----------------------------------
         const int ew = warp - 2;                  // epilogue warp 0..7
         const int quarter = warp & 3;             // TMEM lane quarter this warp may read
@@ -896,11 +971,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int ct = 0; ct < nct; ++ct, ++tile) {
                 const int acc = tile & 1;
                 const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
-                if (!mbar_wait(&acc_full[acc], acc_ph, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
+                // the two warps of a lane quarter meet at named barriers: a warp whose wait
+                // gives up still takes the tile's first one, where the pair decides together
+                const bool got = mbar_wait_all(&acc_full[acc], acc_ph, abort_flag, wait_limit);
+                if (got) tc_fence_after();
                 const int c0 = half * (TC_BN / 2);  // first column of this warp's half
                 const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                        static_cast<uint32_t>(acc * TC_BN + c0);
@@ -910,23 +984,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 uint32_t ra[32], rb2[32];
 #pragma unroll 1
                 for (int hs = 0; hs < 2; ++hs) {
-                    // two chunks of 32 columns, the second load overlapping the first filter
-                    tmem_ld32(taddr + hs * 64, ra);
-                    tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
-                    filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf, my_cnt,
-                                    seg_base, seg_dir, inserted);
-                    tmem_ld_wait();
-                    filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self, tau_f,
-                                    gbuf, my_cnt, seg_base, seg_dir, inserted);
-                    if (hs == 1) {
-                        // accumulator and staged norms of this tile no longer needed by this warp
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                    if (got) {
+                        // two chunks of 32 columns, the second load overlapping the first filter
+                        tmem_ld32(taddr + hs * 64, ra);
+                        tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
+                        filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf,
+                                        my_cnt, seg_base, seg_dir, inserted);
+                        tmem_ld_wait();
+                        filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self,
+                                        tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted);
+                        if (hs == 1) {
+                            // accumulator and staged norms of this tile no longer needed by this warp
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+                        }
                     }
                     // both warps of the quarter have finished this half-tile: shrink full lists
                     rs.cnt[2 * row_in_block + half] = static_cast<uint16_t>(my_cnt);
+                    if (hs == 0 && lane == 0) pair_ok[2 * quarter + half] = got ? 1 : 0;
                     pair_barrier(quarter);
+                    if (hs == 0 && !(pair_ok[2 * quarter] && pair_ok[2 * quarter + 1])) {
+                        ok = false;  // both warps of the pair leave here, after the same barriers
+                        break;
+                    }
                     const int total = rs.cnt[2 * row_in_block] + rs.cnt[2 * row_in_block + 1];
                     uint32_t need = __ballot_sync(0xffffffffu, valid && total > trigger);
                     need &= partner_bit ? 0xaaaaaaaau : 0x55555555u;
@@ -949,6 +1030,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     tau_f = rs.tauf[row_in_block];
                     my_cnt = rs.cnt[2 * row_in_block + half];
                 }
+                if (!ok) break;
             }
             if (!ok) break;
             // row block done: each row's list (both segments, every key <= its threshold)
@@ -988,12 +1070,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             // the next row block reinitialises the row state only after both warps are done
             pair_barrier(quarter);
+            // this warp is done with the row block: the re-rank warps may take it once all are
+            if (lane == 0) {
+                __threadfence_block();
+                atomicAdd(ep_done, 1);
+            }
         }
         if (!ok && lane == 0) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
         if (params.inserted) {
             const uint32_t w = __reduce_add_sync(0xffffffffu, inserted);
             if (lane == 0 && w) atomicAdd(params.inserted, static_cast<unsigned long long>(w));
         }
+    } else if (!BATCHED && p.rr_on) {
+        // ------------------------------ re-rank -----------------------------------
+        // The rows of every row block the epilogue has finished, while it sweeps the next
+        // one; the CTA's last row block (and any rows not reached when the epilogue ends)
+        // are left to the re-rank launch after the kernel, which skips rows marked done.
+        const int rw = warp - 2 - EPI_WARPS;
+        uint64_t* K = reinterpret_cast<uint64_t*>(rr_base) + static_cast<size_t>(rw) * (RR_P + TIE_MAX);
+        double* T64 = reinterpret_cast<double*>(K + RR_P);
+        unsigned long long* cnt =
+            reinterpret_cast<unsigned long long*>(rr_base + RR_WARPS * static_cast<size_t>(RR_P + TIE_MAX) * 8) +
+            rw * RC_COUNT;
+        if (lane < RC_COUNT) cnt[lane] = 0ull;
+        __syncwarp();
+        const int mine = (n_items - static_cast<int>(blockIdx.x) + static_cast<int>(gridDim.x) - 1) /
+                         static_cast<int>(gridDim.x);
+        const int all_done = EPI_WARPS * mine;
+        bool go = true;
+        int j = 0;
+        for (int it = blockIdx.x; it < n_items && go; it += gridDim.x, ++j) {
+            if (!wait_epilogue(ep_done, EPI_WARPS * (j + 1), abort_flag, wait_limit)) break;
+            for (int r = rw; r < TC_BM; r += RR_WARPS) {
+                const int done = __shfl_sync(0xffffffffu, *reinterpret_cast<volatile int*>(ep_done), 0);
+                if (done >= all_done) {
+                    go = false;
+                    break;
+                }
+                const int64_t grow = static_cast<int64_t>(it) * TC_BM + r;
+                if (grow >= p.M) break;
+                if (list_length(p.count[grow], p.flags[grow]) > RR_P) continue;
+                rerank_row<true, 4>(p.rr, grow, RR_P, K, T64, cnt, lane);
+            }
+        }
+        __syncwarp();
+        if (lane == 0) flush_rerank_counts(p.rr.counters, cnt, true);
     }
 
     tc_fence_before();
@@ -1052,10 +1173,10 @@ int fused_cap(int k, int km) {
     return c < 448 ? 448 : c;
 }
 
-int fused_stages(int cap, int precision) {
+int fused_stages(int cap, int precision, bool rr) {
     if (cap > FUSED_CAP_MAX) return 0;  // a list is staged as at most 48 keys per lane
     for (int st = MAX_STAGES; st >= 2; --st)
-        if (tc_smem_bytes(cap, st, precision) <= 232448) return st;
+        if (tc_smem_bytes(cap, st, precision, rr) <= 232448) return st;
     return 0;
 }
 
@@ -1086,7 +1207,7 @@ cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, 
     if (p.n_items <= 0) return cudaSuccess;
     if (p.cap_max > FUSED_CAP_MAX) return cudaErrorInvalidValue;
     CUtensorMap dummy{};
-    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
+    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, false);
     auto kern = fused_kernel<true>(precision, p.cap_max);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -1101,7 +1222,8 @@ cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStre
     CUtensorMap ta, tb;
     if (!make_map(&ta, p.xq, p.M, p.k_bytes, TC_BM, elem)) return cudaErrorInvalidValue;
     if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
-    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision);
+    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, p.rr_on != 0);
+    if (smem > 232448) return cudaErrorInvalidValue;
     auto kern = fused_kernel<false>(precision, p.cap_max);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;

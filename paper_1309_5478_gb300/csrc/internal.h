@@ -33,6 +33,7 @@ enum RowFlag : uint32_t {
 enum RowStatus : uint32_t {
     ROW_UNCERTIFIED = 1u,  // the re-rank could not prove the answer exact
     ROW_FP64 = 2u,         // FP64 decided a near tie in this row
+    ROW_RERANKED = 4u,     // the re-rank has written this row's answer
 };
 
 // Counters accumulated by the re-rank (device memory, zeroed per call).
@@ -43,7 +44,8 @@ struct RerankCounters {
     unsigned long long truncated;
     unsigned long long threshold_miss;
     unsigned long long inserted;  // keys the fused sweep appended to candidate lists
-    unsigned long long pad[2];
+    unsigned long long max_err_ratio;  // float bits of the largest |approximate - exact| / E of a candidate
+    unsigned long long rows_in_sweep;  // rows re-ranked by the fused kernel during its sweep
 };
 
 // ---- prep / bounds (prep.cu) ----
@@ -124,6 +126,8 @@ struct RerankParams {
     uint32_t* row_status;  // M
     RerankCounters* counters;
     int32_t count_min, count_max;  // rows whose list length lies outside are skipped (set by launch_rerank)
+    int32_t skip_done;     // 1: rows whose row_status has ROW_RERANKED are skipped (re-ranked earlier)
+    const int* status;     // optional device status word: when non-zero nothing is re-ranked
 };
 // Lists longer than 512 (and 1024) keys are re-ranked by further launches with larger
 // per-warp buffers, so the common short lists keep the higher occupancy.

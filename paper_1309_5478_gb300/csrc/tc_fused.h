@@ -8,6 +8,8 @@
 
 #include <cuda.h>
 
+#include "internal.h"
+
 namespace knn {
 
 // One problem of a batched launch (device memory, 64-byte aligned for the tensor maps).
@@ -65,6 +67,10 @@ struct FusedParams {
     float spec_d2;             // speculative start threshold in squared distance for every row (+inf: none)
     const FusedProblem* problems;  // batched launch: problem descriptors (else nullptr)
     const FusedWork* work;     // batched launch: work list, largest items first
+    long long wait_limit;      // polls of a bounded wait before the kernel gives up (0: 2^26)
+    int32_t rr_on;             // 1: two extra warps re-rank finished row blocks during the sweep
+                               // (non-batched launch; shared memory sized with rr = true)
+    RerankParams rr;           // the re-rank of the whole problem (rows indexed like the lists)
 };
 
 // Largest candidate-list capacity of the fused form (48 keys per lane of a warp), and the
@@ -74,7 +80,9 @@ constexpr int FUSED_CAP_MAX = 1536;
 constexpr int FUSED_CAP_WIDE = 1024;
 
 bool fused_available();
-int fused_stages(int cap, int precision);  // 0: does not fit
+// Pipeline stages that fit with lists of capacity cap (and the re-rank warps' buffers when
+// rr); 0: does not fit.
+int fused_stages(int cap, int precision, bool rr = false);
 size_t fused_scratch_words(int cap, int grid);
 int fused_cap(int k, int km);
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st);

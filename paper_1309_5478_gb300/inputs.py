@@ -163,6 +163,42 @@ def anisotropic_mixture(n: int = 524288, d: int = 768, components: int = 256, me
     return out
 
 
+STRESS_KINDS = ("offset", "binades_bf16", "binades_fp8", "parallel")
+
+
+def accumulation_stress(kind: str, n: int, d: int, seed: int = SEED_BASE + 8) -> np.ndarray:
+    """Points chosen to stress the reduced-precision distance product (FP32 values).
+
+    offset:       100 + N(0, 1) per coordinate (a large common offset: |c|^2 and 2 q.c cancel);
+    binades_bf16: +-m 2^(e - 7), m uniform in {128..255}, e uniform in {-12..0}: every value is
+                  exactly a BF16 number, spread over 13 binades (the rounding residual is zero, so
+                  only the accumulation of the products is inexact);
+    binades_fp8:  +-m 2^(e - 3), m uniform in {8..15}, e uniform in {-6..0}: exactly e4m3
+                  numbers (up to a power-of-two row scale) over 7 binades;
+    parallel:     unit rows (b + 0.01 g) / |b + 0.01 g| around one random unit direction b, with g
+                  standard normal scaled by 1/sqrt(d): near-parallel directions.
+    """
+    count = n * d
+    if kind == "offset":
+        x = 100.0 + normal(seed, S_VALUES, 0, count)
+    elif kind in ("binades_bf16", "binades_fp8"):
+        bits, e_lo = (7, -12) if kind == "binades_bf16" else (3, -6)
+        m = (1 << bits) + _index_draw(seed, S_VALUES, count, 1 << bits)
+        e = e_lo + _index_draw(seed, S_SCALES, count, 1 - e_lo)
+        sign = np.where(_index_draw(seed, S_COMPONENT, count, 2) == 0, -1.0, 1.0)
+        x = sign * np.ldexp(m.astype(np.float64), (e - bits).astype(np.int64))
+    elif kind == "parallel":
+        b = normal(seed, S_MEANS, 0, d)
+        b /= np.sqrt((b * b).sum())
+        g = normal(seed, S_VALUES, 0, count).reshape(n, d) / math.sqrt(d)
+        y = b[None, :] + 0.01 * g
+        y /= np.sqrt((y * y).sum(axis=1, keepdims=True))
+        return y.astype(np.float32)
+    else:
+        raise ValueError(f"unknown stress kind {kind!r}")
+    return x.reshape(n, d).astype(np.float32)
+
+
 def uniform_matrix(rows: int, cols: int, seed: int = SEED_BASE + 6) -> np.ndarray:
     """Uniformly random FP32 values in [0, 1): the paper's selection test matrices."""
     out = np.empty((rows, cols), dtype=np.float32)

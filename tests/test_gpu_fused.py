@@ -216,3 +216,55 @@ def test_large_k_float_search():
     rows = np.arange(0, 300, 10)
     ref_idx, ref_dist = oracle.knn(Q, C, 500, rows=rows)
     check_float(Q, C, rows, idx.cpu().numpy()[rows], dist.cpu().numpy()[rows], ref_idx, ref_dist, False)
+
+
+@pytest.fixture
+def rerank_in_sweep(monkeypatch):
+    def set_rr(on):
+        monkeypatch.setenv("KNN_RERANK_IN_SWEEP", "1" if on else "0")
+    return set_rr
+
+
+def test_rerank_in_sweep_integer_bit_exact(rerank_in_sweep):
+    # 313 row blocks: the fused kernel's re-rank warps take the rows of finished row
+    # blocks during the sweep, the launch after the kernel the rest
+    X = inputs.integer_lattice(n=40000, d=128, seed=81)
+    rerank_in_sweep(True)
+    a = graph(X, 16)
+    assert 0 < a[2]["rows_reranked_in_sweep"] < len(X), a[2]
+    rerank_in_sweep(False)
+    b = graph(X, 16)
+    assert b[2]["rows_reranked_in_sweep"] == 0
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    rows = inputs.sample_rows(len(X), 64, seed=82)
+    check_exact(a[0][rows], a[1][rows], *oracle.knng(X, 16, rows=rows))
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_rerank_in_sweep_float_identical(precision, rerank_in_sweep):
+    X, t, s = inputs.unit_directions_with_duplicates(n=40000, d=256, seed=83)
+    rerank_in_sweep(True)
+    a = graph(X, 64, precision)
+    rerank_in_sweep(False)
+    b = graph(X, 64, precision)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert a[2]["rows_uncertified"] == b[2]["rows_uncertified"]
+    rows = np.concatenate([t[:8], inputs.sample_rows(len(X), 24, seed=84)])
+    ref_idx, ref_dist = oracle.knng(X, 64, rows=rows)
+    check_float(X, X, rows, a[0][rows], a[1][rows], ref_idx, ref_dist, exclude_self=True)
+
+
+@pytest.mark.parametrize("d", [1024, 4096])
+@pytest.mark.parametrize("kind", inputs.STRESS_KINDS)
+@pytest.mark.parametrize("precision", ["bf16", "fp8"])
+def test_gemm_error_stays_within_its_bound(precision, kind, d):
+    # every certificate rests on |approximate - exact| <= E_i for the GEMM's ranking value;
+    # the re-rank measures that ratio on every candidate it evaluates
+    X = inputs.accumulation_stress(kind, n=2048, d=d)
+    idx, dist, st = graph(X, 16, precision)
+    ratio = st["max_error_ratio"]
+    print(f"{precision} {kind} d={d}: max |approx - exact| / E = {ratio:.4g}")
+    assert 0.0 < ratio <= 1.0, st
+    rows = inputs.sample_rows(len(X), 16, seed=85)
+    ref_idx, ref_dist = oracle.knng(X, 16, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
