@@ -47,13 +47,17 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--d", type=int, default=D_DEFAULT)
     ap.add_argument("--k", type=int, default=K_DEFAULT)
-    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 comparison step")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP32 and FP8 comparison steps")
+    ap.add_argument("--compare-repeats", type=int, default=3,
+                    help="timed repeats (after one warm-up call) of each comparison form; the median is reported")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--mode", choices=["knng", "select", "select_sweep", "batch", "mlp", "metric", "streamed"],
+    ap.add_argument("--mode", choices=["knng", "plain", "select", "select_sweep", "batch", "mlp", "metric", "streamed"],
                     default="knng",
-                    help="select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
+                    help="plain: the plain FP32 form on the integer lattice (--workload lattice: N=4096, d=128, k=16) "
+                         "or the Gaussian mixture (--workload mixture: N=65536, d=256, k=32); "
+                         "select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
                          "metric: the cosine and Pearson similarity graphs of the headline data; "
                          "streamed: search of 65536 queries against a 4M x 256 corpus read from pinned host "
                          "memory in 1M-row chunks, against the same search with the corpus resident; "
@@ -62,6 +66,7 @@ def parse():
                          "batch: 512 independent search problems of uneven shape in one graph; "
                          "mlp: k-NN graph of a 524288 x 768 anisotropic mixture, k=100, with learned per-row "
                          "thresholds against the same graph without them")
+    ap.add_argument("--workload", choices=sorted(PLAIN_WORKLOADS), default="lattice", help="plain mode: workload")
     ap.add_argument("--train-rows", type=int, default=50000, help="mlp mode: training rows")
     ap.add_argument("--epochs", type=int, default=40, help="mlp mode: training epochs")
     ap.add_argument("--problems", type=int, default=512, help="batch mode: number of problems")
@@ -317,6 +322,92 @@ def run_select_only(args):
                                      if (args.q, args.cols, k) == (16384, 65536, 64) else None),
                          "kernel": "select_rows_kernel", "peak_source": P["source"]},
             "clocks": clk, "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+
+
+PLAIN_WORKLOADS = {
+    # name: (generator, k, description)
+    "lattice": (lambda: __import__("paper_1309_5478_gb300.inputs", fromlist=["x"]).integer_lattice(), 16,
+                "k-NN graph, N=4096 integer points uniform in [-8,8]^128, k=16"),
+    "mixture": (lambda: __import__("paper_1309_5478_gb300.inputs", fromlist=["x"]).gaussian_mixture(), 32,
+                "k-NN graph, N=65536 points of a 64-component Gaussian mixture in d=256 "
+                "(means N(0,4I), sigma 0.5), k=32"),
+}
+
+
+def run_plain(args):
+    """The plain FP32 form (SIMT distance GEMM writing the d' matrix in row slabs, the unfused
+    quick multi-select over it, exact re-rank) on the two smaller graph configurations. Each
+    step is one knng_build call, timed by CUDA events, with a 256 MB L2 flush before it
+    (outside the timed region). Reports rows/s, the select's achieved HBM bandwidth on the
+    d' slabs (4 bytes per matrix entry read once, over the select launches' device time), the
+    GEMM's FP32 rate, and the output checked against the FP64 oracle."""
+    import torch
+    import oracle
+    from paper_1309_5478_gb300 import binding as kb
+    gen, k, desc = PLAIN_WORKLOADS[args.workload]
+    X = gen()
+    n, d = X.shape
+    P = peaks()
+    Xd = torch.from_numpy(X).cuda()
+    oi = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    od = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def call():
+        return kb.knng_build(Xd, k, out_idx=oi, out_dist=od, precision="fp32", fused=0,
+                             flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True)[2]
+
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times, stats = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        stats.append(call())
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    clk = clocks.stop()
+    ms = float(np.sum(times)) / args.steps
+    ms_sel = float(np.mean([s["ms_select"] for s in stats]))
+    ms_gemm = float(np.mean([s["ms_gemm"] for s in stats]))
+    ms_rr = float(np.mean([s["ms_rerank"] for s in stats]))
+    sel_bytes = 4.0 * n * n
+    sel_gbs = sel_bytes / (ms_sel / 1000.0) / 1e9
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * P["sm_max_mhz"] * 1e6 / 1e12
+    gemm_tf = 2.0 * n * n * d / (ms_gemm / 1000.0) / 1e12
+    idx, dist = oi.cpu().numpy(), od.cpu().numpy()
+    from paper_1309_5478_gb300 import inputs
+    rows = np.arange(n) if args.workload == "lattice" else inputs.sample_rows(n, 256, seed=78)
+    t0 = time.perf_counter()
+    ri, rd = oracle.knng(X, k, rows=rows)
+    t_cpu = time.perf_counter() - t0
+    check = oracle_check(X, rows, idx[rows], dist[rows], ri, rd)
+    if args.workload == "lattice":
+        check["bit_exact"] = bool(np.array_equal(idx.astype(np.int64), ri) and np.array_equal(dist.astype(np.float64), rd))
+    line = {"metric": f"exact k-NNG rows/s, plain FP32 form ({args.workload})", "value": n / (ms / 1000.0),
+            "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "N": n, "d": d, "k": k, "form": "plain-fp32",
+                       "l2": "256 MB written between steps (outside the timed region)"},
+            "roofline": {"bound": "hbm", "achieved": sel_gbs, "peak": P["hbm_gbs"], "unit": "GB/s",
+                         "frac": sel_gbs / P["hbm_gbs"], "kernel": "select_rows_kernel",
+                         "traffic": None, "peak_source": P["source"],
+                         "algorithmic_bytes": sel_bytes, "launch_ms": ms_sel},
+            "gemm": {"kernel": "gemm_dprime_kernel", "ms": ms_gemm, "tflops": gemm_tf, "alu_peak_tflops": alu_peak,
+                     "frac": gemm_tf / alu_peak},
+            "phases_ms": {"gemm": ms_gemm, "select": ms_sel, "rerank": ms_rr, "prep": stats[-1]["ms_prep"],
+                          "fallback": stats[-1]["ms_fallback"]},
+            "clocks": clk, "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
+            "oracle_check": check,
+            "cpu_baseline": {"value": len(rows) / t_cpu, "unit": "rows/s", "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{len(rows)} rows of the same graph, {t_cpu:.1f} s"}}
     print(json.dumps(line), flush=True)
 
 
@@ -688,6 +779,24 @@ def weak_scaling_rate(rows_per_rank: int, world: int, seconds_slowest: float) ->
     return world * rows_per_rank / seconds_slowest
 
 
+def timed_calls(fn, stream, repeats: int):
+    """One untimed call, then `repeats` calls each timed by CUDA events on `stream`;
+    returns (median ms, the last call's result)."""
+    import torch
+    fn()
+    times, out = [], None
+    for _ in range(max(1, repeats)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    return float(np.median(times)), out
+
+
 def workload_config(args, form: str) -> dict:
     return {"workload": f"k-NN graph, N={args.n} unit-norm Gaussian directions in d={args.d} with 1% exact "
                         f"duplicates, k={args.k}, squared Euclidean", "N": args.n, "d": args.d, "k": args.k,
@@ -703,10 +812,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.mode in ("select", "select_sweep", "batch", "mlp", "metric", "streamed"):
+    if args.mode in ("plain", "select", "select_sweep", "batch", "mlp", "metric", "streamed"):
         import torch
         torch.cuda.set_device(local)
-        {"select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
+        {"plain": run_plain, "select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
          "mlp": run_mlp, "metric": run_metric, "streamed": run_streamed}[args.mode](args)
         return
 
@@ -811,35 +920,32 @@ def main():
             "exactness": {"rows_uncertified": int(s0["rows_uncertified"]), "rows_fallback": int(s0["rows_fallback"]),
                           "rows_fp64_ties": int(s0["rows_fp64_ties"]), "rows_truncated": int(s0["rows_truncated"]),
                           "candidates_per_row": s0["candidates"] / max(1, s0["rows"]),
-                          "inserted_per_row": s0["candidates_inserted"] / max(1, s0["rows"])},
+                          "inserted_per_row": s0["candidates_inserted"] / max(1, s0["rows"]),
+                          "rows_reranked_in_sweep": int(s0["rows_reranked_in_sweep"]),
+                          "list_capacity": int(s0["list_capacity"]),
+                          "max_error_ratio": float(s0["max_error_ratio"])},
             "phases_ms": {"prep": s0["ms_prep"], "gemm_select": s0["ms_select"], "rerank": s0["ms_rerank"],
                           "fallback": s0["ms_fallback"], "gemm": s0["ms_gemm"]}}
 
-    # the plain FP32 form on the same data, for the reported factor
+    # the plain FP32 form on the same data, for the reported factor: one warm-up call, then the
+    # median of the timed repeats (CUDA events on the call's stream), like the headline
     if form == "fused" and not args.no_compare and rank == 0:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        sp = step("fp32", 0)[2]
-        torch.cuda.synchronize()
-        dtp = time.perf_counter() - t0
-        line["plain_fp32"] = {"rows_per_s": args.n / dtp, "ms_per_step": dtp * 1000.0, "gemm_ms": sp["ms_gemm"],
-                              "single_step": True}
-        line["fused_vs_plain"] = (args.n / dtp) and rows_per_s / world / (args.n / dtp)
+        ms_p, sp = timed_calls(lambda: step("fp32", 0)[2], stream, args.compare_repeats)
+        line["plain_fp32"] = {"rows_per_s": args.n / (ms_p / 1000.0), "ms_per_step": ms_p,
+                              "gemm_ms": sp["ms_gemm"], "repeats": args.compare_repeats, "warmup": 1}
+        line["fused_vs_plain"] = rows_per_s / world / (args.n / (ms_p / 1000.0))
 
     # the FP8 e4m3 form on the same data: time, how many rows its first pass certified, fallback
     fp8_out = None
     if form == "fused" and not args.no_compare and rank == 0:
         try:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s8 = step("fp8", 1)[2]
-            torch.cuda.synchronize()
-            dt8 = time.perf_counter() - t0
+            ms8, s8 = timed_calls(lambda: step("fp8", 1)[2], stream, args.compare_repeats)
             fp8_out = (oi.cpu().numpy(), od.cpu().numpy())
-            line["fp8"] = {"rows_per_s": args.n / dt8, "ms_per_step": dt8 * 1000.0, "ms_gemm": s8["ms_gemm"],
+            line["fp8"] = {"rows_per_s": args.n / (ms8 / 1000.0), "ms_per_step": ms8, "ms_gemm": s8["ms_gemm"],
                            "rows_certified_first_pass": int(args.n - s8["rows_uncertified"]),
                            "rows_fallback": int(s8["rows_fallback"]), "candidates_per_row": s8["candidates"] / args.n,
-                           "single_step": True}
+                           "max_error_ratio": float(s8["max_error_ratio"]),
+                           "repeats": args.compare_repeats, "warmup": 1}
         except kb.KnnError as e:
             line["fp8"] = {"unavailable": str(e)}
 
