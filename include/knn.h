@@ -91,6 +91,8 @@ typedef struct knn_stats {
                                   ranking value (exactness rests on this ratio staying <= 1) */
     int64_t rows_reranked_in_sweep; /* fused form: rows re-ranked by the fused kernel while it swept
                                        later row blocks (the rest by the re-rank launch after it) */
+    int32_t symmetric;         /* k-NN graph: 1 when the fused launch computed each pair's product once,
+                                  for both of its rows (the symmetric half of the distance product) */
 } knn_stats;
 
 typedef struct knn_options {

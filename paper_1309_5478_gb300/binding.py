@@ -33,7 +33,7 @@ class KnnStats(ctypes.Structure):
                 ("precision_used", ctypes.c_int32), ("fused_used", ctypes.c_int32),
                 ("exact_arithmetic", ctypes.c_int32), ("list_capacity", ctypes.c_int32),
                 ("candidates_inserted", ctypes.c_int64), ("max_error_ratio", ctypes.c_float),
-                ("rows_reranked_in_sweep", ctypes.c_int64)]
+                ("rows_reranked_in_sweep", ctypes.c_int64), ("symmetric", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -323,7 +323,7 @@ void layout_common(const Problem& pb, int prec, bool with_fallback_plain, Arena&
 }
 
 int prep_and_check(const Problem& pb, int prec, CommonLayout& L, cudaStream_t st, knn_stats* stats,
-                   Timing& tm) {
+                   Timing& tm, bool sym_extra = false) {
     const PrepState& ps = L.ps;
     const bool same = pb.graph;
     KNN_CK(cudaMemsetAsync(ps.gq, 0, sizeof(PrepGlobals), st));
@@ -336,7 +336,7 @@ int prep_and_check(const Problem& pb, int prec, CommonLayout& L, cudaStream_t st
         KNN_CK(launch_prep(pb.Q, pb.M, pb.d, prec, ps.qnorm2, ps.qres, ps.qtn, ps.xq, ldq, ps.qscale, ps.gq, st));
         ++tm.launches;
     }
-    KNN_CK(launch_bounds(ps.qnorm2, ps.qres, ps.qtn, pb.M, pb.d, ps.d_pad, prec, ps.gq, ps.gc, ps.E, st));
+    KNN_CK(launch_bounds(ps.qnorm2, ps.qres, ps.qtn, pb.M, pb.d, ps.d_pad, prec, ps.gq, ps.gc, ps.E, st, sym_extra));
     ++tm.launches;
     if (prec != P_FP32) {
         KNN_CK(launch_bounds(ps.qnorm2, nullptr, nullptr, pb.M, pb.d, pb.d, P_FP32, ps.gq, ps.gc, L.E32, st));
@@ -621,6 +621,9 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
                                    L.fb_qscale, st));
         FusedParams fp = first;
         fp.rr_on = 0;  // the second pass re-ranks its gathered rows after the kernel
+        fp.sym = 0;    // and sweeps every column of its rows
+        fp.inbox = nullptr;
+        fp.inbox_cnt = nullptr;
         fp.xq = L.fb_xq;
         fp.M = n;
         fp.cap = cap2;
@@ -702,6 +705,25 @@ int tile_stride(int64_t n) {
     return 1;
 }
 
+// The symmetric form of a k-NN graph (half the distance product; KNN_SYMMETRIC=0 turns it
+// off): it needs the probe's start threshold, which it also takes as the threshold of the
+// transposed pairs.
+bool symmetric_enabled() {
+    const char* e = std::getenv("KNN_SYMMETRIC");
+    return !e || std::atoi(e) != 0;
+}
+
+// Pairs (i, j) the symmetric form's fused launch computes: row block rb (128 rows) sweeps
+// the columns from 256 (rb / 2) on.
+double symmetric_pairs(int64_t M, int64_t N) {
+    double pairs = 0.0;
+    for (int64_t rb = 0; rb * 128 < M; ++rb) {
+        const int64_t rows = std::min<int64_t>(128, M - rb * 128);
+        pairs += static_cast<double>(rows) * static_cast<double>(N - 256 * (rb / 2));
+    }
+    return pairs;
+}
+
 // Polls of a bounded device-side wait before a kernel gives up (0: the kernel's default).
 // KNN_WAIT_LIMIT overrides it, so that the give-up path can be exercised.
 long long wait_limit() {
@@ -744,6 +766,11 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     const int grid = static_cast<int>(std::min<int64_t>(sms, nrb));
     uint64_t* scratch = nullptr;
     ProbeBuffers pr;
+    // symmetric graph form: transposed pairs land in per-row inboxes
+    const bool sym_want = pb.graph && probe && speculate(pb) && spec_start() && symmetric_enabled();
+    const int cap_in = FUSED_CAP_WIDE;
+    uint64_t* inbox = nullptr;
+    int32_t* inbox_cnt = nullptr;
     auto layout = [&](Arena& ar) {
         layout_common(pb, prec, true, ar, L);
         cand = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap_alloc);
@@ -751,6 +778,10 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
         bound = ar.take<uint64_t>(pb.M);
         flags = ar.take<uint32_t>(pb.M);
         scratch = ar.take<uint64_t>(fused_scratch_words(FUSED_CAP_MAX, grid));  // also serves the second pass
+        if (sym_want) {
+            inbox = ar.take<uint64_t>(static_cast<size_t>(pb.M) * cap_in);
+            inbox_cnt = ar.take<int32_t>(pb.M);
+        }
         if (probe) {
             pr.rows = ar.take<int32_t>(PROBE_ROWS);
             pr.Qs = ar.take<float>(static_cast<size_t>(PROBE_ROWS) * pb.d);
@@ -777,7 +808,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     Events ev;
     KNN_TRY(ev.init(tm.on));
     KNN_TRY(ev.rec(0, st));
-    KNN_TRY(prep_and_check(pb, prec, L, st, stats, tm));
+    KNN_TRY(prep_and_check(pb, prec, L, st, stats, tm, sym_want));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
     float spec_d2 = __builtin_huge_valf();
@@ -818,6 +849,20 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.qnorm2 = L.ps.qnorm2;
     fp.spec_d2 = spec_d2;
     fp.wait_limit = wait_limit();
+    const bool sym = sym_want && std::isfinite(spec_d2);
+    if (sym) {
+        // no speculative ranks mid-sweep: the start threshold alone is speculative, and the
+        // certificate checks it for every row (rows it rejects take the second pass)
+        fp.sym = 1;
+        fp.sym_t = spec_d2;
+        fp.inbox = inbox;
+        fp.inbox_cnt = inbox_cnt;
+        fp.cap_in = cap_in;
+        fp.c2max_bits = &L.ps.gc->max_norm2;
+        fp.spec = 0;
+        fp.perm_a = 1;
+        KNN_CK(cudaMemsetAsync(inbox_cnt, 0, static_cast<size_t>(pb.M) * sizeof(int32_t), st));
+    }
 
     RerankParams rp{};
     rp.Q = pb.Q;
@@ -838,9 +883,15 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     rp.row_status = L.row_status;
     rp.counters = L.counters;
     rp.status = L.status;  // nothing is re-ranked after the fused kernel gave up
+    if (sym) {
+        rp.inbox = inbox;
+        rp.inbox_cnt = inbox_cnt;
+        rp.cap_in = cap_in;
+    }
     // the re-rank of finished row blocks overlaps the sweep of later ones; the launch after
-    // the kernel takes the rows the sweep's re-rank warps did not
-    fp.rr_on = rerank_in_sweep(pb, prec, cap, nrb, grid) ? 1 : 0;
+    // the kernel takes the rows the sweep's re-rank warps did not (a row of the symmetric form
+    // is complete only when every row block above it has passed its columns)
+    fp.rr_on = !sym && rerank_in_sweep(pb, prec, cap, nrb, grid) ? 1 : 0;
     fp.rr = rp;
     rp.skip_done = fp.rr_on;
     if (fp.rr_on) KNN_CK(cudaMemsetAsync(L.row_status, 0, static_cast<size_t>(pb.M) * sizeof(uint32_t), st));
@@ -851,7 +902,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     ++tm.gemm_launches;
     KNN_TRY(ev.rec(2, st));
     KNN_CK(launch_rerank(rp, st));
-    tm.launches += rerank_launches(cap);
+    tm.launches += rerank_launches(cap + (sym ? cap_in : 0));
     KNN_TRY(ev.rec(3, st));
     int hstatus = 0;
     RerankCounters hc{};
@@ -876,7 +927,11 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     KNN_CK(cudaStreamSynchronize(st));
     // the fallback's re-rank adds to the counters after they were read: report the first pass
     fill_stats(stats, pb, hc, fallback, prec == P_BF16 ? KNN_BF16 : KNN_FP8_E4M3, 1, tm, ev.ev);
-    if (stats) stats->list_capacity = cap;
+    if (stats) {
+        stats->list_capacity = cap;
+        stats->symmetric = sym ? 1 : 0;
+        if (sym) stats->gemm_flops = 2.0 * symmetric_pairs(pb.M, pb.N) * pb.d;
+    }
     return KNN_OK;
 }
 

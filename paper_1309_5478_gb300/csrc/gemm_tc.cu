@@ -246,6 +246,7 @@ struct Item {
     const CUtensorMap* tmB;
     int64_t M, N;
     int rb, nk, nct;
+    int t0, nsw;      // first corpus tile of the sweep and tiles swept (symmetric form: t0 = rb / 2)
     int k, km, cap;
     int spec, perm_a;
     float spec_d2;
@@ -263,6 +264,16 @@ struct Item {
     uint32_t* flags;
 };
 
+// Row block of the CTA's work item `it` (non-batched launch). The symmetric form's row
+// blocks have sweeps of decreasing length, so every other full wave of items is dealt
+// in reverse CTA order, which pairs long sweeps with short ones on each CTA.
+__device__ __forceinline__ int item_rb(const FusedParams& p, int it) {
+    if (!p.sym) return it;
+    const int g = static_cast<int>(gridDim.x);
+    const int w = it / g, b = it - w * g;
+    return ((w & 1) && (w + 1) * g <= p.n_items) ? w * g + (g - 1 - b) : it;
+}
+
 template <bool BATCHED>
 __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                          int it) {
@@ -272,7 +283,7 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.tmB = tmB;
         im.M = p.M;
         im.N = p.N;
-        im.rb = it;
+        im.rb = item_rb(p, it);
         im.nk = p.k_bytes / TC_BK_BYTES;
         im.k = p.k;
         im.km = p.km;
@@ -321,12 +332,14 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.qnorm2 = nullptr;
     }
     im.nct = static_cast<int>((im.N + TC_BN - 1) / TC_BN);
+    im.t0 = (!BATCHED && p.sym) ? im.rb >> 1 : 0;
+    im.nsw = im.nct - im.t0;
     return im;
 }
 
 // Corpus tile swept at step ct of a row block's sweep.
 __device__ __forceinline__ int tile_at(const Item& im, int ct) {
-    return im.perm_a == 1 ? ct : static_cast<int>((static_cast<int64_t>(ct) * im.perm_a) % im.nct);
+    return im.perm_a == 1 ? im.t0 + ct : static_cast<int>((static_cast<int64_t>(ct) * im.perm_a) % im.nct);
 }
 
 // Warp-cooperative shrink of the candidate list of row r (of the block) during the
@@ -632,6 +645,19 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return d;
 }
 
+// The transposed direction of the symmetric graph form for one thread's row i: on a tile
+// past row i's own super-block, a column j with v_ij <= tau_j (i.e. squared distance
+// <= sym_t) also belongs in row j's inbox, as the key (d'_ji, i).
+struct SymCtx {
+    bool on;              // this tile feeds the transposed pairs (warp-uniform)
+    float tau_j;          // sym_t - |x_i|^2 (-inf for rows past M)
+    float qi;             // |x_i|^2
+    uint32_t row;         // i
+    uint64_t* inbox;
+    int32_t* inbox_cnt;
+    int32_t cap_in;
+};
+
 // Filters one 32-column chunk of the accumulator into the row's candidate list. The
 // ranking values v = |c_j|^2 - 2 acc (FP8: acc scaled back first) replace the accumulator
 // bits in r (packed pair arithmetic); a tree of three-input minimums gives the lane's
@@ -640,10 +666,14 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 // build their survivor masks and take one survivor per round, its value picked from r
 // by a select tree, appending it to the lane's segment of the row's list (slot
 // base + dir * cnt); the warp runs as many rounds as its lane with the most survivors.
+// In the symmetric form the same vote also admits the transposed pairs (sym), which are
+// appended to the column rows' inboxes with an atomic slot each; their key value
+// (v - |x_j|^2) + |x_i|^2 carries two more roundings than a row's own values, which the
+// error bound of symmetric problems includes.
 template <int P>
 __device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn, const float* cs, float qscale,
                                              int64_t j0, int64_t self, float tau_f, uint64_t* gbuf, int& cnt,
-                                             int base, int dir, uint32_t& inserted) {
+                                             int base, int dir, uint32_t& inserted, const SymCtx& sym) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const float4 c = reinterpret_cast<const float4*>(cn)[q];
@@ -673,6 +703,26 @@ __device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn,
     m[10] = fminf(__uint_as_float(r[30]), __uint_as_float(r[31]));
     const float mn = fminf(min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
                            fminf(m[9], m[10]));
+    const bool any_j = sym.on && __any_sync(0xffffffffu, mn <= sym.tau_j);
+    if (any_j) {
+        uint32_t mj = 0;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) mj |= (__uint_as_float(r[e]) <= sym.tau_j) ? (1u << e) : 0u;
+        const uint32_t rounds_j = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mj)));
+        inserted += static_cast<uint32_t>(__popc(mj));
+        for (uint32_t it = 0; it < rounds_j; ++it) {
+            const int t = (__ffs(mj) - 1) & 31;
+            const bool has = mj != 0u;
+            mj &= mj - 1u;
+            const float v = __uint_as_float(select32(r, t));
+            if (has) {
+                const int64_t j = j0 + t;
+                const float u = __fadd_rn(__fsub_rn(v, cn[t]), sym.qi);
+                const int slot = atomicAdd(sym.inbox_cnt + j, 1);
+                if (slot < sym.cap_in) sym.inbox[j * sym.cap_in + slot] = make_key(u, sym.row);
+            }
+        }
+    }
     if (!__any_sync(0xffffffffu, mn <= tau_f)) return;
     uint32_t m8[8];
 #pragma unroll
@@ -801,7 +851,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int kx = TC_BK_BYTES / (P == P_BF16 ? 2 : 1);
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
-                for (int ct = 0; ct < im.nct && ok; ++ct) {
+                for (int ct = 0; ct < im.nsw && ok; ++ct) {
                     for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, wait_limit)) {
                             ok = false;
@@ -852,7 +902,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int k_per_mma = 32;  // bytes of K per instruction: 16 BF16 or 32 FP8 values
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
                 const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
-                for (int ct = 0; ct < im.nct && ok; ++ct, ++tile) {
+                for (int ct = 0; ct < im.nsw && ok; ++ct, ++tile) {
                     const int acc = tile & 1;
                     const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
                     if (!mbar_wait(&acc_empty[acc], acc_ph ^ 1u, abort_flag, wait_limit)) {
@@ -927,7 +977,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
             const Item p = get_item<BATCHED>(params, &tmA, &tmB, it);
             const int rb = p.rb;
-            const int nct = p.nct;
+            const int nct = p.nsw;
             // room for one half-tile of insertions from both warps: 2 x 64 per row
             const int trigger = p.cap - 128;
             const int keep_mid = p.cap - 160 > p.km ? p.cap - 160 : p.km;
@@ -967,6 +1017,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int seg_dir = half ? -1 : 1;
             int my_cnt = 0;
             const float my_window = (valid && p.E) ? 2.f * p.E[grow] : 0.f;  // shuffled to the shrinking warp
+            SymCtx sym{};
+            const bool sym_item = !BATCHED && params.sym;
+            if (sym_item) {
+                sym.qi = valid ? p.qnorm2[grow] : 0.f;
+                sym.tau_j = valid ? params.sym_t - sym.qi : -F_INF;
+                sym.row = static_cast<uint32_t>(grow);
+                sym.inbox = params.inbox;
+                sym.inbox_cnt = params.inbox_cnt;
+                sym.cap_in = params.cap_in;
+            }
 
             for (int ct = 0; ct < nct; ++ct, ++tile) {
                 const int acc = tile & 1;
@@ -981,6 +1041,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const float* cn = cn_smem + acc * TC_BN + c0;
                 const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN + c0;
                 const int64_t jt = static_cast<int64_t>(tile_at(p, ct)) * TC_BN + c0;
+                sym.on = sym_item && ct > 0;  // past the row block's own super-block
                 uint32_t ra[32], rb2[32];
 #pragma unroll 1
                 for (int hs = 0; hs < 2; ++hs) {
@@ -989,10 +1050,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         tmem_ld32(taddr + hs * 64, ra);
                         tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
                         filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf,
-                                        my_cnt, seg_base, seg_dir, inserted);
+                                        my_cnt, seg_base, seg_dir, inserted, sym);
                         tmem_ld_wait();
                         filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self,
-                                        tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted);
+                                        tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted, sym);
                         if (hs == 1) {
                             // accumulator and staged norms of this tile no longer needed by this warp
                             tc_fence_before();
@@ -1064,8 +1125,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const float t = p.thr[grow];
                     if (t == t && t < F_INF) fl |= ROW_TRUNCATED | (c0 + c1 < p.k ? ROW_THRESHOLD_MISS : 0u);
                 }
+                uint64_t bnd = rs.tau[row_in_block];
+                if (sym_item) {
+                    // keys of the transposed pairs left out have value above sym_t - |x_i|^2 - delta
+                    // (delta: the filter's and the key's roundings, each below 2^-24 of a magnitude
+                    // of at most 3 max|x|^2 or sym_t)
+                    const float c2max = __uint_as_float(*params.c2max_bits);
+                    const float delta = 0x1p-20f * (c2max + fabsf(params.sym_t));
+                    const uint64_t bi = key_ceiling(__fsub_rd(__fsub_rd(params.sym_t, sym.qi), delta));
+                    bnd = bi < bnd ? bi : bnd;
+                }
                 p.count[grow] = c0 | (c1 << 16);
-                p.bound[grow] = rs.tau[row_in_block];
+                p.bound[grow] = bnd;
                 p.flags[grow] = fl;
             }
             // the next row block reinitialises the row state only after both warps are done
@@ -1107,9 +1178,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     go = false;
                     break;
                 }
-                const int64_t grow = static_cast<int64_t>(it) * TC_BM + r;
+                const int64_t grow = static_cast<int64_t>(item_rb(p, it)) * TC_BM + r;
                 if (grow >= p.M) break;
-                if (list_length(p.count[grow], p.flags[grow]) > RR_P) continue;
+                if (row_keys(p.rr, grow) > RR_P) continue;
                 rerank_row<true, 4>(p.rr, grow, RR_P, K, T64, cnt, lane);
             }
         }

@@ -53,9 +53,10 @@ cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precisi
                         float* tnorm, void* xq, int32_t ldq, float* inv_scale, PrepGlobals* g, cudaStream_t st);
 
 // E[i]: bound on |approximate - exact| of every d'_ij of row i (0 in exact arithmetic).
+// With sym_extra, E also covers the two extra roundings of the symmetric form's transposed keys.
 cudaError_t launch_bounds(const float* qnorm2, const float* qres, const float* qtnorm, int64_t M, int32_t d,
                           int32_t d_pad, int32_t precision, const PrepGlobals* gq, const PrepGlobals* gc, float* E,
-                          cudaStream_t st);
+                          cudaStream_t st, bool sym_extra = false);
 
 // ---- FP32 SIMT distance GEMM (gemm_simt.cu) ----
 // D[i*ldd + j] = cnorm2[j] - 2 q_i.c_j (+ qnorm2[i] when qnorm2 != nullptr); +inf where
@@ -128,11 +129,16 @@ struct RerankParams {
     int32_t count_min, count_max;  // rows whose list length lies outside are skipped (set by launch_rerank)
     int32_t skip_done;     // 1: rows whose row_status has ROW_RERANKED are skipped (re-ranked earlier)
     const int* status;     // optional device status word: when non-zero nothing is re-ranked
+    // symmetric graph form: keys of the transposed pairs of row i in inbox[i * cap_in ...],
+    // inbox_cnt[i] of them (more than cap_in: keys were lost and the row is not certified)
+    const uint64_t* inbox;
+    const int32_t* inbox_cnt;
+    int32_t cap_in;
 };
 // Lists longer than 512 (and 1024) keys are re-ranked by further launches with larger
 // per-warp buffers, so the common short lists keep the higher occupancy.
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st);
-inline int rerank_launches(int cap) { return cap > 1024 ? 3 : (cap > 512 ? 2 : 1); }
+inline int rerank_launches(int keys) { return keys > 1024 ? 3 : (keys > 512 ? 2 : 1); }
 
 // ---- band probe (probe.cu) ----
 // out_count[i] = #{ j != self_col[i] : D[i][j] <= max(vals[i][km-1], vals[i][k-1] + 2 E[i]) },

@@ -321,10 +321,14 @@ __global__ void __launch_bounds__(256) prep_batched_kernel(const BatchDev* __res
 //          (safety factor 4 over FP32's gamma for BF16, a 2^-14-unit accumulator for FP8).
 //   Exact arithmetic: integer-valued inputs with 4 d A^2 <= 2^24 (A the largest magnitude)
 //          make every product, partial sum and norm an exact FP32 integer, so E_i = 0.
+//   sym_extra (symmetric graph form): a transposed key is formed as (v - |x_j|^2) + |x_i|^2
+//          from the value v of the other row, two more roundings of quantities at most
+//          3 max|x|^2 in magnitude, covered by 2^-20 max|x|^2.
 __device__ __forceinline__ void bounds_row(const float* __restrict__ qnorm2, const float* __restrict__ qres,
                                            const float* __restrict__ qtnorm, int64_t i, int32_t d, int32_t d_pad,
                                            int32_t precision, const PrepGlobals* __restrict__ gq,
-                                           const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
+                                           const PrepGlobals* __restrict__ gc, float* __restrict__ E,
+                                           bool sym_extra = false) {
     const float amax = fmaxf(__uint_as_float(gq->max_abs), __uint_as_float(gc->max_abs));
     const bool integer = gq->noninteger == 0 && gc->noninteger == 0;
     const bool small = 4.0 * static_cast<double>(d_pad) * amax * amax <= 16777216.0;
@@ -350,16 +354,17 @@ __device__ __forceinline__ void bounds_row(const float* __restrict__ qnorm2, con
         const float norms = static_cast<float>(d + 4) * 0x1p-23f * (c2max + 2.f * qn * cmax);
         e = quant + accum + norms;
     }
+    if (sym_extra) e += 0x1p-20f * c2max;
     E[i] = e * (1.f + 0x1p-10f);
 }
 
 __global__ void bounds_kernel(const float* __restrict__ qnorm2, const float* __restrict__ qres,
                               const float* __restrict__ qtnorm, int64_t M, int32_t d, int32_t d_pad,
                               int32_t precision, const PrepGlobals* __restrict__ gq,
-                              const PrepGlobals* __restrict__ gc, float* __restrict__ E) {
+                              const PrepGlobals* __restrict__ gc, float* __restrict__ E, bool sym_extra) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    bounds_row(qnorm2, qres, qtnorm, i, d, d_pad, precision, gq, gc, E);
+    bounds_row(qnorm2, qres, qtnorm, i, d, d_pad, precision, gq, gc, E, sym_extra);
 }
 
 __global__ void bounds_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs,
@@ -502,10 +507,10 @@ cudaError_t launch_bounds_batched(const BatchDev* probs, const BatchSeg* segs, i
 
 cudaError_t launch_bounds(const float* qnorm2, const float* qres, const float* qtnorm, int64_t M, int32_t d,
                           int32_t d_pad, int32_t precision, const PrepGlobals* gq, const PrepGlobals* gc, float* E,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool sym_extra) {
     if (M <= 0) return cudaSuccess;
     const unsigned blocks = static_cast<unsigned>((M + 255) / 256);
-    bounds_kernel<<<blocks, 256, 0, st>>>(qnorm2, qres, qtnorm, M, d, d_pad, precision, gq, gc, E);
+    bounds_kernel<<<blocks, 256, 0, st>>>(qnorm2, qres, qtnorm, M, d, d_pad, precision, gq, gc, E, sym_extra);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,7 @@ __global__ void rerank_kernel(RerankParams p, int P) {
     // a fused kernel that stopped (bounded wait expired) leaves its lists unfinished
     const bool stopped = p.status != nullptr && *p.status != 0;
     if (row < p.M && !stopped && !(p.skip_done && (p.row_status[row] & ROW_RERANKED))) {
-        const int c = list_length(p.count[row], p.flags[row]);
+        const int c = row_keys(p, row);
         if (c >= p.count_min && c <= p.count_max) {
             uint64_t* K = reinterpret_cast<uint64_t*>(smem_raw) + static_cast<size_t>(warp) * (P + TIE_MAX);
             double* T64 = reinterpret_cast<double*>(K + P);
@@ -158,7 +158,8 @@ cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cma
 
 cudaError_t launch_rerank(const RerankParams& p, cudaStream_t st) {
     if (p.M <= 0) return cudaSuccess;
-    const int P = pow2_ceil(p.cap > 32 ? p.cap : 32);
+    const int keys = p.cap + (p.inbox ? p.cap_in : 0);  // longest list the re-rank may sort
+    const int P = pow2_ceil(keys > 32 ? keys : 32);
     int lo = INT32_MIN;
     for (int tier : {512, 1024}) {
         if (P <= tier) break;

@@ -142,6 +142,18 @@ __device__ __forceinline__ int list_length(int raw, uint32_t flags) {
     return (flags & ROW_RAW_LIST) ? (raw & 0xffff) + (raw >> 16) : raw;
 }
 
+// Keys of a row's inbox (symmetric graph form) that the re-rank reads: at most cap_in.
+__device__ __forceinline__ int inbox_length(const RerankParams& p, int64_t row) {
+    if (!p.inbox_cnt) return 0;
+    const int c = p.inbox_cnt[row];
+    return c < p.cap_in ? c : p.cap_in;
+}
+
+// Keys the re-rank of a row sorts: its list and its inbox.
+__device__ __forceinline__ int row_keys(const RerankParams& p, int64_t row) {
+    return list_length(p.count[row], p.flags[row]) + inbox_length(p, row);
+}
+
 // Exact keys for positions [lo, hi) of K (approximate keys in, exact keys out), NC
 // candidates at a time; err_max collects |approximate + qn2 - exact| / E (E > 0).
 template <bool VEC, int NC>
@@ -201,14 +213,21 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
     //    select does: sorted, then the keys <= min(bound, max(key_(k+m), ceiling(v_(k) +
     //    2E))) kept. A row whose bound came from a speculative threshold is truncated
     //    there when that band reaches beyond it.
+    //    In the symmetric graph form the row's inbox (keys of the transposed pairs, every one
+    //    at or below the row's bound is there unless the inbox overflowed) joins the list.
     int count;
     bool spec_cut = false;
     bool sorted = false;
+    bool lost = false;  // the inbox overflowed: keys below the bound may be missing
     if (flags & ROW_RAW_LIST) {
-        const int n0 = raw & 0xffff, n = n0 + (raw >> 16);
+        const int n0 = raw & 0xffff, nl = n0 + (raw >> 16);
+        const int nin = inbox_length(p, row);
+        lost = p.inbox_cnt != nullptr && p.inbox_cnt[row] > p.cap_in;
+        const uint64_t* inbox = p.inbox ? p.inbox + row * static_cast<int64_t>(p.cap_in) : nullptr;
+        const int n = nl + nin;
         const int Pn = pow2_ceil(n > 32 ? n : 32) < P ? pow2_ceil(n > 32 ? n : 32) : P;
         for (int i = static_cast<int>(lane); i < Pn; i += 32)
-            K[i] = i < n0 ? cand[i] : (i < n ? cand[p.cap - 1 - (i - n0)] : KEY_MAX);
+            K[i] = i < n0 ? cand[i] : (i < nl ? cand[p.cap - 1 - (i - n0)] : (i < n ? inbox[i - nl] : KEY_MAX));
         __syncwarp();
         warp_bitonic_sort_smem(K, Pn);
         const int kk = n < p.k ? n : p.k;
@@ -350,7 +369,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         }
     }
     const bool truncated = (flags & ROW_TRUNCATED) || spec_cut;
-    bool certified = kk == k && !(flags & ROW_SELECT_ERROR) && !giant_tie;
+    bool certified = kk == k && !(flags & ROW_SELECT_ERROR) && !giant_tie && !lost;
     if (certified && truncated && !exact) {
         // every left-out point has d' >= value(bound), so d2 >= value(bound) + |q|^2 - E
         double qn2d = 0.0;

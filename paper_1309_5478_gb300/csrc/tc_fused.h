@@ -71,6 +71,16 @@ struct FusedParams {
     int32_t rr_on;             // 1: two extra warps re-rank finished row blocks during the sweep
                                // (non-batched launch; shared memory sized with rr = true)
     RerankParams rr;           // the re-rank of the whole problem (rows indexed like the lists)
+    // Symmetric k-NN graph (non-batched launch, M == N, queries = corpus): row block rb sweeps
+    // only the corpus tiles t >= rb / 2 (its own 256-point super-block and later ones). On the
+    // tiles after its own super-block the product x_i . x_j also serves row j: keys (d'_ji, i)
+    // with squared distance <= sym_t go to row j's inbox. Half the distance product is computed.
+    int32_t sym;
+    float sym_t;               // squared-distance threshold of the transposed pairs (the probe's start threshold)
+    uint64_t* inbox;           // M x cap_in keys of the transposed pairs
+    int32_t* inbox_cnt;        // M, zeroed before the launch (may exceed cap_in: the row then lost keys)
+    int32_t cap_in;
+    const uint32_t* c2max_bits;  // float bits of max |x|^2 over the points (prep statistics)
 };
 
 // Largest candidate-list capacity of the fused form (48 keys per lane of a warp), and the

@@ -22,6 +22,7 @@ def test_bounded_wait_gives_up_with_a_status_and_the_device_stays_usable(monkeyp
     # 313 row blocks, so the re-rank warps wait for whole row-block sweeps: with one poll
     # allowed per wait the kernel gives up, and the call reports it
     X = inputs.integer_lattice(n=40000, d=128, seed=91)
+    monkeypatch.setenv("KNN_SYMMETRIC", "0")  # the full sweep, whose re-rank warps wait on the epilogue
     monkeypatch.setenv("KNN_WAIT_LIMIT", "1")
     with pytest.raises(kb.KnnError) as err:
         kb.knng_build(dev(X), 16, precision="bf16", fused=1)

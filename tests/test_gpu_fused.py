@@ -220,6 +220,10 @@ def test_large_k_float_search():
 
 @pytest.fixture
 def rerank_in_sweep(monkeypatch):
+    # the in-sweep re-rank serves the full sweep (a graph this size would otherwise take the
+    # symmetric form, whose rows are complete only after the whole launch)
+    monkeypatch.setenv("KNN_SYMMETRIC", "0")
+
     def set_rr(on):
         monkeypatch.setenv("KNN_RERANK_IN_SWEEP", "1" if on else "0")
     return set_rr
