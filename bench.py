@@ -67,6 +67,8 @@ def parse():
                          "mlp: k-NN graph of a 524288 x 768 anisotropic mixture, k=100, with learned per-row "
                          "thresholds against the same graph without them")
     ap.add_argument("--workload", choices=sorted(PLAIN_WORKLOADS), default="lattice", help="plain mode: workload")
+    ap.add_argument("--max-workspace-mb", type=int, default=0,
+                    help="plain mode: workspace cap in MiB (sizes the distance-matrix slabs; 0 = library default)")
     ap.add_argument("--train-rows", type=int, default=50000, help="mlp mode: training rows")
     ap.add_argument("--epochs", type=int, default=40, help="mlp mode: training epochs")
     ap.add_argument("--problems", type=int, default=512, help="batch mode: number of problems")
@@ -75,9 +77,28 @@ def parse():
     return ap.parse_args()
 
 
+SCHEDULE_NAMES = {0: "fused", 1: "plain-fp32", 2: "fused-no-speculation", 3: "fused-speculation"}
+
+
+def autotune_table(path: str) -> dict:
+    """The autotuner's cache file as {"device": tag, "buckets": {bucket: schedule name}}."""
+    try:
+        raw = json.load(open(path))
+    except (OSError, ValueError):
+        return {"unavailable": f"no cache at {path}"}
+    dev = raw.pop("_device", None)
+    return {"device": dev, "buckets": {k: SCHEDULE_NAMES.get(v, v) for k, v in sorted(raw.items())},
+            "counts": {name: sum(1 for v in raw.values() if SCHEDULE_NAMES.get(v) == name)
+                       for name in SCHEDULE_NAMES.values()}}
+
+
 def run_batch(args):
     """512 independent k-NN search problems (M~U[256,16384], N~U[1024,65536], d in {64,128,256,768},
     k in {1,8,32,128,512}, N(0,1) FP32 data) answered by one knn_search_batched call (one CUDA graph)."""
+    import tempfile
+    # a fresh autotuner cache for this run, read back afterwards for the choice table
+    tune_dir = tempfile.mkdtemp(prefix="knn_tune_")
+    os.environ["KNN_AUTOTUNE_CACHE"] = os.path.join(tune_dir, "autotune.json")
     import torch
     from paper_1309_5478_gb300 import binding as kb
     from paper_1309_5478_gb300 import inputs
@@ -129,7 +150,8 @@ def run_batch(args):
                                                    "fused_used", "kernel_launches")},
             "phases_ms": {"call_host_total": stats["ms_total"], "graph": stats["ms_gemm"],
                           "prep_bounds": stats["ms_prep"], "fused": stats["ms_select"],
-                          "rerank": stats["ms_rerank"], "plain_problems": stats["ms_fallback"]}}
+                          "rerank": stats["ms_rerank"], "plain_problems": stats["ms_fallback"]},
+            "autotuner": autotune_table(os.environ["KNN_AUTOTUNE_CACHE"])}
     # oracle on a few rows of a few problems
     import oracle
     sample = []
@@ -357,7 +379,8 @@ def run_plain(args):
 
     def call():
         return kb.knng_build(Xd, k, out_idx=oi, out_dist=od, precision="fp32", fused=0,
-                             flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True)[2]
+                             flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True,
+                             max_workspace_bytes=args.max_workspace_mb << 20)[2]
 
     for _ in range(args.warmup):
         call()
@@ -395,6 +418,7 @@ def run_plain(args):
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "N": n, "d": d, "k": k, "form": "plain-fp32",
+                       "max_workspace_mb": args.max_workspace_mb,
                        "l2": "256 MB written between steps (outside the timed region)"},
             "roofline": {"bound": "hbm", "achieved": sel_gbs, "peak": P["hbm_gbs"], "unit": "GB/s",
                          "frac": sel_gbs / P["hbm_gbs"], "kernel": "select_rows_kernel",
@@ -902,19 +926,25 @@ def main():
     roof["traffic"] = tr * 1.0 if tr is not None else None
     roof["launch_ms"] = ms_gemm / launches_gemm
     roof["share_of_step"] = ms_gemm / ms_step
-    # whole-path roofline of the method: the slower of GEMM flops at tensor peak and compulsory bytes at HBM
+    # whole-path roofline of the method: the slower of the distance product the form computes at
+    # tensor peak (the symmetric graph form computes each pair's product once: about N^2 d, not
+    # 2 N^2 d) and the compulsory bytes at HBM bandwidth
     compulsory = args.n * args.d * 4 + args.n * k * 8 + (args.n * args.d * 2 * 2 if form == "fused" else 0)
     if form == "plain":
         compulsory += 8 * args.n * args.n
-    t_roof = max(2.0 * args.n * args.n * args.d / (P["bf16_sustained"] * 1e12), compulsory / (P["hbm_gbs"] * 1e9))
+    t_roof = max(flops / (P["bf16_sustained"] * 1e12), compulsory / (P["hbm_gbs"] * 1e9))
     path_frac = t_roof / (ms_step / 1000.0)
 
     line = {"metric": METRIC, "value": rows_per_s, "unit": "rows/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if form == "fused" else "f32", "data": "synthetic",
-            "config": workload_config(args, "fused-bf16" if form == "fused" else "plain-fp32"),
+            "config": workload_config(args, ("fused-bf16-symmetric" if s0.get("symmetric", 0) else "fused-bf16")
+                                      if form == "fused" else "plain-fp32"),
             "pairs_per_s": world * args.n * (args.n - 1) / (ms_step / 1000.0),
             "path_roofline_frac": path_frac,
+            "path_roofline": {"t_roof_ms": t_roof * 1000.0, "gemm_flops": flops,
+                              "symmetric": bool(s0.get("symmetric", 0)),
+                              "full_product_flops": 2.0 * args.n * args.n * args.d},
             "roofline": roof, "clocks": clk,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "exactness": {"rows_uncertified": int(s0["rows_uncertified"]), "rows_fallback": int(s0["rows_fallback"]),

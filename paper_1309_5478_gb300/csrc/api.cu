@@ -677,6 +677,7 @@ int fused_retry(const Problem& pb, int prec, const CommonLayout& L, const FusedP
 constexpr int64_t SPEC_MIN_N = 16384;
 
 bool speculate(const Problem& pb) {
+    if (pb.spec >= 0) return pb.spec != 0 && pb.N >= 2 * 256;
     if (const char* e = std::getenv("KNN_SPECULATE")) return std::atoi(e) != 0 && pb.N >= 2 * 256;
     return pb.N >= SPEC_MIN_N;
 }

@@ -13,6 +13,7 @@
 // most of them idle.
 #include <cuda_runtime.h>
 #include <sys/stat.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <chrono>
@@ -32,17 +33,49 @@
 
 namespace knn {
 
-enum Schedule : int { SCHED_FUSED = 0, SCHED_PLAIN = 1 };
+// Schedules a problem of a batch can take: the fused tensor-core form with speculative
+// thresholds in its sweep or without them (a choice of the select's work inside the GEMM
+// epilogue), or the plain FP32 form (SIMT GEMM slabs, unfused multi-select).
+// SCHED_FUSED leaves speculation to the size rule (from 16384 points on).
+enum Schedule : int { SCHED_FUSED = 0, SCHED_PLAIN = 1, SCHED_FUSED_NOSPEC = 2, SCHED_FUSED_SPEC = 3 };
+constexpr int TUNE_VERSION = 2;  // bumped when the schedule table or its timing changes
+
+bool is_fused(int sched) { return sched != SCHED_PLAIN; }
+
+const char* schedule_name(int sched) {
+    switch (sched) {
+        case SCHED_PLAIN: return "plain-fp32";
+        case SCHED_FUSED_NOSPEC: return "fused-no-speculation";
+        case SCHED_FUSED_SPEC: return "fused-speculation";
+        default: return "fused";
+    }
+}
 
 namespace {
 
 // --------------------------------------------------------------------------------------
 // autotuner: schedule per shape bucket, measured once on a synthetic problem of the
 // bucket, cached in a JSON file (KNN_AUTOTUNE_CACHE, default ~/.cache/knn_gb300_autotune.json)
+// whose "_device" entry names the GPU, its SM count and the schedule table's version;
+// entries written for another device or version are ignored.
 // --------------------------------------------------------------------------------------
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune;
 bool g_tune_loaded = false;
+
+std::string tune_device_tag() {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    char b[320];
+    std::snprintf(b, sizeof(b), "%s sm%d v%d", prop.name, prop.multiProcessorCount, TUNE_VERSION);
+    for (char* c = b; *c; ++c)
+        if (*c == '"' || *c == '\\') *c = '_';
+    return b;
+}
 
 std::string tune_path() {
     const char* e = std::getenv("KNN_AUTOTUNE_CACHE");
@@ -56,18 +89,29 @@ void tune_load() {
     g_tune_loaded = true;
     FILE* f = std::fopen(tune_path().c_str(), "r");
     if (!f) return;
-    char key[256];
-    int v;
-    // the file is a flat JSON object {"bucket": schedule, ...}
+    char key[320];
+    // the file is a flat JSON object {"_device": "tag", "bucket": schedule, ...}
+    std::map<std::string, int> entries;
+    std::string device;
     int c;
     while ((c = std::fgetc(f)) != EOF) {
         if (c != '"') continue;
         int n = 0;
-        while ((c = std::fgetc(f)) != EOF && c != '"' && n < 255) key[n++] = static_cast<char>(c);
+        while ((c = std::fgetc(f)) != EOF && c != '"' && n < 319) key[n++] = static_cast<char>(c);
         key[n] = 0;
-        if (std::fscanf(f, " : %d", &v) == 1) g_tune[key] = v;
+        if (std::strcmp(key, "_device") == 0) {
+            while ((c = std::fgetc(f)) != EOF && c != '"') {
+            }
+            std::string tag;
+            while ((c = std::fgetc(f)) != EOF && c != '"') tag += static_cast<char>(c);
+            device = tag;
+            continue;
+        }
+        int v;
+        if (std::fscanf(f, " : %d", &v) == 1 && v >= SCHED_FUSED && v <= SCHED_FUSED_SPEC) entries[key] = v;
     }
     std::fclose(f);
+    if (device == tune_device_tag()) g_tune = entries;
 }
 
 void tune_save() {
@@ -82,15 +126,18 @@ void tune_save() {
                 (void)::mkdir(part.c_str(), 0755);
             }
     }
-    FILE* f = std::fopen((path + ".tmp").c_str(), "w");
+    // a temporary file of this process, renamed over the cache (concurrent writers each
+    // replace the whole file; the last one wins)
+    const std::string tmp = path + "." + std::to_string(static_cast<long long>(::getpid())) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
     if (!f) return;
-    std::fprintf(f, "{\n");
+    std::fprintf(f, "{\n  \"_device\": \"%s\"%s\n", tune_device_tag().c_str(), g_tune.empty() ? "" : ",");
     size_t i = 0;
     for (const auto& kv : g_tune)
         std::fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < g_tune.size() ? "," : "");
     std::fprintf(f, "}\n");
     std::fclose(f);
-    std::rename((path + ".tmp").c_str(), path.c_str());
+    std::rename(tmp.c_str(), path.c_str());
 }
 
 int ilog2(int64_t x) {
@@ -147,8 +194,9 @@ int time_schedule(const Problem& p, int sched, float* ms_per_row) {
         q.out_idx = oi;
         q.out_dist = od;
         q.flags = KNN_FLAG_NO_FALLBACK;
-        q.precision = sched == SCHED_FUSED ? KNN_BF16 : KNN_FP32;
-        q.fused = sched == SCHED_FUSED ? 1 : 0;
+        q.precision = is_fused(sched) ? KNN_BF16 : KNN_FP32;
+        q.fused = is_fused(sched) ? 1 : 0;
+        q.spec = sched == SCHED_FUSED_SPEC ? 1 : (sched == SCHED_FUSED_NOSPEC ? 0 : -1);
         ::knn_stats s{};
         float best = 1e30f;
         for (int rep = 0; rep < 3 && rc == KNN_OK; ++rep) {
@@ -168,7 +216,7 @@ int time_schedule(const Problem& p, int sched, float* ms_per_row) {
         // In a batch the fused kernel's row blocks share every SM with other problems'
         // work items; alone, a problem of nrb row blocks occupies only nrb SMs. Charge the
         // fused form for the share of the GPU it actually used.
-        if (sched == SCHED_FUSED) {
+        if (is_fused(sched)) {
             int dev = 0, sms = 1;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -201,10 +249,18 @@ int choose_schedule(const Problem& p, int precision_req, bool* fused_capable) {
     const std::string key = bucket_of(p);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) return it->second;
-    float tf = 0.f, tp = 0.f;
+    // the fastest schedule per row of the bucket's synthetic problem (speculation needs a
+    // sweep of a few tiles: below 512 points only the plain sweep is timed)
     int sched = SCHED_FUSED;
-    if (time_schedule(p, SCHED_FUSED, &tf) == KNN_OK && time_schedule(p, SCHED_PLAIN, &tp) == KNN_OK)
-        sched = tf <= tp ? SCHED_FUSED : SCHED_PLAIN;
+    float best = 1e30f;
+    for (int s : {SCHED_FUSED_SPEC, SCHED_FUSED_NOSPEC, SCHED_PLAIN}) {
+        if (s == SCHED_FUSED_SPEC && p.N < 512) continue;
+        float t = 0.f;
+        if (time_schedule(p, s, &t) == KNN_OK && t < best) {
+            best = t;
+            sched = s;
+        }
+    }
     g_last_error.clear();
     g_tune[key] = sched;
     tune_save();
@@ -294,7 +350,7 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
     L.dev.assign(n, BatchDev{});
     L.fused_ids.clear();
     L.plain_ids.clear();
-    for (int i = 0; i < n; ++i) (sched[i] == SCHED_FUSED ? L.fused_ids : L.plain_ids).push_back(i);
+    for (int i = 0; i < n; ++i) (is_fused(sched[i]) ? L.fused_ids : L.plain_ids).push_back(i);
     L.cap_max = 0;
     int64_t plain_slab_bytes = 0;
     L.slab_rows = 0;
@@ -303,7 +359,7 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
     for (int i = 0; i < n; ++i) {
         const Problem& p = probs[i];
         BatchDev& b = L.dev[i];
-        const bool fused = sched[i] == SCHED_FUSED;
+        const bool fused = is_fused(sched[i]);
         const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
         b.Q = p.Q;
         b.C = p.C;
@@ -578,7 +634,9 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         q.count = b.count;
         q.bound = b.bound;
         q.flags = b.flags;
-        q.spec = b.N >= 16384 ? 1 : 0;
+        // speculation as the autotuner chose it, else from 16384 points on
+        const int sc = sched[L.fused_ids[f]];
+        q.spec = sc == SCHED_FUSED_NOSPEC ? 0 : (sc == SCHED_FUSED_SPEC || b.N >= 16384 ? 1 : 0);
         if (!encode_problem_maps(&q, b.xq, b.xc, prec))
             return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
     }

@@ -105,15 +105,53 @@ def test_bad_problem_reports_its_status():
         kb.knn_search_batched([probs[0], bad])
 
 
-def test_autotuner_writes_its_cache(monkeypatch, tmp_path):
-    monkeypatch.setenv("KNN_AUTOTUNE", "1")
-    path = tmp_path / "tune2.json"
-    monkeypatch.setenv("KNN_AUTOTUNE_CACHE", str(path))
-    probs, refs = make_problems([(500, 4000, 128, 16, False)], seed0=800)
-    # a fresh cache path in a fresh process; an already loaded cache is reused in-process
-    st = kb.knn_search_batched(probs)
-    assert st == [0]
-    check_all(probs, refs)
+TUNE_SCRIPT = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+from paper_1309_5478_gb300 import binding as kb
+from paper_1309_5478_gb300 import inputs
+C = torch.from_numpy(inputs.integer_lattice(n=4000, d=128, lo=-6, hi=6, seed=801)).cuda()
+Q = torch.from_numpy(inputs.integer_lattice(n=500, d=128, lo=-6, hi=6, seed=802)).cuda()
+probs = [{"Q": Q, "C": C, "k": 16, "out_idx": torch.empty((500, 16), dtype=torch.int32, device="cuda"),
+          "out_dist": torch.empty((500, 16), dtype=torch.float32, device="cuda")}]
+st, stats = kb.knn_search_batched(probs, return_stats=True)
+print(json.dumps({"status": st, "fused_used": stats["fused_used"]}))
+"""
+
+
+def run_tuned_batch(cache):
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, KNN_AUTOTUNE="1", KNN_AUTOTUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, "-c", TUNE_SCRIPT, root], env=env, capture_output=True, text=True,
+                       timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_autotuner_cache_is_written_keyed_and_reused(tmp_path):
+    # each run is a fresh process: the cache file, not memory, carries the choices
+    import json
+    cache = tmp_path / "tune.json"
+    first = run_tuned_batch(cache)
+    assert first["status"] == [0]
+    data = json.loads(cache.read_text())
+    tag = data.pop("_device")
+    assert " sm" in tag and tag.endswith(" v2"), tag
+    assert data and all(v in (1, 2, 3) for v in data.values()), data  # measured: plain or a fused variant
+    # a second process follows the file: every bucket forced to the plain form
+    cache.write_text(json.dumps({"_device": tag, **{b: 1 for b in data}}))
+    second = run_tuned_batch(cache)
+    assert second["status"] == [0] and second["fused_used"] == 0
+    # entries of another device are ignored: the bucket is measured again and the file rewritten
+    cache.write_text(json.dumps({"_device": "another GPU sm1 v2", **{b: 1 for b in data}}))
+    third = run_tuned_batch(cache)
+    assert third["status"] == [0]
+    again = json.loads(cache.read_text())
+    assert again.pop("_device") == tag and set(again) == set(data)
 
 
 def test_uncertified_rows_of_a_batch_are_recomputed():
