@@ -46,6 +46,7 @@ struct RerankCounters {
     unsigned long long inserted;  // keys the fused sweep appended to candidate lists
     unsigned long long max_err_ratio;  // float bits of the largest |approximate - exact| / E of a candidate
     unsigned long long rows_in_sweep;  // rows re-ranked by the fused kernel during its sweep
+    unsigned long long next_row[4];    // work counters of the re-rank launches (one per list-length tier)
 };
 
 // ---- prep / bounds (prep.cu) ----
