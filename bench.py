@@ -53,9 +53,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--mode", choices=["knng", "plain", "select", "select_sweep", "batch", "mlp", "metric", "streamed"],
+    ap.add_argument("--mode", choices=["knng", "plain", "fp8", "select", "select_sweep", "batch", "mlp", "metric",
+                                       "streamed"],
                     default="knng",
-                    help="plain: the plain FP32 form on the integer lattice (--workload lattice: N=4096, d=128, k=16) "
+                    help="fp8: FP8 e4m3 against BF16 on 262144 near-duplicate points (2048 groups of 128) in d=1024; "
+                         "plain: the plain FP32 form on the integer lattice (--workload lattice: N=4096, d=128, k=16) "
                          "or the Gaussian mixture (--workload mixture: N=65536, d=256, k=32); "
                          "select: the quick multi-select alone on a Q x n uniform random matrix (paper's experiments); "
                          "metric: the cosine and Pearson similarity graphs of the headline data; "
@@ -432,6 +434,58 @@ def run_plain(args):
             "oracle_check": check,
             "cpu_baseline": {"value": len(rows) / t_cpu, "unit": "rows/s", "cores": oracle.threads(), "kind": "oracle",
                              "sample": f"{len(rows)} rows of the same graph, {t_cpu:.1f} s"}}
+    print(json.dumps(line), flush=True)
+
+
+def run_fp8(args):
+    """FP8 e4m3 against BF16 on a workload whose FP8 error bound still separates the answer:
+    the k-NN graph (k = 64) of 262144 points in d = 1024 made of 2048 groups of 128
+    near-duplicates (unit-norm centres, members within about 1e-2 of their centre). The band
+    of either form is the point's own group, so both certify their rows in the first pass, and
+    FP8 halves the tensor work. Each form: one untimed call, then the median of the timed
+    steps (CUDA events); inputs (1.07 GB) exceed L2."""
+    import torch
+    import oracle
+    from paper_1309_5478_gb300 import binding as kb
+    from paper_1309_5478_gb300 import inputs
+    n, d, k = 262144, 1024, 64
+    X = inputs.tight_groups(n=n, d=d, group=128)
+    Xd = torch.from_numpy(X).cuda()
+    oi = torch.empty((n, k), dtype=torch.int32, device="cuda")
+    od = torch.empty((n, k), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    P = peaks()
+    forms = {}
+    outs = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for prec in ("bf16", "fp8"):
+        def call():
+            return kb.knng_build(Xd, k, out_idx=oi, out_dist=od, precision=prec, rerank_extra=M_EXTRA, fused=1,
+                                 flags=kb.KNN_FLAG_CHECK_FINITE | kb.KNN_FLAG_TIMING, return_stats=True)[2]
+        ms, st = timed_calls(call, stream, args.steps)
+        outs[prec] = (oi.cpu().numpy(), od.cpu().numpy())
+        forms[prec] = {"ms_per_step": ms, "rows_per_s": n / (ms / 1000.0), "ms_gemm": st["ms_gemm"],
+                       "gemm_tflops": st["gemm_flops"] / (st["ms_gemm"] / 1000.0) / 1e12,
+                       "rows_certified_first_pass": int(n - st["rows_uncertified"]),
+                       "rows_fallback": int(st["rows_fallback"]), "symmetric": bool(st["symmetric"]),
+                       "candidates_per_row": st["candidates"] / n, "max_error_ratio": float(st["max_error_ratio"]),
+                       "phases_ms": {"prep": st["ms_prep"], "gemm_select": st["ms_select"],
+                                     "rerank": st["ms_rerank"], "fallback": st["ms_fallback"]}}
+    clk = clocks.stop()
+    rows = inputs.sample_rows(n, 64, seed=79)
+    ri, rd = oracle.knng(X, k, rows=rows)
+    for prec in forms:
+        forms[prec]["oracle_check"] = oracle_check(X, rows, outs[prec][0][rows], outs[prec][1][rows], ri, rd)
+    line = {"metric": "exact k-NNG rows/s, FP8 e4m3 against BF16 (near-duplicate groups)",
+            "value": forms["fp8"]["rows_per_s"], "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": forms["fp8"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8-e4m3", "data": "synthetic",
+            "config": {"workload": f"k-NN graph, N={n} points in d={d}: 2048 groups of 128 near-duplicates "
+                                   "(unit-norm centres, members c + 0.01 z / sqrt(d)), k=64, squared Euclidean",
+                       "N": n, "d": d, "k": k, "seed": 20130909, "l2": "input 1.07 GB > L2"},
+            "forms": forms, "fp8_vs_bf16": forms["bf16"]["ms_per_step"] / forms["fp8"]["ms_per_step"],
+            "clocks": clk, "peak_bf16_sustained": P["bf16_sustained"]}
     print(json.dumps(line), flush=True)
 
 
@@ -836,10 +890,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.mode in ("plain", "select", "select_sweep", "batch", "mlp", "metric", "streamed"):
+    if args.mode in ("plain", "fp8", "select", "select_sweep", "batch", "mlp", "metric", "streamed"):
         import torch
         torch.cuda.set_device(local)
-        {"plain": run_plain, "select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
+        {"plain": run_plain, "fp8": run_fp8, "select": run_select_only, "select_sweep": run_select_sweep, "batch": run_batch,
          "mlp": run_mlp, "metric": run_metric, "streamed": run_streamed}[args.mode](args)
         return
 
@@ -914,7 +968,9 @@ def main():
         kern = "knn_fused_gemm_select"
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": f"{P['source']} bf16 sustained", "kernel": kern}
-        src = ["paper_1309_5478_gb300/csrc/gemm_tc.cu"]
+        src = ["paper_1309_5478_gb300/csrc/gemm_tc.cu", "paper_1309_5478_gb300/csrc/rerank_core.cuh",
+               "paper_1309_5478_gb300/csrc/select_core.cuh", "paper_1309_5478_gb300/csrc/tc_fused.h",
+               "paper_1309_5478_gb300/csrc/common.cuh"]
     else:
         peak = SM_COUNT * FP32_LANES_PER_SM * 2 * P["sm_max_mhz"] * 1e6 / 1e12
         achieved = flops / (ms_gemm / 1000.0) / 1e12

@@ -324,6 +324,9 @@ struct BatchLayout {
     std::vector<FusedWork> work;
     int64_t prep_rows = 0, query_rows = 0, plain_prep_rows = 0, plain_query_rows = 0;
     int cap_max = 0, stages = 0, grid = 0;
+    // the fused work runs as two launches: problems whose lists hold at most 512 keys (the
+    // kernel variant with 16 keys a lane and four pipeline stages), then the longer lists
+    int n_short = 0, cap_short = 0, cap_long = 0;
     // device pointers
     BatchDev* d_dev = nullptr;
     FusedProblem* d_fprob = nullptr;
@@ -442,18 +445,27 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
         L.plain_query_rows += probs[i].M;
     }
     L.fprob.assign(L.fused_ids.size(), FusedProblem{});
-    for (size_t f = 0; f < L.fused_ids.size(); ++f) {
-        const int i = L.fused_ids[f];
-        const Problem& p = probs[i];
-        const int nrb = static_cast<int>((p.M + 127) / 128);
-        for (int rb = 0; rb < nrb; ++rb) L.work.push_back({static_cast<int32_t>(f), rb});
+    L.cap_short = L.cap_long = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const size_t first = L.work.size();
+        for (size_t f = 0; f < L.fused_ids.size(); ++f) {
+            const int i = L.fused_ids[f];
+            const Problem& p = probs[i];
+            const int cap = L.dev[i].cap;
+            if ((cap <= 512) != (pass == 0)) continue;
+            (pass == 0 ? L.cap_short : L.cap_long) = std::max(pass == 0 ? L.cap_short : L.cap_long, cap);
+            const int nrb = static_cast<int>((p.M + 127) / 128);
+            for (int rb = 0; rb < nrb; ++rb) L.work.push_back({static_cast<int32_t>(f), rb});
+        }
+        // largest items first: cost of a row block ~ corpus tiles x k-steps
+        std::stable_sort(L.work.begin() + static_cast<std::ptrdiff_t>(first), L.work.end(),
+                         [&](const FusedWork& a, const FusedWork& b) {
+                             const Problem& pa = probs[L.fused_ids[a.problem]];
+                             const Problem& pb = probs[L.fused_ids[b.problem]];
+                             return (pa.N + 255) / 256 * ((pa.d + 63) / 64) > (pb.N + 255) / 256 * ((pb.d + 63) / 64);
+                         });
+        if (pass == 0) L.n_short = static_cast<int>(L.work.size());
     }
-    // largest items first: cost of a row block ~ corpus tiles x k-steps
-    std::stable_sort(L.work.begin(), L.work.end(), [&](const FusedWork& a, const FusedWork& b) {
-        const Problem& pa = probs[L.fused_ids[a.problem]];
-        const Problem& pb = probs[L.fused_ids[b.problem]];
-        return (pa.N + 255) / 256 * ((pa.d + 63) / 64) > (pb.N + 255) / 256 * ((pb.d + 63) / 64);
-    });
     L.grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(sms), L.work.size())));
     L.stages = L.fused_ids.empty() ? 0 : fused_stages(L.cap_max, prec);
     L.d_dev = ar.take<BatchDev>(static_cast<size_t>(n));
@@ -490,15 +502,21 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
         KNN_CK(launch_bounds_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
                                      prec, st));
         KNN_CK(mark(1));
-        FusedParams fp{};
-        fp.status = L.status;
-        fp.scratch = L.scratch;
-        fp.stages = L.stages;
-        fp.cap_max = L.cap_max;
-        fp.n_items = static_cast<int32_t>(L.work.size());
-        fp.problems = L.d_fprob;
-        fp.work = L.d_work;
-        KNN_CK(launch_fused_batched(fp, prec, L.grid, st));
+        int sms = L.grid;
+        for (int part = 0; part < 2; ++part) {
+            const int first = part == 0 ? 0 : L.n_short;
+            const int count = part == 0 ? L.n_short : static_cast<int>(L.work.size()) - L.n_short;
+            if (count <= 0) continue;
+            FusedParams fp{};
+            fp.status = L.status;
+            fp.scratch = L.scratch;
+            fp.cap_max = part == 0 ? L.cap_short : L.cap_long;
+            fp.stages = fused_stages(fp.cap_max, prec);
+            fp.n_items = count;
+            fp.problems = L.d_fprob;
+            fp.work = L.d_work + first;
+            KNN_CK(launch_fused_batched(fp, prec, std::min(sms, count), st));
+        }
         KNN_CK(mark(2));
         KNN_CK(launch_rerank_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
                                      L.cap_max, L.counters, st));
@@ -772,7 +790,9 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         for (const Problem& p : probs) flops += 2.0 * double(p.M) * double(p.N) * double(p.d);
         stats->gemm_flops = flops;
         stats->kernel_launches =
-            1 + (L.fused_ids.empty() ? 0 : 3 + rerank_launches(L.cap_max)) + (L.plain_ids.empty() ? 0 : 2);
+            1 + (L.fused_ids.empty() ? 0 : 2 + (L.n_short > 0) + (static_cast<int>(L.work.size()) > L.n_short) +
+                                                rerank_launches(L.cap_max)) +
+            (L.plain_ids.empty() ? 0 : 2);
         for (int i : L.plain_ids) {
             const Problem& p = probs[i];
             const int64_t ldn = (p.N + 31) / 32 * 32;

@@ -62,9 +62,12 @@ __device__ __forceinline__ int find_seg(const BatchSeg* segs, int32_t nseg, int6
     return lo;
 }
 
-__global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs,
-                                      int32_t nseg, int64_t rows, int P, int32_t count_min, int32_t count_max,
-                                      RerankCounters* counters) {
+// Every query row of a batch, one warp per row, persistent: warps take the next row (in
+// problem order, so a problem's corpus stays in L2 while its rows are re-ranked) from a counter.
+__global__ void __launch_bounds__(256, 3)
+    rerank_batched_kernel(const BatchDev* __restrict__ probs, const BatchSeg* __restrict__ segs, int32_t nseg,
+                          int64_t rows, int P, int32_t count_min, int32_t count_max, RerankCounters* counters,
+                          unsigned long long* next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long cnt[8][RC_COUNT];
     const int warp = static_cast<int>(threadIdx.x / 32);
@@ -72,8 +75,12 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
     const uint32_t lane = lane_id();
     if (lane < RC_COUNT) cnt[warp][lane] = 0ull;
     __syncwarp();
-    const int64_t row = static_cast<int64_t>(blockIdx.x) * warps + warp;
-    if (row < rows) {
+    for (;;) {
+    unsigned long long rr = 0;
+    if (lane == 0) rr = atomicAdd(next, 1ull);
+    const int64_t row = static_cast<int64_t>(__shfl_sync(0xffffffffu, rr, 0));
+    if (row >= rows) break;
+    {
         const BatchSeg sg = segs[find_seg(segs, nseg, row)];
         const BatchDev& b = probs[sg.problem];
         RerankParams rp{};
@@ -105,6 +112,7 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
                 rerank_row<false, 4>(rp, r, Pp, K, T64, cnt[warp], lane);
         }
     }
+    }
     block_flush(counters, cnt, warps);
 }
 
@@ -113,7 +121,7 @@ __global__ void rerank_batched_kernel(const BatchDev* __restrict__ probs, const 
 
 namespace {
 cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
-                                        int P, int32_t cmin, int32_t cmax, RerankCounters* counters,
+                                        int P, int32_t cmin, int32_t cmax, int tier, RerankCounters* counters,
                                         cudaStream_t st) {
     const size_t per_warp = static_cast<size_t>(P + TIE_MAX) * 8;
     int warps = static_cast<int>((64u * 1024u) / per_warp);
@@ -123,9 +131,18 @@ cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* s
     cudaError_t e = cudaFuncSetAttribute(rerank_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    const int64_t blocks = (rows + warps - 1) / warps;
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rerank_batched_kernel, warps * 32,
+                                                                           smem);
+    if (e != cudaSuccess) return e;
+    unsigned long long* next = &counters->next_row[tier];
+    e = cudaMemsetAsync(next, 0, sizeof(*next), st);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>((rows + warps - 1) / warps, static_cast<int64_t>(std::max(1, per_sm)) * sms);
     rerank_batched_kernel<<<static_cast<unsigned>(blocks), warps * 32, smem, st>>>(probs, segs, nseg, rows, P, cmin,
-                                                                                   cmax, counters);
+                                                                                   cmax, counters, next);
     return cudaGetLastError();
 }
 }  // namespace
@@ -138,13 +155,14 @@ cudaError_t launch_rerank_batched(const BatchDev* probs, const BatchSeg* segs, i
     if (rows <= 0) return cudaSuccess;
     const int P = pow2_ceil(cap_max > 32 ? cap_max : 32);
     int lo = INT32_MIN;
+    int t = 0;
     for (int tier : {512, 1024}) {
         if (P <= tier) break;
-        cudaError_t e = launch_rerank_batched_range(probs, segs, nseg, rows, tier, lo, tier, counters, st);
+        cudaError_t e = launch_rerank_batched_range(probs, segs, nseg, rows, tier, lo, tier, t++, counters, st);
         if (e != cudaSuccess) return e;
         lo = tier + 1;
     }
-    return launch_rerank_batched_range(probs, segs, nseg, rows, P, lo, INT32_MAX, counters, st);
+    return launch_rerank_batched_range(probs, segs, nseg, rows, P, lo, INT32_MAX, t, counters, st);
 }
 
 namespace {

@@ -176,12 +176,11 @@ __device__ __forceinline__ void exact_keys(const RerankParams& p, const float* _
         sqdist_multi<VEC, NC>(q, cp, d, r);
 #pragma unroll
         for (int i = 0; i < NC; ++i) err_max = fmaxf(err_max, fabsf((a[i] + qn2) - r[i]) * inv_e);
-        __syncwarp();
+        // every lane has read these keys before the reduction's shuffles: lane 0 may overwrite them
         if (lane == 0) {
 #pragma unroll
             for (int i = 0; i < NC; ++i) K[c + i] = make_key(r[i], j[i]);
         }
-        __syncwarp();
     }
     for (; c < hi; ++c) {
         const uint64_t key = K[c];
@@ -189,10 +188,9 @@ __device__ __forceinline__ void exact_keys(const RerankParams& p, const float* _
         float r[1];
         sqdist_multi<VEC, 1>(q, cp, d, r);
         err_max = fmaxf(err_max, fabsf((key_val(key) + qn2) - r[0]) * inv_e);
-        __syncwarp();
         if (lane == 0) K[c] = make_key(r[0], key_idx(key));
-        __syncwarp();
     }
+    __syncwarp();
 }
 
 // One warp re-ranks row `row` of p; K is the warp's shared-memory array of P keys

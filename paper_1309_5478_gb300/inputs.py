@@ -163,6 +163,26 @@ def anisotropic_mixture(n: int = 524288, d: int = 768, components: int = 256, me
     return out
 
 
+def tight_groups(n: int = 262144, d: int = 1024, group: int = 128, spread: float = 0.01,
+                 seed: int = SEED_BASE + 9) -> np.ndarray:
+    """Groups of near-duplicate points: n / group unit-norm Gaussian centres g / |g|, each with
+    `group` members c + spread * z / sqrt(d) (z standard normal), rows in a seeded order
+    (members of a group are not adjacent). Within a group squared distances are about
+    2 spread^2; between groups about 2."""
+    groups = n // group
+    centres = _rows_normal(seed, S_MEANS, groups, d)
+    centres /= np.sqrt((centres * centres).sum(axis=1, keepdims=True))
+    owner = permutation(seed, S_PERM, n) % groups
+    out = np.empty((n, d), dtype=np.float32)
+    rows_per = max(1, _CHUNK // d)
+    scale = spread / math.sqrt(d)
+    for r in range(0, n, rows_per):
+        m = min(rows_per, n - r)
+        z = normal(seed, S_VALUES, r * d, m * d).reshape(m, d)
+        out[r:r + m] = (centres[owner[r:r + m]] + scale * z).astype(np.float32)
+    return out
+
+
 STRESS_KINDS = ("offset", "binades_bf16", "binades_fp8", "parallel")
 
 

@@ -272,3 +272,14 @@ def test_gemm_error_stays_within_its_bound(precision, kind, d):
     rows = inputs.sample_rows(len(X), 16, seed=85)
     ref_idx, ref_dist = oracle.knng(X, 16, rows=rows)
     check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
+
+
+def test_fp8_certifies_near_duplicate_groups():
+    # groups of 128 near-duplicates: the FP8 error bound is far below the gap between groups,
+    # so every row is certified by the first pass (no fallback) and the graph is exact
+    X = inputs.tight_groups(n=32768, d=256, group=128, seed=86)
+    idx, dist, st = graph(X, 64, "fp8")
+    assert st["rows_uncertified"] == 0 and st["rows_fallback"] == 0, st
+    rows = inputs.sample_rows(len(X), 48, seed=87)
+    ref_idx, ref_dist = oracle.knng(X, 64, rows=rows)
+    check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
