@@ -26,7 +26,9 @@
  *     pageable) are copied to the device and back on the call's stream.
  *   - The caller owns all inputs and outputs. The library owns its workspace, cached
  *     per device and released by knn_shutdown().
- *   - Calls are synchronous: they return once outputs are written (or on error).
+ *   - Calls are synchronous: they return once outputs are written (or on error). Calls on
+ *     the same device from several host threads must be serialised by the caller: they share
+ *     the device's cached workspace and staging buffers.
  *   - Errors are returned as a knn_status, never by aborting. On a non-OK status the
  *     outputs are undefined; knn_last_error() gives a message (per thread).
  *   - Indices are int32; N must be below 2^31.

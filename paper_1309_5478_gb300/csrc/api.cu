@@ -44,6 +44,8 @@ struct DevWs {
 };
 std::mutex g_ws_mu;
 std::unordered_map<int, DevWs> g_ws;
+std::mutex g_stage_mu;
+std::unordered_map<int, std::vector<DevWs>> g_stage;  // staging buffers of host arrays, per device and slot
 thread_local int64_t g_ws_cap = 0;  // knn_options.max_workspace_bytes of the running call (0: none)
 }  // namespace
 
@@ -96,6 +98,16 @@ void workspace_release_all() {
         }
     }
     g_ws.clear();
+    {
+        std::lock_guard<std::mutex> lk2(g_stage_mu);
+        for (auto& kv : g_stage) {
+            cudaSetDevice(kv.first);
+            cudaDeviceSynchronize();
+            for (auto& w : kv.second)
+                if (w.ptr) cudaFree(w.ptr);
+        }
+        g_stage.clear();
+    }
     cudaSetDevice(cur);
     cudaGetLastError();
 }
@@ -545,7 +557,7 @@ struct ProbeBuffers {
 // sweep (truncated, re-rank certificate, second pass). Where the edges spread widely
 // the proposal is loose and costs nothing.
 int probe_cap(const Problem& pb, int prec, int km, const CommonLayout& L, const ProbeBuffers& pr, cudaStream_t st,
-              Timing& tm, int* cap_out, float* spec_d2) {
+              Timing& tm, int* cap_out, float* spec_d2, int* keys_le_t = nullptr) {
     std::vector<int32_t> rows(PROBE_ROWS);
     for (int i = 0; i < PROBE_ROWS; ++i) rows[i] = static_cast<int32_t>((pb.M * (2 * i + 1)) / (2 * PROBE_ROWS));
     KNN_CK(cudaMemcpyAsync(pr.rows, rows.data(), PROBE_ROWS * sizeof(int32_t), cudaMemcpyHostToDevice, st));
@@ -577,6 +589,16 @@ int probe_cap(const Problem& pb, int prec, int km, const CommonLayout& L, const 
         const float med = edge[PROBE_ROWS / 2], mx = edge[PROBE_ROWS - 1];
         const float t = mx + 2.f * (mx - med) + 1e-6f * std::fabs(mx);
         *spec_d2 = std::isfinite(t) ? t : __builtin_huge_valf();
+        if (keys_le_t && std::isfinite(t)) {
+            // the most keys any sampled row has at or below t (its inbox in the symmetric form)
+            KNN_CK(launch_count_le(pr.D, PROBE_ROWS, pb.N, pb.N, t, L.ps.qnorm2, pr.rows,
+                                   pb.graph ? pr.rows : nullptr, pr.cnt, st));
+            ++tm.launches;
+            std::vector<int32_t> le(PROBE_ROWS);
+            KNN_CK(cudaMemcpyAsync(le.data(), pr.cnt, PROBE_ROWS * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            KNN_CK(cudaStreamSynchronize(st));
+            *keys_le_t = *std::max_element(le.begin(), le.end());
+        }
     }
     std::sort(cnt.begin(), cnt.end());
     std::sort(cnt4.begin(), cnt4.end());
@@ -707,12 +729,13 @@ int tile_stride(int64_t n) {
 }
 
 // The symmetric form of a k-NN graph (half the distance product; KNN_SYMMETRIC=0 turns it
-// off): it needs the probe's start threshold, which it also takes as the threshold of the
-// transposed pairs.
-bool symmetric_enabled() {
+// off, 2 takes it even where the probe expects inboxes to overflow): it needs the probe's
+// start threshold, which it also takes as the threshold of the transposed pairs.
+int symmetric_mode() {
     const char* e = std::getenv("KNN_SYMMETRIC");
-    return !e || std::atoi(e) != 0;
+    return e ? std::atoi(e) : 1;
 }
+bool symmetric_enabled() { return symmetric_mode() != 0; }
 
 // Pairs (i, j) the symmetric form's fused launch computes: row block rb (128 rows) sweeps
 // the columns from 256 (rb / 2) on.
@@ -814,7 +837,10 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     KNN_CK(cudaMemsetAsync(L.status, 0, sizeof(int), st));
     float spec_d2 = __builtin_huge_valf();
     const bool spec = speculate(pb);
-    if (probe) KNN_TRY(probe_cap(pb, prec, km, L, pr, st, tm, &cap, spec && spec_start() ? &spec_d2 : nullptr));
+    int keys_le_t = 0;
+    if (probe)
+        KNN_TRY(probe_cap(pb, prec, km, L, pr, st, tm, &cap, spec && spec_start() ? &spec_d2 : nullptr,
+                          sym_want ? &keys_le_t : nullptr));
     if (cap_env > 0) cap = cap_env;
     const int stages = fused_stages(cap, prec);
     if (stages == 0) return set_error(KNN_EINTERNAL, "fused list capacity %d does not fit", cap);
@@ -850,7 +876,10 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.qnorm2 = L.ps.qnorm2;
     fp.spec_d2 = spec_d2;
     fp.wait_limit = wait_limit();
-    const bool sym = sym_want && std::isfinite(spec_d2);
+    // the symmetric form needs the inboxes to hold a row's transposed pairs: where sampled rows
+    // already have more keys below the threshold than three quarters of an inbox (crowded or
+    // unevenly dense data), the full sweep is kept
+    const bool sym = sym_want && std::isfinite(spec_d2) && (keys_le_t <= (3 * cap_in) / 4 || symmetric_mode() == 2);
     if (sym) {
         // no speculative ranks mid-sweep: the start threshold alone is speculative, and the
         // certificate checks it for every row (rows it rejects take the second pass)
@@ -939,10 +968,42 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // host-array staging
 // ---------------------------------------------------------------------------
+// Device copies of host arrays. The buffers are cached per device and slot (the i-th array a
+// call stages) and only grow, like the workspace, so repeated calls on host arrays neither
+// allocate nor free (cudaFree would also synchronise the device); knn_shutdown releases them.
 struct Staged {
-    std::vector<std::pair<void*, size_t>> owned;
+    int slot = 0;
+    cudaStream_t stream = nullptr;
+    bool finished = false;
+    // a call that returns early may leave copies into the cached buffers in flight: they end
+    // before the buffers can serve another call
     ~Staged() {
-        for (auto& p : owned) cudaFree(p.first);
+        if (slot > 0 && !finished) cudaStreamSynchronize(stream);
+    }
+    int take(size_t bytes, void** d) {
+        int dev = 0;
+        KNN_CK(cudaGetDevice(&dev));
+        std::lock_guard<std::mutex> lk(g_stage_mu);
+        std::vector<DevWs>& v = g_stage[dev];
+        if (static_cast<int>(v.size()) <= slot) v.resize(static_cast<size_t>(slot) + 1);
+        DevWs& w = v[static_cast<size_t>(slot++)];
+        if (w.bytes < bytes) {
+            if (w.ptr) {
+                KNN_CK(cudaDeviceSynchronize());
+                KNN_CK(cudaFree(w.ptr));
+                w.ptr = nullptr;
+                w.bytes = 0;
+            }
+            cudaError_t e = cudaMalloc(&w.ptr, bytes ? bytes : 1);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                w.ptr = nullptr;
+                return set_error(KNN_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
+            }
+            w.bytes = bytes ? bytes : 1;
+        }
+        *d = w.ptr;
+        return KNN_OK;
     }
     int in(const void* p, size_t bytes, cudaStream_t st, const void** out) {
         if (!p || is_device_pointer(p)) {
@@ -950,12 +1011,8 @@ struct Staged {
             return KNN_OK;
         }
         void* d = nullptr;
-        cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(KNN_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
-        }
-        owned.emplace_back(d, bytes);
+        stream = st;
+        KNN_TRY(take(bytes, &d));
         KNN_CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, st));
         *out = d;
         return KNN_OK;
@@ -968,20 +1025,17 @@ struct Staged {
             return KNN_OK;
         }
         void* d = nullptr;
-        cudaError_t e = cudaMalloc(&d, bytes ? bytes : 1);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return set_error(KNN_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e));
-        }
-        owned.emplace_back(d, bytes);
+        KNN_TRY(take(bytes, &d));
         outs.emplace_back(p, d, bytes);
         *dev = d;
         return KNN_OK;
     }
     int copy_back(cudaStream_t st) {
+        stream = st;
         for (auto& t : outs)
             KNN_CK(cudaMemcpyAsync(std::get<0>(t), std::get<1>(t), std::get<2>(t), cudaMemcpyDeviceToHost, st));
         KNN_CK(cudaStreamSynchronize(st));
+        finished = true;
         return KNN_OK;
     }
 };

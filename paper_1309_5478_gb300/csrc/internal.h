@@ -151,6 +151,11 @@ cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t l
                               const int32_t* row_ids, int32_t* out_count, int32_t* out_count4, float* out_edge,
                               cudaStream_t st);
 
+// out[i] = #{ j != self_col[i] : D[i][j] + qnorm2[row_ids[i]] <= t } for the sampled rows: the
+// keys at or below the squared distance t (the most the symmetric form sends to a row's inbox).
+cudaError_t launch_count_le(const float* D, int64_t rows, int64_t N, int64_t ldd, float t, const float* qnorm2,
+                            const int32_t* row_ids, const int32_t* self_col, int32_t* out, cudaStream_t st);
+
 // ---- batched problems (batched.cu, with batched kernels in prep.cu / rerank.cu) ----
 // Device-side description of one problem of a batch and of its buffers.
 struct BatchDev {

@@ -52,7 +52,36 @@ __global__ void band_count_kernel(const float* __restrict__ D, int64_t N, int64_
     }
 }
 
+// Keys of each sampled row at or below a squared distance t (other than the row itself): the
+// transposed pairs the symmetric form would send to that row's inbox, at most.
+__global__ void count_le_kernel(const float* __restrict__ D, int64_t N, int64_t ldd, float t,
+                                const float* __restrict__ qnorm2, const int32_t* __restrict__ rows,
+                                const int32_t* __restrict__ self_col, int32_t* __restrict__ out) {
+    const int64_t i = blockIdx.x;
+    const float lim = t - qnorm2[rows[i]];
+    const float* row = D + i * ldd;
+    const int64_t self = self_col ? self_col[i] : -1;
+    int c = 0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) c += (row[j] <= lim && j != self) ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    __shared__ int part[32];
+    if ((threadIdx.x & 31u) == 0) part[threadIdx.x / 32] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int w = 0; w < static_cast<int>(blockDim.x / 32); ++w) s += part[w];
+        out[i] = s;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_count_le(const float* D, int64_t rows, int64_t N, int64_t ldd, float t, const float* qnorm2,
+                            const int32_t* row_ids, const int32_t* self_col, int32_t* out, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    count_le_kernel<<<static_cast<unsigned>(rows), 512, 0, st>>>(D, N, ldd, t, qnorm2, row_ids, self_col, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_band_count(const float* D, int64_t rows, int64_t N, int64_t ldd, const float* vals, int32_t k,
                               int32_t km, const float* E, const int32_t* self_col, const float* qnorm2,

@@ -20,8 +20,9 @@ def dev(x):
 
 @pytest.fixture
 def symmetric(monkeypatch):
+    # on: 1 (the probe may keep the full sweep where inboxes would overflow), forced: 2
     def set_sym(on):
-        monkeypatch.setenv("KNN_SYMMETRIC", "1" if on else "0")
+        monkeypatch.setenv("KNN_SYMMETRIC", str(int(on)))
     return set_sym
 
 
@@ -31,8 +32,8 @@ def graph(X, k, precision="bf16"):
     return i.cpu().numpy(), d.cpu().numpy(), st
 
 
-def both(X, k, symmetric, precision="bf16"):
-    symmetric(True)
+def both(X, k, symmetric, precision="bf16", forced=False):
+    symmetric(2 if forced else 1)
     a = graph(X, k, precision)
     symmetric(False)
     b = graph(X, k, precision)
@@ -45,8 +46,10 @@ def both(X, k, symmetric, precision="bf16"):
 @pytest.mark.parametrize("precision", ["bf16", "fp8"])
 def test_symmetric_integer_bit_exact(precision, symmetric):
     # 2^30 pairs and more: the band probe runs and proposes the threshold of the transposed pairs
+    # forced: lattice distances are few integers, so many keys tie below the threshold and the
+    # probe alone would keep the full sweep
     X = inputs.integer_lattice(n=33000, d=64, seed=101)
-    a, b = both(X, 16, symmetric, precision)
+    a, b = both(X, 16, symmetric, precision, forced=True)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     rows = np.concatenate([np.arange(0, 300), inputs.sample_rows(len(X), 64, seed=102), np.arange(len(X) - 200, len(X))])
     check_exact(a[0][rows], a[1][rows], *oracle.knng(X, 16, rows=rows))
@@ -66,7 +69,7 @@ def test_symmetric_clustered_rows_beyond_the_threshold(symmetric):
     # uneven cluster sizes: rows in sparse clusters have k-th distances beyond the sampled
     # threshold; the certificate rejects them and the second pass makes them exact
     X = inputs.anisotropic_mixture(n=36000, d=96, components=40, seed=105)
-    a, b = both(X, 32, symmetric)
+    a, b = both(X, 32, symmetric, forced=True)
     assert np.array_equal(a[0], b[0])
     assert np.allclose(a[1], b[1], rtol=1e-6, atol=0)
     rows = inputs.sample_rows(len(X), 96, seed=106)
@@ -77,13 +80,16 @@ def test_symmetric_clustered_rows_beyond_the_threshold(symmetric):
 def test_symmetric_inbox_overflow_is_caught(symmetric):
     # points crowded far from the origin: the reduced-precision bound dwarfs the distances,
     # every transposed pair passes the threshold, the inboxes overflow, and every row is
-    # recomputed -- still exact
+    # recomputed -- still exact. Left to the probe, the full sweep is taken instead.
     rng = np.random.default_rng(107)
     base = rng.standard_normal(32).astype(np.float32) * 30
     X = (base + 0.05 * rng.standard_normal((33000, 32))).astype(np.float32)
-    symmetric(True)
+    symmetric(2)  # forced: the probe alone would keep the full sweep here
     i, d, st = graph(X, 8)
     assert st["symmetric"] == 1 and st["rows_fallback"] == len(X)
+    symmetric(1)
+    assert graph(X, 8)[2]["symmetric"] == 0
     rows = inputs.sample_rows(len(X), 48, seed=108)
     ref_idx, ref_dist = oracle.knng(X, 8, rows=rows)
     check_float(X, X, rows, i[rows], d[rows], ref_idx, ref_dist, exclude_self=True)
+
