@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--train-rows", type=int, default=50000, help="mlp mode: training rows")
     ap.add_argument("--epochs", type=int, default=40, help="mlp mode: training epochs")
     ap.add_argument("--problems", type=int, default=512, help="batch mode: number of problems")
+    ap.add_argument("--batch-k", type=str, default="",
+                    help="batch mode: keep only the problems whose k is in this comma list (same shapes and seeds)")
+    ap.add_argument("--batch-d", type=str, default="",
+                    help="batch mode: keep only the problems whose d is in this comma list")
     ap.add_argument("--q", type=int, default=16384, help="select mode: rows")
     ap.add_argument("--cols", type=int, default=65536, help="select mode: row length n")
     return ap.parse_args()
@@ -105,14 +109,23 @@ def run_batch(args):
     from paper_1309_5478_gb300 import binding as kb
     from paper_1309_5478_gb300 import inputs
     shapes = inputs.batch_problems(count=args.problems)
+    keep_k = {int(v) for v in args.batch_k.split(",") if v}
+    keep_d = {int(v) for v in args.batch_d.split(",") if v}
     g = torch.Generator(device="cuda").manual_seed(20130904)
     probs = []
+    kept = []
     for pr in shapes:
         Q = torch.randn((pr.M, pr.d), device="cuda", generator=g, dtype=torch.float32)
         C = torch.randn((pr.N, pr.d), device="cuda", generator=g, dtype=torch.float32)
+        if (keep_k and pr.k not in keep_k) or (keep_d and pr.d not in keep_d):
+            del Q, C  # drawn all the same, so a subset keeps the full batch's data
+            continue
+        kept.append(pr)
         probs.append({"Q": Q, "C": C, "k": pr.k,
                       "out_idx": torch.empty((pr.M, pr.k), dtype=torch.int32, device="cuda"),
                       "out_dist": torch.empty((pr.M, pr.k), dtype=torch.float32, device="cuda")})
+    subset = len(kept) != len(shapes)
+    shapes = kept
     rows = sum(pr.M for pr in shapes)
     pairs = sum(pr.M * pr.N for pr in shapes)
     flops = sum(2.0 * pr.M * pr.N * pr.d for pr in shapes)
@@ -142,7 +155,9 @@ def run_batch(args):
             "unit": "rows/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": f"{len(shapes)} independent k-NN search problems, M~U[256,16384], N~U[1024,65536], "
-                                   "d in {64,128,256,768}, k in {1,8,32,128,512}, N(0,1) FP32",
+                                   "d in {64,128,256,768}, k in {1,8,32,128,512}, N(0,1) FP32"
+                                   + (f" (subset: k in {sorted(keep_k) or 'all'}, d in {sorted(keep_d) or 'all'})"
+                                      if subset else ""),
                        "rows": rows, "pairs": pairs, "gemm_tflop": flops / 1e12, "k_histogram": kinds,
                        "l2": "inputs ~26 GB > L2"},
             "pairs_per_s": pairs / (ms / 1e3), "effective_tflops": flops / (ms / 1e3) / 1e12,

@@ -22,6 +22,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -283,12 +284,20 @@ std::map<int, BatchWs> g_bws;
 // fused launch, after the fused problems' re-rank, end (after the plain problems).
 constexpr int N_MARKS = 5;
 
+struct BatchLayout;
+
+// A batch signature's graph, with the layout (and the descriptors uploaded for it) that
+// the graph's launches read; valid while the workspace keeps its generation.
 struct CachedGraph {
     cudaGraphExec_t exec = nullptr;
     uint64_t generation = 0;
     cudaEvent_t marks[N_MARKS] = {};
+    std::shared_ptr<BatchLayout> layout;
+    size_t ws_bytes = 0;
 };
 std::map<std::string, CachedGraph> g_graphs;
+// signature whose descriptors the workspace of each device currently holds
+std::map<int, std::string> g_uploaded;
 
 int batch_ws_get(size_t bytes, void** out, uint64_t* generation) {
     int dev = 0;
@@ -336,6 +345,7 @@ struct BatchLayout {
     RerankCounters* counters = nullptr;
     int* status = nullptr;
     uint64_t* scratch = nullptr;
+    PrepGlobals* globals = nullptr;     // 2 per problem (queries, corpus), read back in one copy
     // plain problems share one set of slab buffers (they run one after another)
     float* slab = nullptr;
     uint64_t* slab_cand = nullptr;
@@ -351,6 +361,7 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
                   BatchLayout& L) {
     const int n = static_cast<int>(probs.size());
     L.dev.assign(n, BatchDev{});
+    L.globals = ar.take<PrepGlobals>(2 * static_cast<size_t>(std::max(n, 1)));
     L.fused_ids.clear();
     L.plain_ids.clear();
     for (int i = 0; i < n; ++i) (is_fused(sched[i]) ? L.fused_ids : L.plain_ids).push_back(i);
@@ -375,8 +386,8 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
         b.vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
                 (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
         const int64_t n_pad = (p.N + 255) / 256 * 256;
-        b.gq = ar.take<PrepGlobals>(1);
-        b.gc = p.graph ? b.gq : ar.take<PrepGlobals>(1);
+        b.gq = L.globals ? L.globals + 2 * i : nullptr;
+        b.gc = p.graph ? b.gq : (L.globals ? L.globals + 2 * i + 1 : nullptr);
         b.cnorm2 = ar.take<float>(n_pad);
         b.qnorm2 = p.graph ? b.cnorm2 : ar.take<float>(p.M);
         b.E = ar.take<float>(p.M);
@@ -573,6 +584,7 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
                 rp.out_dist = p.out_dist + r0 * p.k;
                 rp.row_status = b.row_status + r0;
                 rp.counters = L.counters;
+                rp.uncertified = &b.gq->uncertified;
                 KNN_CK(launch_rerank(rp, st));
             }
         }
@@ -613,73 +625,91 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
     int dev = 0, sms = 0;
     KNN_CK(cudaGetDevice(&dev));
     KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BatchLayout L;
-    Arena sz;
-    layout_batch(probs, sched, prec, sms, sz, L);
-    if (!L.fused_ids.empty() && L.stages == 0) {
-        for (int i : L.fused_ids) sched[i] = SCHED_PLAIN;  // cannot happen: capable problems fit
-        Arena sz2;
-        L = BatchLayout{};
-        layout_batch(probs, sched, prec, sms, sz2, L);
-        sz = sz2;
-    }
+    // the graph, layout and descriptors are kept per batch signature; a repeated call with
+    // the same signature and workspace only launches the graph
+    const std::string sig = signature(probs, sched, prec);
+    std::lock_guard<std::mutex> lk(g_bws_mu);
+    CachedGraph& cg = g_graphs[sig];
     void* base = nullptr;
     uint64_t gen = 0;
-    std::lock_guard<std::mutex> lk(g_bws_mu);
-    KNN_TRY(batch_ws_get(sz.used(), &base, &gen));
-    Arena ar(static_cast<char*>(base), sz.used());
-    L = BatchLayout{};
-    layout_batch(probs, sched, prec, sms, ar, L);
-    // descriptors: tensor maps of the fused problems, then everything to the device
-    for (size_t f = 0; f < L.fused_ids.size(); ++f) {
-        const int i = L.fused_ids[f];
-        const BatchDev& b = L.dev[i];
-        FusedProblem& q = L.fprob[f];
-        const int km = static_cast<int>(std::min<int64_t>(probs[i].k + probs[i].m, probs[i].N - (probs[i].graph ? 1 : 0)));
-        q.M = b.M;
-        q.N = b.N;
-        q.k_bytes = b.d_pad * (prec == P_BF16 ? 2 : 1);
-        q.k = b.k;
-        q.km = km;
-        q.cap = b.cap;
-        q.self_offset = b.graph ? 0 : -1;
-        q.cnorm2 = b.cnorm2;
-        q.E = b.E;
-        q.thr = nullptr;
-        q.q_inv_scale = b.qscale;
-        q.c_inv_scale = b.cscale;
-        q.cand = b.cand;
-        q.count = b.count;
-        q.bound = b.bound;
-        q.flags = b.flags;
-        // speculation as the autotuner chose it, else from 16384 points on
-        const int sc = sched[L.fused_ids[f]];
-        q.spec = sc == SCHED_FUSED_NOSPEC ? 0 : (sc == SCHED_FUSED_SPEC || b.N >= 16384 ? 1 : 0);
-        if (!encode_problem_maps(&q, b.xq, b.xc, prec))
-            return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
+    std::shared_ptr<BatchLayout> Lp;
+    if (cg.exec && cg.layout) {
+        KNN_TRY(batch_ws_get(cg.ws_bytes, &base, &gen));
+        if (gen == cg.generation) Lp = cg.layout;
     }
-    KNN_CK(cudaMemcpyAsync(L.d_dev, L.dev.data(), L.dev.size() * sizeof(BatchDev), cudaMemcpyHostToDevice, st));
-    if (!L.fprob.empty())
-        KNN_CK(cudaMemcpyAsync(L.d_fprob, L.fprob.data(), L.fprob.size() * sizeof(FusedProblem), cudaMemcpyHostToDevice,
-                               st));
-    auto put = [&](auto* dst, const auto& v) -> cudaError_t {
-        if (v.empty()) return cudaSuccess;
-        return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
-    };
-    KNN_CK(put(L.d_prep_segs, L.prep_segs));
-    KNN_CK(put(L.d_query_segs, L.query_segs));
-    KNN_CK(put(L.d_plain_prep_segs, L.plain_prep_segs));
-    KNN_CK(put(L.d_plain_query_segs, L.plain_query_segs));
-    KNN_CK(put(L.d_work, L.work));
-    KNN_CK(cudaStreamSynchronize(st));
+    if (!Lp) {
+        Lp = std::make_shared<BatchLayout>();
+        BatchLayout& L = *Lp;
+        Arena sz;
+        layout_batch(probs, sched, prec, sms, sz, L);
+        if (!L.fused_ids.empty() && L.stages == 0) {
+            for (int i : L.fused_ids) sched[i] = SCHED_PLAIN;  // cannot happen: capable problems fit
+            Arena sz2;
+            L = BatchLayout{};
+            layout_batch(probs, sched, prec, sms, sz2, L);
+            sz = sz2;
+        }
+        KNN_TRY(batch_ws_get(sz.used(), &base, &gen));
+        Arena ar(static_cast<char*>(base), sz.used());
+        L = BatchLayout{};
+        layout_batch(probs, sched, prec, sms, ar, L);
+        // descriptors: tensor maps of the fused problems
+        for (size_t f = 0; f < L.fused_ids.size(); ++f) {
+            const int i = L.fused_ids[f];
+            const BatchDev& b = L.dev[i];
+            FusedProblem& q = L.fprob[f];
+            const int km =
+                static_cast<int>(std::min<int64_t>(probs[i].k + probs[i].m, probs[i].N - (probs[i].graph ? 1 : 0)));
+            q.M = b.M;
+            q.N = b.N;
+            q.k_bytes = b.d_pad * (prec == P_BF16 ? 2 : 1);
+            q.k = b.k;
+            q.km = km;
+            q.cap = b.cap;
+            q.self_offset = b.graph ? 0 : -1;
+            q.cnorm2 = b.cnorm2;
+            q.E = b.E;
+            q.thr = nullptr;
+            q.q_inv_scale = b.qscale;
+            q.c_inv_scale = b.cscale;
+            q.cand = b.cand;
+            q.count = b.count;
+            q.bound = b.bound;
+            q.flags = b.flags;
+            // speculation as the autotuner chose it, else from 16384 points on
+            const int sc = sched[L.fused_ids[f]];
+            q.spec = sc == SCHED_FUSED_NOSPEC ? 0 : (sc == SCHED_FUSED_SPEC || b.N >= 16384 ? 1 : 0);
+            if (!encode_problem_maps(&q, b.xq, b.xc, prec))
+                return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
+        }
+        if (cg.exec) {
+            cudaGraphExecDestroy(cg.exec);  // captured for another workspace
+            cg.exec = nullptr;
+        }
+        cg.layout = nullptr;
+        cg.ws_bytes = sz.used();
+        g_uploaded[dev].clear();
+    }
+    BatchLayout& L = *Lp;
+    if (g_uploaded[dev] != sig) {
+        // the descriptors to the device (the layout's host vectors outlive the copies)
+        KNN_CK(cudaMemcpyAsync(L.d_dev, L.dev.data(), L.dev.size() * sizeof(BatchDev), cudaMemcpyHostToDevice, st));
+        if (!L.fprob.empty())
+            KNN_CK(cudaMemcpyAsync(L.d_fprob, L.fprob.data(), L.fprob.size() * sizeof(FusedProblem),
+                                   cudaMemcpyHostToDevice, st));
+        auto put = [&](auto* dst, const auto& v) -> cudaError_t {
+            if (v.empty()) return cudaSuccess;
+            return cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice, st);
+        };
+        KNN_CK(put(L.d_prep_segs, L.prep_segs));
+        KNN_CK(put(L.d_query_segs, L.query_segs));
+        KNN_CK(put(L.d_plain_prep_segs, L.plain_prep_segs));
+        KNN_CK(put(L.d_plain_query_segs, L.plain_query_segs));
+        KNN_CK(put(L.d_work, L.work));
+        g_uploaded[dev] = sig;
+    }
 
     // the graph: captured once per batch signature, replayed afterwards
-    const std::string sig = signature(probs, sched, prec);
-    CachedGraph& cg = g_graphs[sig];
-    if (cg.exec && cg.generation != gen) {
-        cudaGraphExecDestroy(cg.exec);
-        cg.exec = nullptr;
-    }
     if (!cg.marks[0])
         for (auto& e : cg.marks) KNN_CK(cudaEventCreate(&e));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -700,6 +730,7 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         cudaGraphDestroy(g);
         KNN_CK(ei);
         cg.generation = gen;
+        cg.layout = Lp;
     }
     KNN_CK(cudaEventCreate(&e0));
     KNN_CK(cudaEventCreate(&e1));
@@ -708,8 +739,10 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
     KNN_CK(cudaEventRecord(e1, st));
     RerankCounters hc{};
     int hstatus = 0;
+    std::vector<PrepGlobals> hg(2 * static_cast<size_t>(n));
     KNN_CK(cudaMemcpyAsync(&hc, L.counters, sizeof(hc), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaMemcpyAsync(&hstatus, L.status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    KNN_CK(cudaMemcpyAsync(hg.data(), L.globals, hg.size() * sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
     KNN_CK(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -726,13 +759,10 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
     // per problem: NaN/Inf inputs, then rows the batch could not certify
     int first = KNN_OK;
     int64_t fallback_rows = 0;
-    std::vector<PrepGlobals> hg(2);
     for (int i = 0; i < n; ++i) {
-        const BatchDev& b = L.dev[i];
-        KNN_CK(cudaMemcpyAsync(&hg[0], b.gq, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
-        KNN_CK(cudaMemcpyAsync(&hg[1], b.gc, sizeof(PrepGlobals), cudaMemcpyDeviceToHost, st));
-        KNN_CK(cudaStreamSynchronize(st));
-        if (hg[0].nonfinite || hg[1].nonfinite) {
+        const PrepGlobals& gq = hg[2 * static_cast<size_t>(i)];
+        const PrepGlobals& gc = probs[i].graph ? gq : hg[2 * static_cast<size_t>(i) + 1];
+        if (gq.nonfinite || gc.nonfinite) {
             status[i] = set_error(KNN_EINVAL, "problem %d: input holds NaN or Inf", i);
             if (first == KNN_OK) first = status[i];
         }
@@ -740,7 +770,8 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
     if (hc.uncertified > 0) {
         std::vector<uint32_t> rs;
         for (int i = 0; i < n; ++i) {
-            if (status[i] != KNN_OK) continue;
+            // the re-rank counted each problem's uncertified rows in its query statistics
+            if (status[i] != KNN_OK || hg[2 * static_cast<size_t>(i)].uncertified == 0) continue;
             const BatchDev& b = L.dev[i];
             rs.resize(static_cast<size_t>(b.M));
             KNN_CK(cudaMemcpyAsync(rs.data(), b.row_status, b.M * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));

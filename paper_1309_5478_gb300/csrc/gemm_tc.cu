@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int64_t grow = static_cast<int64_t>(item_rb(p, it)) * TC_BM + r;
                 if (grow >= p.M) break;
                 if (row_keys(p.rr, grow) > RR_P) continue;
-                rerank_row<true, 4>(p.rr, grow, RR_P, K, T64, cnt, lane);
+                rerank_row<true, 4, 32>(p.rr, grow, RR_P, K, T64, cnt, lane);
             }
         }
         __syncwarp();

@@ -17,7 +17,8 @@ struct PrepGlobals {
     uint32_t max_tnorm;   // max |x~|
     uint32_t nonfinite;   // rows holding NaN or Inf
     uint32_t noninteger;  // rows holding a non-integer value
-    uint32_t pad[2];
+    uint32_t uncertified; // query rows the re-rank left uncertified (batched form, query side)
+    uint32_t pad;
 };
 
 // Per-row candidate state handed from the select to the re-rank.
@@ -135,6 +136,7 @@ struct RerankParams {
     const uint64_t* inbox;
     const int32_t* inbox_cnt;
     int32_t cap_in;
+    uint32_t* uncertified;  // optional: counts the rows left uncertified (one atomic per such row)
 };
 // Lists longer than 512 (and 1024) keys are re-ranked by further launches with larger
 // per-warp buffers, so the common short lists keep the higher occupancy.

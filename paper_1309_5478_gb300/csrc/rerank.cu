@@ -23,7 +23,7 @@ __device__ __forceinline__ void block_flush(RerankCounters* counters, unsigned l
 // One warp per row. With a work counter (next != nullptr) the launch is persistent: every
 // warp takes the next row from the counter until none is left, so warps never wait for the
 // slowest row of their CTA; without one, warp w of CTA b takes row b * warps + w.
-template <bool VEC, int NC, int MINB>
+template <bool VEC, int NC, int MINB, int G>
 __global__ void __launch_bounds__(256, MINB) rerank_kernel(RerankParams p, int P, unsigned long long* next) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long cnt[8][RC_COUNT];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256, MINB) rerank_kernel(RerankParams p, int P
         if (row >= p.M) break;
         if (!(p.skip_done && (p.row_status[row] & ROW_RERANKED))) {
             const int c = row_keys(p, row);
-            if (c >= p.count_min && c <= p.count_max) rerank_row<VEC, NC>(p, row, P, K, T64, cnt[warp], lane);
+            if (c >= p.count_min && c <= p.count_max) rerank_row<VEC, NC, G>(p, row, P, K, T64, cnt[warp], lane);
         }
         if (!next) break;
     }
@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(256, 3)
         rp.out_idx = b.out_idx;
         rp.out_dist = b.out_dist;
         rp.row_status = b.row_status;
+        rp.uncertified = &b.gq->uncertified;
         const int64_t r = row - sg.row0;
         const int c = list_length(b.count[r], b.flags[r]);
         if (c >= count_min && c <= count_max) {
@@ -171,7 +172,16 @@ using RerankKernel = void (*)(RerankParams, int, unsigned long long*);
 // 64 registers a thread (four CTAs of eight warps an SM): the re-rank is bound by the latency
 // of its gathers, and more warps in flight beat longer unrolls (measured on GB300: 19.6 ms for
 // the 262144-row graph against 20.7 ms at 116 registers and 24.5-26.1 ms with 8-candidate groups).
-RerankKernel rerank_variant(bool vec) { return vec ? rerank_kernel<true, 4, 4> : rerank_kernel<false, 4, 4>; }
+template <int G>
+RerankKernel rerank_variant_g(bool vec) { return vec ? rerank_kernel<true, 4, 4, G> : rerank_kernel<false, 4, 4, G>; }
+// lanes per candidate of the distance evaluation by dimension (rerank_group)
+RerankKernel rerank_variant(bool vec, int d) {
+    switch (rerank_group(d)) {
+        case 8: return rerank_variant_g<8>(vec);
+        case 16: return rerank_variant_g<16>(vec);
+        default: return rerank_variant_g<32>(vec);
+    }
+}
 
 cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cmax, int tier, cudaStream_t st) {
     p.count_min = cmin;
@@ -183,7 +193,7 @@ cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cma
     const size_t smem = per_warp * warps;
     const bool vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
-    auto kern = rerank_variant(vec);
+    auto kern = rerank_variant(vec, p.d);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int64_t blocks = (p.M + warps - 1) / warps;

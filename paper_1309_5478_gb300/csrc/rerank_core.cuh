@@ -5,9 +5,9 @@
 // ranking values d'_ij = |c_j|^2 - 2 q_i.c_j (Methods, "Distance calculation").
 // Here every candidate's squared distance is recomputed in the direct difference
 // form sum_t (q_t - c_t)^2, which has no cancellation:
-//   - each lane adds its four products of a 16-byte group with FMAs and folds the
-//     group sum into a (sum, error) pair with Knuth's TwoSum; the warp reduction adds
-//     the pairs with TwoSum as well. The result's relative error is at most about
+//   - 8, 16 or 32 lanes share a candidate (by dimension); each lane adds its four
+//     products of a 16-byte group with FMAs and folds the group sum into a (sum, error)
+//     pair with Knuth's TwoSum; the reduction over the lanes adds the pairs with TwoSum. The result's relative error is at most about
 //     8 units in the last place (2 for the rounded differences, 4 for the group sums,
 //     2 for the final roundings), below 2^-20.
 //   - candidates are taken in ascending approximate order. Once the first k are exact,
@@ -155,9 +155,10 @@ __device__ __forceinline__ int row_keys(const RerankParams& p, int64_t row) {
 }
 
 // Exact keys for positions [lo, hi) of K (approximate keys in, exact keys out), NC
-// candidates at a time; err_max collects |approximate + qn2 - exact| / E (E > 0).
+// candidates at a time, each shared by the whole warp; err_max collects
+// |approximate + qn2 - exact| / E (E > 0).
 template <bool VEC, int NC>
-__device__ __forceinline__ void exact_keys(const RerankParams& p, const float* __restrict__ q, uint64_t* K, int lo,
+__device__ __forceinline__ void exact_keys_warp(const RerankParams& p, const float* __restrict__ q, uint64_t* K, int lo,
                                            int hi, float qn2, float inv_e, float& err_max, uint32_t lane) {
     const int d = p.d;
     int c = lo;
@@ -193,10 +194,112 @@ __device__ __forceinline__ void exact_keys(const RerankParams& p, const float* _
     __syncwarp();
 }
 
+// The (sum, error) pair reduced over an aligned group of G lanes (xor shuffles stay
+// inside the group); every lane of the group returns the group's total.
+template <int G>
+__device__ __forceinline__ float group_reduce_pair(float s, float e) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(0xffffffffu, s, o);
+        const float eo = __shfl_xor_sync(0xffffffffu, e, o);
+        float t, err;
+        two_sum(s, so, t, err);
+        s = t;
+        e = e + eo + err;
+    }
+    return s + e;
+}
+
+// Exact keys for positions [lo, hi) of K (approximate keys in, exact keys out), with
+// the warp split into 32 / G groups of G lanes; err_max collects
+// |approximate + qn2 - exact| / E (E > 0) and is warp-uniform on return. A group takes NC
+// candidates at a time, each lane reading one 16-byte piece of each candidate row per
+// step, so one pass evaluates 32 / G * NC candidates and a distance's reduction takes
+// log2(G) shuffle levels.
+template <bool VEC, int G, int NC>
+__device__ __forceinline__ void exact_keys_g(const RerankParams& p, const float* __restrict__ q, uint64_t* K, int lo,
+                                             int hi, float qn2, float inv_e, float& err_max, uint32_t lane) {
+    constexpr int PER = (32 / G) * NC;
+    const int d = p.d;
+    const int g = static_cast<int>(lane) / G;
+    const int gl = static_cast<int>(lane) % G;
+    for (int c = lo; c < hi; c += PER) {
+        uint32_t j[NC];
+        float a[NC];
+        const float* cp[NC];
+        bool live[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) {
+            const int pos = c + g * NC + i;
+            live[i] = pos < hi;
+            const uint64_t key = K[live[i] ? pos : lo];
+            j[i] = key_idx(key);
+            a[i] = key_val(key);
+            cp[i] = p.C + static_cast<int64_t>(j[i]) * d;
+        }
+        float s[NC], e[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) s[i] = e[i] = 0.f;
+#pragma unroll 2
+        for (int t = gl * 4; t < d; t += 4 * G) {
+            const float4 qa = load4(q, t, d, VEC);
+#pragma unroll
+            for (int i = 0; i < NC; ++i) {
+                float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (live[i]) b = load4(cp[i], t, d, VEC);
+                group_sum(qa, b, s[i], e[i]);
+            }
+        }
+        float r[NC];
+#pragma unroll
+        for (int i = 0; i < NC; ++i) r[i] = group_reduce_pair<G>(s[i], e[i]);
+#pragma unroll
+        for (int i = 0; i < NC; ++i)
+            if (live[i]) err_max = fmaxf(err_max, fabsf((a[i] + qn2) - r[i]) * inv_e);
+        // every lane has read these keys before the reduction's shuffles: the group's first
+        // lane may overwrite its group's keys
+        if (gl == 0) {
+#pragma unroll
+            for (int i = 0; i < NC; ++i)
+                if (live[i]) K[c + g * NC + i] = make_key(r[i], j[i]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) err_max = fmaxf(err_max, __shfl_xor_sync(0xffffffffu, err_max, o));
+    __syncwarp();
+}
+
+// Lanes per candidate by dimension: short rows are shared by fewer lanes (more candidates
+// at once, fewer shuffle levels); above d = 256 the whole warp reads each row in 512-byte
+// steps (exact_keys_warp), which keeps the gathers in long bursts per row (measured on
+// GB300: with groups of 8 lanes the 262144 x 1024 graph's re-rank took 33 ms instead of
+// 19.6 ms, while the d = 64 problems of a batch went from 15.8 to 13.1 ms).
+__host__ __device__ constexpr int rerank_group(int d) { return d <= 128 ? 8 : (d <= 256 ? 16 : 32); }
+
+// G: lanes per candidate (32: exact_keys_warp), or 0 to choose by p.d at run time among
+// the grouped forms (kernels whose rows have several dimensions; fewer registers than with
+// exact_keys_warp among them).
+template <bool VEC, int G, int NC>
+__device__ __forceinline__ void exact_keys(const RerankParams& p, const float* __restrict__ q, uint64_t* K, int lo,
+                                           int hi, float qn2, float inv_e, float& err_max, uint32_t lane) {
+    if constexpr (G == 32) {
+        exact_keys_warp<VEC, NC>(p, q, K, lo, hi, qn2, inv_e, err_max, lane);
+    } else if constexpr (G != 0) {
+        exact_keys_g<VEC, G, NC>(p, q, K, lo, hi, qn2, inv_e, err_max, lane);
+    } else {
+        if (p.d <= 128)
+            exact_keys_g<VEC, 8, NC>(p, q, K, lo, hi, qn2, inv_e, err_max, lane);
+        else if (p.d <= 256)
+            exact_keys_g<VEC, 16, NC>(p, q, K, lo, hi, qn2, inv_e, err_max, lane);
+        else
+            exact_keys_g<VEC, 32, NC>(p, q, K, lo, hi, qn2, inv_e, err_max, lane);
+    }
+}
+
 // One warp re-ranks row `row` of p; K is the warp's shared-memory array of P keys
 // (P >= the row's list length, a power of two) and T64 its TIE_MAX doubles for one
 // near-tie group; cnt the warp's RC_COUNT counters (shared memory).
-template <bool VEC, int NC>
+template <bool VEC, int NC, int G = 0>
 __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, int P, uint64_t* K, double* T64,
                                            unsigned long long* cnt, uint32_t lane) {
     const int raw = p.count[row];
@@ -268,7 +371,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
 
     // 1. direct-difference FP32 distances: the first k candidates, then the rest up to
     //    the first one that provably lies beyond the k-th exact distance
-    exact_keys<VEC, NC>(p, q, K, 0, kk, qn2, inv_e, err_max, lane);
+    exact_keys<VEC, G, NC>(p, q, K, 0, kk, qn2, inv_e, err_max, lane);
     int stop = count;
     if (can_stop) {
         float mx = 0.f;
@@ -287,7 +390,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
             }
         stop = static_cast<int>(__reduce_min_sync(0xffffffffu, static_cast<uint32_t>(first)));
     }
-    exact_keys<VEC, NC>(p, q, K, kk, stop, qn2, inv_e, err_max, lane);
+    exact_keys<VEC, G, NC>(p, q, K, kk, stop, qn2, inv_e, err_max, lane);
     count = stop;
 
     // sort only the power of two that holds the list (P bounds it)
@@ -384,6 +487,7 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
     }
     if (lane == 0) {
         p.row_status[row] = (certified ? 0u : ROW_UNCERTIFIED) | (used64 ? ROW_FP64 : 0u) | ROW_RERANKED;
+        if (!certified && p.uncertified) atomicAdd(p.uncertified, 1u);
         cnt[RC_CANDIDATES] += static_cast<unsigned long long>(count);
         if (used64) cnt[RC_FP64_ROWS] += 1ull;
         if (!certified) cnt[RC_UNCERTIFIED] += 1ull;
