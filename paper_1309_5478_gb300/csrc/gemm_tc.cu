@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const int64_t grow = static_cast<int64_t>(item_rb(p, it)) * TC_BM + r;
                 if (grow >= p.M) break;
                 if (row_keys(p.rr, grow) > RR_P) continue;
-                rerank_row<true, 4, 32>(p.rr, grow, RR_P, K, T64, cnt, lane);
+                rerank_row<true, 4, 0>(p.rr, grow, RR_P, K, T64, cnt, lane);
             }
         }
         __syncwarp();
@@ -1280,7 +1280,7 @@ cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, 
     CUtensorMap dummy{};
     const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, false);
     auto kern = fused_kernel<true>(precision, p.cap_max);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
     return cudaGetLastError();
@@ -1296,7 +1296,7 @@ cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStre
     const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, p.rr_on != 0);
     if (smem > 232448) return cudaErrorInvalidValue;
     auto kern = fused_kernel<false>(precision, p.cap_max);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);
     return cudaGetLastError();

@@ -51,6 +51,12 @@ struct RerankCounters {
 };
 
 // ---- prep / bounds (prep.cu) ----
+// Raises a kernel's dynamic shared-memory limit on the current device to at least `bytes`
+// and never lowers it: a kernel launched with several sizes (re-rank tiers, list
+// capacities) keeps every launch recorded earlier valid, including kernel nodes of a
+// captured graph that are launched again on their own (as a profiler's replay does).
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes);
+
 cudaError_t launch_prep(const float* X, int64_t rows, int32_t d, int32_t precision, float* norm2, float* res,
                         float* tnorm, void* xq, int32_t ldq, float* inv_scale, PrepGlobals* g, cudaStream_t st);
 

@@ -167,7 +167,7 @@ cudaError_t launch_sim_rerank(const SimRerankParams& p, int32_t centered, cudaSt
     const size_t smem = stage ? staged : base;
     auto kern = centered ? (stage ? sim_rerank_kernel<true, true> : sim_rerank_kernel<true, false>)
                          : (stage ? sim_rerank_kernel<false, true> : sim_rerank_kernel<false, false>);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(p.M), RR_THREADS, smem, st>>>(p);
     return cudaGetLastError();

@@ -129,8 +129,7 @@ cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* s
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
     const size_t smem = per_warp * warps;
-    cudaError_t e = cudaFuncSetAttribute(rerank_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(rerank_batched_kernel), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaGetDevice(&dev);
@@ -194,7 +193,7 @@ cudaError_t launch_rerank_range(RerankParams p, int P, int32_t cmin, int32_t cma
     const bool vec = (p.d % 4 == 0) && (reinterpret_cast<uintptr_t>(p.Q) % 16 == 0) &&
                      (reinterpret_cast<uintptr_t>(p.C) % 16 == 0);
     auto kern = rerank_variant(vec, p.d);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int64_t blocks = (p.M + warps - 1) / warps;
     unsigned long long* next = nullptr;

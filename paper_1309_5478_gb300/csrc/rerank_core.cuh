@@ -7,9 +7,11 @@
 // form sum_t (q_t - c_t)^2, which has no cancellation:
 //   - 8, 16 or 32 lanes share a candidate (by dimension); each lane adds its four
 //     products of a 16-byte group with FMAs and folds the group sum into a (sum, error)
-//     pair with Knuth's TwoSum; the reduction over the lanes adds the pairs with TwoSum. The result's relative error is at most about
-//     8 units in the last place (2 for the rounded differences, 4 for the group sums,
-//     2 for the final roundings), below 2^-20.
+//     pair with Knuth's TwoSum, then rounds its pair to one float, and the lanes' floats
+//     are summed by a shuffle tree. Every term is non-negative, so each rounding adds at
+//     most one unit of the total: the relative error is at most 2 units in the last place
+//     for the rounded differences, 4 for the group sums, 1 for a lane's pair and 5 for
+//     the tree over 32 lanes (3 over 8), 12 in all: below 2^-20.
 //   - candidates are taken in ascending approximate order. Once the first k are exact,
 //     the largest of them bounds the exact k-th distance of the row from above; a
 //     candidate whose approximate value is more than E_i above that bound (with
@@ -96,6 +98,17 @@ __device__ __forceinline__ float4 load4(const float* __restrict__ p, int t, int 
     return a;
 }
 
+// Sum over an aligned group of G lanes of each lane's (sum, error) pair rounded to one
+// float (plain tree: the partial sums are non-negative, one rounding per level); every
+// lane of the group returns the group's total.
+template <int G>
+__device__ __forceinline__ float group_fold_sum(float s, float e) {
+    float v = s + e;
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Squared distances of the query q to NC candidate rows at once (NC rows of loads in flight
 // per lane); every lane returns the results. VEC: d % 4 == 0 and 16-byte aligned rows.
 template <bool VEC, int NC>
@@ -115,7 +128,7 @@ __device__ __forceinline__ void sqdist_multi(const float* __restrict__ q, const 
         for (int i = 0; i < NC; ++i) group_sum(a, b[i], s[i], e[i]);
     }
 #pragma unroll
-    for (int i = 0; i < NC; ++i) r[i] = warp_reduce_pair(s[i], e[i]);
+    for (int i = 0; i < NC; ++i) r[i] = group_fold_sum<32>(s[i], e[i]);
 }
 
 // |q|^2 with the same compensated summation (relative error below 2^-20).
@@ -194,22 +207,6 @@ __device__ __forceinline__ void exact_keys_warp(const RerankParams& p, const flo
     __syncwarp();
 }
 
-// The (sum, error) pair reduced over an aligned group of G lanes (xor shuffles stay
-// inside the group); every lane of the group returns the group's total.
-template <int G>
-__device__ __forceinline__ float group_reduce_pair(float s, float e) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const float so = __shfl_xor_sync(0xffffffffu, s, o);
-        const float eo = __shfl_xor_sync(0xffffffffu, e, o);
-        float t, err;
-        two_sum(s, so, t, err);
-        s = t;
-        e = e + eo + err;
-    }
-    return s + e;
-}
-
 // Exact keys for positions [lo, hi) of K (approximate keys in, exact keys out), with
 // the warp split into 32 / G groups of G lanes; err_max collects
 // |approximate + qn2 - exact| / E (E > 0) and is warp-uniform on return. A group takes NC
@@ -252,7 +249,7 @@ __device__ __forceinline__ void exact_keys_g(const RerankParams& p, const float*
         }
         float r[NC];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) r[i] = group_reduce_pair<G>(s[i], e[i]);
+        for (int i = 0; i < NC; ++i) r[i] = group_fold_sum<G>(s[i], e[i]);
 #pragma unroll
         for (int i = 0; i < NC; ++i)
             if (live[i]) err_max = fmaxf(err_max, fabsf((a[i] + qn2) - r[i]) * inv_e);
@@ -278,7 +275,8 @@ __host__ __device__ constexpr int rerank_group(int d) { return d <= 128 ? 8 : (d
 
 // G: lanes per candidate (32: exact_keys_warp), or 0 to choose by p.d at run time among
 // the grouped forms (kernels whose rows have several dimensions; fewer registers than with
-// exact_keys_warp among them).
+// exact_keys_warp among them). exact_keys_g<32> and exact_keys_warp do the same operations
+// on every candidate, so every kernel gives a row bit-identical distances.
 template <bool VEC, int G, int NC>
 __device__ __forceinline__ void exact_keys(const RerankParams& p, const float* __restrict__ q, uint64_t* K, int lo,
                                            int hi, float qn2, float inv_e, float& err_max, uint32_t lane) {

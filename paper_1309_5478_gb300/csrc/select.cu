@@ -357,7 +357,7 @@ cudaError_t launch_variant(const SelectParams& p, int bufk, int64_t self_offset,
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || static_cast<int>(smem) > smem_set[dev].load(std::memory_order_relaxed)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) smem_set[dev].store(static_cast<int>(smem), std::memory_order_relaxed);
     }
@@ -487,8 +487,7 @@ cudaError_t launch_select_merge(const int32_t* seg_idx, const float* seg_val, co
     const int P = pow2_ceil(S * k > 32 ? S * k : 32);
     const int warps = 4;
     const size_t smem = static_cast<size_t>(warps) * P * 8;
-    cudaError_t e = cudaFuncSetAttribute(select_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(select_merge_kernel), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     select_merge_kernel<<<static_cast<unsigned>((M + warps - 1) / warps), warps * 32, smem, st>>>(
         seg_idx, seg_val, seg_flags, M, S, k, seg_len, P, out_idx, out_val, flags);
@@ -787,7 +786,7 @@ cudaError_t launch_block_variant(const SelectParams& p, int bufk, int32_t* out_i
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64 || static_cast<int>(smem) > smem_set[dev].load(std::memory_order_relaxed)) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+        e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         if (dev >= 0 && dev < 64) smem_set[dev].store(static_cast<int>(smem), std::memory_order_relaxed);
     }

@@ -111,7 +111,7 @@ cudaError_t launch_stream_merge(const StreamMergeParams& p, cudaStream_t st) {
     const bool stage = staged <= 160 * 1024;
     const size_t smem = stage ? staged : base;
     auto kern = stage ? stream_merge_kernel<true> : stream_merge_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<static_cast<unsigned>(p.M), MG_THREADS, smem, st>>>(p);
     return cudaGetLastError();
