@@ -501,9 +501,9 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
 // the row state untouched, when no such value exists (keep_trunc = 0 disables truncation);
 // the caller then runs shrink_row_k.
 template <int KPL>
-__device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es, const RowState& rs, int r,
-                                                int64_t grow, float window, int rk, int rkm, int keep_max,
-                                                int keep_trunc) {
+__device__ __forceinline__ bool shrink_mid_fast_body(const Item& p, const EpiSmem& es, const RowState& rs, int r,
+                                                     int64_t grow, float window, int rk, int rkm, int keep_max,
+                                                     int keep_trunc) {
     const int lane = static_cast<int>(lane_id());
     const int n0 = rs.cnt[2 * r];
     const int n = n0 + rs.cnt[2 * r + 1];
@@ -607,6 +607,27 @@ __device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es
     }
     __syncwarp();
     return true;
+}
+
+// Out-of-line copy for the longest-list variant (48 keys a lane): its keys would otherwise
+// count against the register allocation of the whole epilogue loop, which then spills inside
+// its filter, while at a shrink only a few of the loop's values are live (lists of 1248 keys
+// in a batch: fused launch 112 -> 108 ms).
+template <int KPL>
+__device__ __noinline__ bool shrink_mid_fast_call(const Item& p, const EpiSmem& es, const RowState& rs, int r,
+                                                  int64_t grow, float window, int rk, int rkm, int keep_max,
+                                                  int keep_trunc) {
+    return shrink_mid_fast_body<KPL>(p, es, rs, r, grow, window, rk, rkm, keep_max, keep_trunc);
+}
+
+template <int KPL>
+__device__ __forceinline__ bool shrink_mid_fast(const Item& p, const EpiSmem& es, const RowState& rs, int r,
+                                                int64_t grow, float window, int rk, int rkm, int keep_max,
+                                                int keep_trunc) {
+    if constexpr (KPL > 32)
+        return shrink_mid_fast_call<KPL>(p, es, rs, r, grow, window, rk, rkm, keep_max, keep_trunc);
+    else
+        return shrink_mid_fast_body<KPL>(p, es, rs, r, grow, window, rk, rkm, keep_max, keep_trunc);
 }
 
 // Value of r[t] for a lane-dependent t (0..31) by a 5-level select tree (no local memory).
