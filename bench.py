@@ -1027,7 +1027,15 @@ def main():
             "path_roofline_frac": path_frac,
             "path_roofline": {"t_roof_ms": t_roof * 1000.0, "gemm_flops": flops,
                               "symmetric": bool(s0.get("symmetric", 0)),
-                              "full_product_flops": 2.0 * args.n * args.n * args.d},
+                              "full_product_flops": 2.0 * args.n * args.n * args.d,
+                              # the full product at tensor peak: the floor of a form without the
+                              # symmetric halving, which this step is compared against
+                              "t_full_product_ms": 2.0 * args.n * args.n * args.d / (P["bf16_sustained"] * 1e12) * 1e3,
+                              # the exact re-rank's gathers (candidates x 4 d bytes) at HBM bandwidth,
+                              # serial after the GEMM: the floor of this form's design
+                              "rerank_gather_bytes": s0["candidates"] * args.d * 4.0,
+                              "t_gemm_then_rerank_ms": (t_roof + s0["candidates"] * args.d * 4.0
+                                                        / (P["hbm_gbs"] * 1e9)) * 1e3},
             "roofline": roof, "clocks": clk,
             "gpu_launches": int(sum(s["kernel_launches"] for s in stats)),
             "exactness": {"rows_uncertified": int(s0["rows_uncertified"]), "rows_fallback": int(s0["rows_fallback"]),

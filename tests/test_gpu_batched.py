@@ -75,6 +75,25 @@ def test_graph_replay_gives_the_same_answer():
     check_all(probs, refs)
 
 
+def test_alternating_batches_keep_their_own_descriptors():
+    # two batches share the batch workspace; each keeps its graph and layout, and the descriptors
+    # the workspace holds are uploaded again whenever the other batch ran in between
+    pa, ra = make_problems(SHAPES[:4], seed0=420)
+    pb, rb = make_problems(SHAPES[4:], seed0=440)
+    runs = []
+    for probs in (pa, pb, pa, pb, pa):
+        for p in probs:
+            p["out_idx"].fill_(-7)
+            p["out_dist"].fill_(-7.0)
+        assert kb.knn_search_batched(probs) == [0] * len(probs)
+        runs.append([(p["out_idx"].clone(), p["out_dist"].clone()) for p in probs])
+    for a, b in ((0, 2), (2, 4), (1, 3)):
+        for (i0, d0), (i1, d1) in zip(runs[a], runs[b]):
+            assert torch.equal(i0, i1) and torch.equal(d0, d1)
+    check_all(pa, ra)
+    check_all(pb, rb)
+
+
 def test_batch_recipe_float_data():
     ps = inputs.batch_problems(count=16, m_range=(256, 1024), n_range=(1024, 6000))
     probs, refs = [], []
