@@ -759,14 +759,6 @@ __device__ __forceinline__ void filter_chunk(uint32_t (&r)[32], const float* cn,
     const uint32_t rounds = __reduce_max_sync(0xffffffffu, static_cast<uint32_t>(__popc(mask)));
     inserted += static_cast<uint32_t>(__popc(mask));
     const uint32_t jlo = static_cast<uint32_t>(j0);
-    if (rounds == 32u && __all_sync(0xffffffffu, mask == 0xffffffffu)) {
-        // every lane keeps the whole chunk (a list's first fill): the same keys in the same
-        // order, stored straight from the registers
-#pragma unroll
-        for (int e = 0; e < 32; ++e) gbuf[base + dir * (cnt + e)] = make_key(__uint_as_float(r[e]), jlo + e);
-        cnt += 32;
-        return;
-    }
     for (uint32_t it = 0; it < rounds; ++it) {
         const int t = (__ffs(mask) - 1) & 31;
         const bool has = mask != 0u;
