@@ -370,7 +370,10 @@ int prep_and_check(const Problem& pb, int prec, CommonLayout& L, cudaStream_t st
         ++tm.launches;
     }
     if (pb.thr) {
-        KNN_CK(launch_threshold_to_dprime(pb.thr, ps.qnorm2, pb.M, ps.thr_dprime, st));
+        if (pb.thr_bound)
+            KNN_CK(launch_bound_to_dprime(pb.thr, ps.qnorm2, ps.E, pb.M, pb.d, ps.thr_dprime, st));
+        else
+            KNN_CK(launch_threshold_to_dprime(pb.thr, ps.qnorm2, pb.M, ps.thr_dprime, st));
         ++tm.launches;
     }
     PrepGlobals hq{}, hc{};
@@ -518,8 +521,10 @@ int run_plain(const Problem& pb, knn_stats* stats, cudaStream_t st) {
     KNN_TRY(prep_and_check(pb, P_FP32, L, st, stats, tm));
     KNN_CK(cudaMemsetAsync(L.counters, 0, sizeof(RerankCounters), st));
     KNN_TRY(ev.rec(1, st));
-    KNN_TRY(plain_pipeline(pb, pb.Q, pb.M, nullptr, pb.graph ? 0 : -1, L.ps.cnorm2, L.ps.E, L.ps.thr_dprime,
-                           pb.out_idx, pb.out_dist, L.row_status, B, L.counters, st, tm));
+    // a bounding threshold only saves work in the fused sweep; the plain form runs without it
+    KNN_TRY(plain_pipeline(pb, pb.Q, pb.M, nullptr, pb.graph ? 0 : -1, L.ps.cnorm2, L.ps.E,
+                           pb.thr_bound ? nullptr : L.ps.thr_dprime, pb.out_idx, pb.out_dist, L.row_status, B,
+                           L.counters, st, tm));
     KNN_TRY(ev.rec(2, st));
     KNN_TRY(ev.rec(3, st));
     RerankCounters hc{};
@@ -873,6 +878,7 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     fp.cnorm2 = L.ps.cnorm2;
     fp.E = L.ps.E;
     fp.thr = L.ps.thr_dprime;
+    fp.thr_bound = pb.thr_bound ? 1 : 0;
     fp.q_inv_scale = L.ps.qscale;
     fp.c_inv_scale = L.ps.cscale;
     fp.self_offset = pb.graph ? 0 : -1;
@@ -1327,6 +1333,12 @@ int stream_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
     KNN_TRY(cb.take(static_cast<size_t>(M) * k, &run_f32));
     KNN_TRY(cb.take(static_cast<size_t>(M) * kc_max, &cidx));
     KNN_TRY(cb.take(static_cast<size_t>(M) * kc_max, &cdist));
+    // from the second chunk on, each query's running k-th distance bounds the chunk's search
+    // (KNN_STREAM_BOUND=0: every chunk searched without it)
+    const char* bound_env = std::getenv("KNN_STREAM_BOUND");
+    const bool bound_on = !(bound_env && bound_env[0] == '0');
+    float* thr_run = nullptr;
+    if (bound_on) KNN_TRY(cb.take(static_cast<size_t>(M), &thr_run));
     struct StreamEvents {
         cudaStream_t cs = nullptr;
         cudaEvent_t copied[2] = {nullptr, nullptr}, merged[2] = {nullptr, nullptr};
@@ -1380,6 +1392,12 @@ int stream_impl(const float* Q, int64_t M, const float* C, int64_t N, int32_t d,
         pb.precision = opt.precision;
         pb.fused = opt.fused;
         pb.flags = opt.flags & ~KNN_FLAG_TIMING;
+        if (bound_on && ci > 0) {
+            KNN_CK(launch_stream_bound(run_d64, M, k, thr_run, st));
+            pb.thr = thr_run;
+            pb.thr_bound = true;
+            ++launches;
+        }
         knn_stats cs_stats{};
         KNN_TRY(run_problem(pb, &cs_stats, st));
         StreamMergeParams mp{};

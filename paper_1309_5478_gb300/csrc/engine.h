@@ -60,6 +60,10 @@ struct Problem {
     int32_t d, k, m;
     bool graph;           // k-NN graph: Q == C, row i excludes column i
     const float* thr;     // optional per-row squared-distance thresholds (device), M entries
+    // thr bounds the answer instead of guessing it (the out-of-core search's running k-th
+    // distance): a point farther than thr[i] is not wanted, a row may keep fewer than k points,
+    // and its answer is exact among the points at or below thr[i]
+    bool thr_bound = false;
     int32_t* out_idx;     // M x k
     float* out_dist;      // M x k
     int64_t slab_bytes;   // distance-matrix slab budget (0 = default)
@@ -105,6 +109,11 @@ int pick_cap(int k, int km);
 
 cudaError_t launch_select_ex(const SelectParams& p, int64_t self_offset, bool check_nan, cudaStream_t st);
 cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, int64_t M, float* out, cudaStream_t st);
+// Bounding thresholds (squared distances) to the d' scale of the approximate values: every point
+// whose exact squared distance is at most thr[i] has an approximate value at most out[i] (the
+// row's bound E[i] and the FP32 roundings of |q|^2 added); non-finite or negative entries: none.
+cudaError_t launch_bound_to_dprime(const float* thr, const float* qnorm2, const float* E, int64_t M, int32_t d,
+                                   float* out, cudaStream_t st);
 cudaError_t launch_gather_rows(const float* Q, int32_t d, const int32_t* rows, int32_t n, const float* E,
                                const float* thr, float* Qs, float* Es, float* Ts, cudaStream_t st);
 // Gathers rows of a reduced-precision operand (row_bytes a multiple of 16) and, when

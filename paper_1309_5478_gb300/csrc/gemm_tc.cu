@@ -1144,7 +1144,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // k survivors is a miss outright
                 if (p.thr) {
                     const float t = p.thr[grow];
-                    if (t == t && t < F_INF) fl |= ROW_TRUNCATED | (c0 + c1 < p.k ? ROW_THRESHOLD_MISS : 0u);
+                    if (t == t && t < F_INF) {
+                        if (params.thr_bound) {
+                            // a bound, not a guess: fewer than k keys is no miss, and a list whose
+                            // threshold never fell below the bound holds every key at or below it
+                            fl |= ROW_TRUNCATED | (rs.tau[row_in_block] >= key_ceiling(t) ? ROW_BOUNDED : 0u);
+                        } else {
+                            fl |= ROW_TRUNCATED | (c0 + c1 < p.k ? ROW_THRESHOLD_MISS : 0u);
+                        }
+                    }
                 }
                 uint64_t bnd = rs.tau[row_in_block];
                 if (sym_item) {

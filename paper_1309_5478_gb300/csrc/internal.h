@@ -29,6 +29,8 @@ enum RowFlag : uint32_t {
     ROW_SPECULATIVE = 8u,     // a speculative threshold was used: the band must be checked against the bound
     ROW_RAW_LIST = 16u,       // the list holds every key <= bound, not yet reduced to the band, in two
                               // segments: count = front | back << 16, the back filled from cand[cap - 1] down
+    ROW_BOUNDED = 32u,        // a bounding threshold (Problem::thr_bound) was supplied and the list holds
+                              // every key at or below it: exact among the points within the bound
 };
 
 enum RowStatus : uint32_t {
@@ -250,6 +252,9 @@ struct StreamMergeParams {
 };
 cudaError_t launch_stream_init(int64_t n, int32_t* idx, double* d64, float* f32, cudaStream_t st);
 cudaError_t launch_stream_merge(const StreamMergeParams& p, cudaStream_t st);
+// thr[i] = the running k-th FP64 distance of query i rounded up to FP32 (+inf while fewer than k
+// points have been merged): the bound for the next chunk's search.
+cudaError_t launch_stream_bound(const double* run_d64, int64_t M, int32_t k, float* thr, cudaStream_t st);
 
 // Exact FP64 answer for a list of rows (last-resort path; slow, used for rows no other path certifies).
 cudaError_t launch_exact_rows_fp64(const float* Q, const float* C, int64_t N, int32_t d, int32_t k,

@@ -387,6 +387,29 @@ __global__ void thr_kernel(const float* __restrict__ thr, const float* __restric
     out[i] = (t == t && t >= 0.f && t < F_INF) ? t - qnorm2[i] : F_INF;
 }
 
+// A bounding threshold t (squared distance) in the scale of the approximate values: a point with
+// exact squared distance d2 <= t has exact d' = d2 - |q|^2 <= t - |q|^2 and approximate value at
+// most that plus E. |q|^2 comes from the prep pass (an FP32 FMA chain per lane, then a five-level
+// warp sum: relative error below (d / 32 + 6) 2^-24), so less than qnorm2 is subtracted by a
+// margin of that size; the sum is formed in FP64 and rounded up to FP32.
+__global__ void bound_kernel(const float* __restrict__ thr, const float* __restrict__ qnorm2,
+                             const float* __restrict__ E, int64_t M, int32_t d, float* __restrict__ out) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const float t = thr[i];
+    if (!(t == t && t >= 0.f && t < F_INF)) {
+        out[i] = F_INF;
+        return;
+    }
+    const double g = (static_cast<double>(d) / 32.0 + 8.0) * 0x1p-24;
+    const double q2 = static_cast<double>(qnorm2[i]);
+    const double e = E ? static_cast<double>(E[i]) : 0.0;
+    const double v = static_cast<double>(t) * (1.0 + 0x1p-40) - q2 * (1.0 - g) + e * (1.0 + 0x1p-10);
+    float f = static_cast<float>(v);
+    if (static_cast<double>(f) < v) f = nextafterf(f, F_INF);
+    out[i] = f;
+}
+
 __global__ void gather_rows_kernel(const float* __restrict__ Q, int32_t d, const int32_t* __restrict__ rows,
                                    int32_t n, const float* __restrict__ E, const float* __restrict__ thr,
                                    float* __restrict__ Qs, float* __restrict__ Es, float* __restrict__ Ts) {
@@ -453,6 +476,13 @@ cudaError_t launch_threshold_to_dprime(const float* thr, const float* qnorm2, in
                                        cudaStream_t st) {
     if (M <= 0) return cudaSuccess;
     thr_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, st>>>(thr, qnorm2, M, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bound_to_dprime(const float* thr, const float* qnorm2, const float* E, int64_t M, int32_t d,
+                                   float* out, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    bound_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, st>>>(thr, qnorm2, E, M, d, out);
     return cudaGetLastError();
 }
 

@@ -468,8 +468,11 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         }
     }
     const bool truncated = (flags & ROW_TRUNCATED) || spec_cut;
-    bool certified = kk == k && !(flags & ROW_SELECT_ERROR) && !giant_tie && !lost;
-    if (certified && truncated && !exact) {
+    // a list complete up to a bounding threshold answers exactly among the points within it,
+    // with fewer than k of them when the bound holds fewer
+    const bool bounded = (flags & ROW_BOUNDED) != 0u;
+    bool certified = (kk == k || bounded) && !(flags & ROW_SELECT_ERROR) && !giant_tie && !lost;
+    if (certified && truncated && !exact && !bounded) {
         // every left-out point has d' >= value(bound), so d2 >= value(bound) + |q|^2 - E
         double qn2d = 0.0;
         for (int t = static_cast<int>(lane); t < d; t += 32) qn2d = fma((double)q[t], (double)q[t], qn2d);

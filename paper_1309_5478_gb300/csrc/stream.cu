@@ -86,6 +86,19 @@ __global__ void __launch_bounds__(MG_THREADS) stream_merge_kernel(StreamMergePar
     }
 }
 
+// A later chunk's point enters query i's answer only when its distance is below the running
+// k-th (one at the same distance has a higher index and loses the tie), so the running k-th,
+// rounded up, bounds what the next chunk's search has to find.
+__global__ void stream_bound_kernel(const double* __restrict__ run_d64, int64_t M, int32_t k,
+                                    float* __restrict__ thr) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double v = run_d64[i * k + k - 1];
+    float f = static_cast<float>(v);
+    if (static_cast<double>(f) < v) f = nextafterf(f, __int_as_float(0x7f800000));
+    thr[i] = f;
+}
+
 __global__ void stream_init_kernel(int64_t n, int32_t* idx, double* d64, float* f32) {
     for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -101,6 +114,12 @@ cudaError_t launch_stream_init(int64_t n, int32_t* idx, double* d64, float* f32,
     if (n <= 0) return cudaSuccess;
     const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
     stream_init_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(n, idx, d64, f32);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_bound(const double* run_d64, int64_t M, int32_t k, float* thr, cudaStream_t st) {
+    if (M <= 0) return cudaSuccess;
+    stream_bound_kernel<<<static_cast<unsigned>((M + 255) / 256), 256, 0, st>>>(run_d64, M, k, thr);
     return cudaGetLastError();
 }
 

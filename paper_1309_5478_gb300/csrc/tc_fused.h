@@ -46,6 +46,8 @@ struct FusedParams {
     const float* cnorm2;       // |c_j|^2 from the FP32 points, padded with NaN to a multiple of 256
     const float* E;            // per-row bound on |approximate - exact| of d'
     const float* thr;          // per-row d' threshold or nullptr
+    int32_t thr_bound;         // 1: thr bounds the answer (rows within it are kept complete, fewer than k
+                               // allowed: ROW_BOUNDED) instead of guessing it (fewer than k is a miss)
     const float* q_inv_scale;  // FP8: 1 / per-row scale of the queries
     const float* c_inv_scale;  // FP8: same for the corpus (padded like cnorm2)
     int64_t self_offset;       // >= 0: row i excludes column i + self_offset

@@ -62,3 +62,41 @@ def test_bad_chunk_rows():
     C = inputs.integer_lattice(n=100, d=4, seed=86)
     with pytest.raises(kb.KnnError):
         kb.knn_search_streamed(dev(C[:5]), C, 3, chunk_rows=-1)
+
+
+def test_later_chunks_beyond_the_bound():
+    # the first chunk holds every query's neighbours, the later chunks lie far away: from the
+    # second chunk on the running k-th distance bounds the search, the later chunks' rows keep no
+    # point within it, and the answer is the first chunk's
+    rng = np.random.default_rng(87)
+    near = rng.standard_normal((3000, 48)).astype(np.float32)
+    far = (rng.standard_normal((9000, 48)) + 40.0).astype(np.float32)
+    C = np.concatenate([near, far])
+    Q = rng.standard_normal((300, 48)).astype(np.float32)
+    si, sd, st = kb.knn_search_streamed(dev(Q), np.ascontiguousarray(C), 25, chunk_rows=3000, return_stats=True)
+    si = si.cpu().numpy()
+    assert st["rows_fallback"] == 0
+    assert si.max() < 3000
+    rows = inputs.sample_rows(len(Q), 40, seed=88)
+    ref_idx, _ = oracle.knn(Q, C, 25, rows=rows)
+    assert np.array_equal(si[rows], ref_idx)
+
+
+@pytest.mark.parametrize("data", ["ties", "float"])
+def test_bound_on_and_off_identical(monkeypatch, data):
+    if data == "ties":
+        C = inputs.integer_lattice(n=5000, d=8, lo=-2, hi=2, seed=89)
+        Q = inputs.integer_lattice(n=150, d=8, lo=-2, hi=2, seed=90)
+    else:
+        C = inputs.gaussian_mixture(n=24000, d=96, components=12, seed=91)
+        Q = inputs.gaussian_mixture(n=180, d=96, components=6, seed=92)
+    out = []
+    for b in ("1", "0"):
+        monkeypatch.setenv("KNN_STREAM_BOUND", b)
+        si, sd = kb.knn_search_streamed(dev(Q), np.ascontiguousarray(C), 20, chunk_rows=3001)
+        out.append((si.cpu().numpy(), sd.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    rows = inputs.sample_rows(len(Q), 30, seed=93)
+    ref_idx, ref_dist = oracle.knn(Q, C, 20, rows=rows)
+    if data == "ties":
+        assert np.array_equal(out[0][0][rows], ref_idx)
