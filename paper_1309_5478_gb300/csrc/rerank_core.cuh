@@ -5,13 +5,13 @@
 // ranking values d'_ij = |c_j|^2 - 2 q_i.c_j (Methods, "Distance calculation").
 // Here every candidate's squared distance is recomputed in the direct difference
 // form sum_t (q_t - c_t)^2, which has no cancellation:
-//   - 8, 16 or 32 lanes share a candidate (by dimension); each lane adds its four
-//     products of a 16-byte group with FMAs and folds the group sum into a (sum, error)
+//   - 8, 16 or 32 lanes share a candidate (by dimension); each lane adds the eight
+//     products of two 16-byte pieces with FMAs and folds that sum into a (sum, error)
 //     pair with Knuth's TwoSum, then rounds its pair to one float, and the lanes' floats
 //     are summed by a shuffle tree. Every term is non-negative, so each rounding adds at
 //     most one unit of the total: the relative error is at most 2 units in the last place
-//     for the rounded differences, 4 for the group sums, 1 for a lane's pair and 5 for
-//     the tree over 32 lanes (3 over 8), 12 in all: below 2^-20.
+//     for the rounded differences, 8 for the sums of eight products, 1 for a lane's pair
+//     and 5 for the tree over 32 lanes (3 over 8), 16 in all: at most 2^-20.
 //   - candidates are taken in ascending approximate order. Once the first k are exact,
 //     the largest of them bounds the exact k-th distance of the row from above; a
 //     candidate whose approximate value is more than E_i above that bound (with
@@ -56,6 +56,25 @@ enum RerankCount : int {
     RC_ROWS,       // rows re-ranked
     RC_COUNT
 };
+
+// The squares of two 16-byte pieces (eight differences, one rounding each) summed by a
+// multiply and seven FMAs, then added to the lane's (sum, error) pair by TwoSum.
+__device__ __forceinline__ void group_sum8(float4 q0, float4 c0, float4 q1, float4 c1, float& s, float& e) {
+    const float d0 = q0.x - c0.x, d1 = q0.y - c0.y, d2 = q0.z - c0.z, d3 = q0.w - c0.w;
+    const float d4 = q1.x - c1.x, d5 = q1.y - c1.y, d6 = q1.z - c1.z, d7 = q1.w - c1.w;
+    float g = d0 * d0;
+    g = fmaf(d1, d1, g);
+    g = fmaf(d2, d2, g);
+    g = fmaf(d3, d3, g);
+    g = fmaf(d4, d4, g);
+    g = fmaf(d5, d5, g);
+    g = fmaf(d6, d6, g);
+    g = fmaf(d7, d7, g);
+    float t, err;
+    two_sum(s, g, t, err);
+    s = t;
+    e += err;
+}
 
 __device__ __forceinline__ void group_sum(float4 q, float4 c, float& s, float& e) {
     const float d0 = q.x - c.x, d1 = q.y - c.y, d2 = q.z - c.z, d3 = q.w - c.w;
@@ -118,14 +137,20 @@ __device__ __forceinline__ void sqdist_multi(const float* __restrict__ q, const 
     float s[NC], e[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) s[i] = e[i] = 0.f;
-#pragma unroll 2
-    for (int t = static_cast<int>(lane) * 4; t < d; t += 128) {
-        const float4 a = load4(q, t, d, VEC);
-        float4 b[NC];
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int t = static_cast<int>(lane) * 4; t < d; t += 256) {
+        const bool two = t + 128 < d;
+        const float4 a0 = load4(q, t, d, VEC);
+        const float4 a1 = two ? load4(q, t + 128, d, VEC) : z;
+        float4 b0[NC], b1[NC];
 #pragma unroll
-        for (int i = 0; i < NC; ++i) b[i] = load4(c[i], t, d, VEC);
+        for (int i = 0; i < NC; ++i) {
+            b0[i] = load4(c[i], t, d, VEC);
+            b1[i] = two ? load4(c[i], t + 128, d, VEC) : z;
+        }
 #pragma unroll
-        for (int i = 0; i < NC; ++i) group_sum(a, b[i], s[i], e[i]);
+        for (int i = 0; i < NC; ++i) group_sum8(a0, b0[i], a1, b1[i], s[i], e[i]);
     }
 #pragma unroll
     for (int i = 0; i < NC; ++i) r[i] = group_fold_sum<32>(s[i], e[i]);
@@ -237,14 +262,20 @@ __device__ __forceinline__ void exact_keys_g(const RerankParams& p, const float*
         float s[NC], e[NC];
 #pragma unroll
         for (int i = 0; i < NC; ++i) s[i] = e[i] = 0.f;
-#pragma unroll 2
-        for (int t = gl * 4; t < d; t += 4 * G) {
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+        for (int t = gl * 4; t < d; t += 8 * G) {
+            const bool two = t + 4 * G < d;
             const float4 qa = load4(q, t, d, VEC);
+            const float4 qb = two ? load4(q, t + 4 * G, d, VEC) : z;
 #pragma unroll
             for (int i = 0; i < NC; ++i) {
-                float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (live[i]) b = load4(cp[i], t, d, VEC);
-                group_sum(qa, b, s[i], e[i]);
+                float4 b0 = z, b1 = z;
+                if (live[i]) {
+                    b0 = load4(cp[i], t, d, VEC);
+                    if (two) b1 = load4(cp[i], t + 4 * G, d, VEC);
+                }
+                group_sum8(qa, b0, qb, b1, s[i], e[i]);
             }
         }
         float r[NC];

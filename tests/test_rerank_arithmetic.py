@@ -1,10 +1,11 @@
 """The exact re-rank's FP32 distance arithmetic, replayed on the CPU (no GPU needed).
 
 The re-rank computes sum_t (q_t - c_t)^2 in FP32 with a fixed order: lanes of a group of
-G (8, 16 or 32) take 16-byte pieces of the rows in turn; each piece's four squares are
-summed with a multiply and three fused multiply-adds, the piece sums are accumulated per
-lane with TwoSum into a (sum, error) pair, each lane rounds its pair to one float, and the
-lanes' floats are summed by an xor-shuffle tree. The near-tie rule (FP32 distances within
+G (8, 16 or 32) take 16-byte pieces of the rows in turn, two at a time (pieces t and t + 4G);
+the eight squares of a pair of pieces are summed with a multiply and seven fused
+multiply-adds, those sums are accumulated per lane with TwoSum into a (sum, error) pair,
+each lane rounds its pair to one float, and the lanes' floats are summed by an xor-shuffle
+tree. The near-tie rule (FP32 distances within
 2^-19 of each other are ordered in FP64) and the early stop need this to be within 2^-20
 of the exact distance; these tests replay the same operations with FP32 rounding after
 every step and check that bound against FP64 on inputs chosen to stress it.
@@ -38,12 +39,12 @@ def replay(q: np.ndarray, c: np.ndarray, G: int) -> np.float32:
     for gl in range(G):
         s = f32(0.0)
         e = f32(0.0)
-        for t in range(gl * 4, d, 4 * G):
-            d0, d1, d2, d3 = (f32(qp[t + i] - cp[t + i]) for i in range(4))
-            g = f32(d0 * d0)
-            g = _fma(d1, d1, g)
-            g = _fma(d2, d2, g)
-            g = _fma(d3, d3, g)
+        for t in range(gl * 4, d, 8 * G):
+            pos = [t + i for i in range(4)] + [t + 4 * G + i for i in range(4)]
+            diffs = [f32(qp[p] - cp[p]) if p < len(qp) else f32(0.0) for p in pos]
+            g = f32(diffs[0] * diffs[0])
+            for x in diffs[1:]:
+                g = _fma(x, x, g)
             s, err = _two_sum(s, g)
             e = f32(e + err)
         lane_vals.append(f32(s + e))
