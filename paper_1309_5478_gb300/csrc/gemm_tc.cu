@@ -49,7 +49,6 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK_BYTES = 128;  // one 128-byte swizzle row per stage: 64 BF16 or 128 FP8 values
-constexpr int TC_STAGES = 4;
 constexpr int TC_THREADS = 384;  // producer, MMA issuer, 8 epilogue warps, 2 re-rank warps
 constexpr int A_BYTES = TC_BM * TC_BK_BYTES;  // 16 KB
 constexpr int B_BYTES = TC_BN * TC_BK_BYTES;  // 32 KB
@@ -171,11 +170,6 @@ __device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     tmem_ld32_issue(taddr, r);
     tmem_ld_wait();
-}
-
-// Largest value a key <= tau can carry (+inf for the open threshold).
-__device__ __forceinline__ float tau_value(uint64_t tau) {
-    return (tau >> 32) == 0xffffffffull ? F_INF : key_val(tau);
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {

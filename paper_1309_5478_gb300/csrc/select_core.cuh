@@ -454,7 +454,6 @@ __device__ __forceinline__ bool two_ranks_sampled(const uint32_t* a, uint32_t* b
         if (static_cast<int>(lane) >= o) incl += y;
     }
     const uint32_t excl = incl - h;
-    const uint32_t h32 = hist[32];
     const uint32_t total31 = __shfl_sync(0xffffffffu, incl, 31);
     // 4. each rank: its bucket, the bucket's members, then an exact small select
     uint32_t out[2];
@@ -463,17 +462,15 @@ __device__ __forceinline__ bool two_ranks_sampled(const uint32_t* a, uint32_t* b
     for (int q = 0; q < 2; ++q) {
         const int r = rr[q];
         int bkt;
-        uint32_t base_cnt, cnt;
+        uint32_t base_cnt;
         if (static_cast<uint32_t>(r) >= total31) {
             bkt = 32;
             base_cnt = total31;
-            cnt = h32;
         } else {
             const uint32_t hit = __ballot_sync(0xffffffffu, excl <= static_cast<uint32_t>(r) &&
                                                                  static_cast<uint32_t>(r) < incl);
             bkt = __ffs(hit) - 1;
             base_cnt = __shfl_sync(0xffffffffu, excl, bkt);
-            cnt = __shfl_sync(0xffffffffu, h, bkt);
         }
         // bucket bounds: [pivot bkt-1, pivot bkt)
         const uint32_t lo_v = bkt > 0 ? __shfl_sync(0xffffffffu, piv, bkt - 1) : 0u;
@@ -498,7 +495,6 @@ __device__ __forceinline__ bool two_ranks_sampled(const uint32_t* a, uint32_t* b
         } else {
             return false;  // a crowded bucket (ties) and no auxiliary array: caller takes the exact path
         }
-        (void)cnt;
         __syncwarp();
     }
     v1 = out[0];
