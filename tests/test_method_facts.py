@@ -2,6 +2,10 @@
 
 - Out-of-core search: the k smallest of the union of every chunk's k smallest (by distance,
   then index) are the k smallest of the whole corpus.
+- Out-of-core running bound: with each chunk's search restricted to the points at or below the
+  running k-th distance (and every chunk's answer merged as before), the answer is unchanged.
+- The bound's conversion to the approximate values' scale (`bound_kernel`): with |q|^2 summed
+  in FP32 as the prep pass sums it, t - exact |q|^2 <= the converted bound - E for every t.
 - Similarity certificate: for unit rows rounded to FP32 from FP64 means and norms,
   |d2(u_i, u_j) - (2 - 2 s_ij)| <= eta(d) = 9 2^-24 + (4 d + 64) 2^-53, with s_ij the FP64
   similarity from the same means and norms.
@@ -62,3 +66,65 @@ def test_similarity_certificate_bound(centered, d, kind):
     d2 = sq[:, None] + sq[None, :] - 2.0 * (U64 @ U64.T)  # exact to ~1e-16 for these sizes
     gap = np.abs(d2 - (2.0 - 2.0 * s))
     assert gap.max() <= eta(d), (gap.max(), eta(d))
+
+
+@pytest.mark.parametrize("chunk", [7, 100, 333])
+def test_running_bound_keeps_the_answer(chunk):
+    # a later chunk only contributes points strictly below the running k-th distance (one at
+    # the same distance has a higher index and loses the tie), so searching it among the points
+    # at or below that distance (fewer than k of them allowed) changes nothing
+    C = inputs.integer_lattice(n=1000, d=5, lo=-2, hi=2, seed=93)  # many exact ties
+    Q = inputs.integer_lattice(n=30, d=5, lo=-2, hi=2, seed=94)
+    k = 12
+    ref_idx, ref_dist = oracle.knn(Q, C, k)
+    run = [[] for _ in range(len(Q))]
+    for c0 in range(0, len(C), chunk):
+        Cc = C[c0:c0 + chunk]
+        D = ((Q[:, None, :].astype(np.float64) - Cc[None, :, :]) ** 2).sum(-1)
+        for r in range(len(Q)):
+            bound = run[r][-1][0] if len(run[r]) == k else np.inf
+            within = [(D[r, j], c0 + j) for j in range(len(Cc)) if D[r, j] <= bound]
+            run[r] = sorted(run[r] + sorted(within)[:k])[:k]
+    for r in range(len(Q)):
+        assert [j for _, j in run[r]] == list(ref_idx[r])
+        assert [d for d, _ in run[r]] == list(ref_dist[r])
+
+
+def _prep_norm2(x):
+    # |x|^2 as the prep pass forms it: each of 32 lanes an FP32 FMA chain over its stride, then
+    # a five-level tree
+    f32 = np.float32
+    lanes = []
+    for l in range(32):
+        s = f32(0.0)
+        for t in range(l, len(x), 32):
+            s = f32(np.float64(x[t]) * np.float64(x[t]) + np.float64(s))
+        lanes.append(s)
+    o = 16
+    while o:
+        lanes = [f32(lanes[i] + lanes[i ^ o]) for i in range(32)]
+        o //= 2
+    return lanes[0]
+
+
+def _bound_to_dprime(t, qn2, e, d):
+    # the conversion of bound_kernel: FP64, then rounded up to FP32
+    g = (d / 32.0 + 8.0) * 2.0 ** -24
+    v = float(t) * (1.0 + 2.0 ** -40) - float(qn2) * (1.0 - g) + float(e) * (1.0 + 2.0 ** -10)
+    f = np.float32(v)
+    if float(f) < v:
+        f = np.nextafter(f, np.float32(np.inf))
+    return float(f)
+
+
+@pytest.mark.parametrize("d", [3, 64, 256, 1024, 4096])
+def test_bound_conversion_covers_the_exact_norm(d):
+    rng = np.random.default_rng(95 + d)
+    for scale in (1e-3, 1.0, 37.0):
+        for _ in range(20):
+            q = (rng.standard_normal(d) * scale).astype(np.float32)
+            exact = float(np.sum(q.astype(np.float64) ** 2))
+            qn2 = _prep_norm2(q)
+            t = np.float32(exact * rng.uniform(0.5, 3.0))
+            e = np.float32(rng.uniform(0.0, 1e-3) * exact)
+            assert _bound_to_dprime(t, qn2, e, d) - float(e) >= float(t) - exact
