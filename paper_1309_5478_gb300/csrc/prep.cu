@@ -296,13 +296,23 @@ __global__ void __launch_bounds__(256) prep_batched_kernel(const BatchDev* __res
         const int64_t stop = seg_end < r1 ? seg_end : r1;
         const BatchDev& b = probs[sg.problem];
         RowStatsAcc acc;
+        // rows of four-value groups from 16-byte aligned bases take the 16-byte loads (the
+        // reduced-precision copies are 256-byte aligned with rows of a multiple of 64 values)
         if (sg.which == 0) {
-            for (; row < stop; ++row)
-                prep_row<P>(b.C, row - sg.row0, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, acc);
+            for (; row < stop; ++row) {
+                if (b.vec)
+                    prep_row_vec<P>(b.C, row - sg.row0, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, acc);
+                else
+                    prep_row<P>(b.C, row - sg.row0, b.d, b.cnorm2, b.cres, b.ctn, b.xc, b.d_pad, b.cscale, acc);
+            }
             acc.flush(b.gc, P != P_FP32);
         } else {
-            for (; row < stop; ++row)
-                prep_row<P>(b.Q, row - sg.row0, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, acc);
+            for (; row < stop; ++row) {
+                if (b.vec)
+                    prep_row_vec<P>(b.Q, row - sg.row0, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, acc);
+                else
+                    prep_row<P>(b.Q, row - sg.row0, b.d, b.qnorm2, b.qres, b.qtn, b.xq, b.d_pad, b.qscale, acc);
+            }
             acc.flush(b.gq, P != P_FP32);
         }
     }
