@@ -93,3 +93,20 @@ def test_symmetric_inbox_overflow_is_caught(symmetric):
     ref_idx, ref_dist = oracle.knng(X, 8, rows=rows)
     check_float(X, X, rows, i[rows], d[rows], ref_idx, ref_dist, exclude_self=True)
 
+
+
+def test_headline_graph_full_size_sampled_rows():
+    # the bench's workload and launch configuration: 262144 unit directions in d = 1024 with 1%
+    # exact duplicates, k = 64, the default form (symmetric fused BF16 with the band probe);
+    # sampled rows, duplicate targets among them, against the FP64 oracle
+    X, targets, sources = inputs.unit_directions_with_duplicates(n=262144, d=1024)
+    i, d, st = kb.knng_build(dev(X), 64, return_stats=True)
+    torch.cuda.synchronize()
+    assert st["symmetric"] == 1 and st["rows_uncertified"] == 0
+    i, d = i.cpu().numpy(), d.cpu().numpy()
+    rows = np.unique(np.concatenate([targets[:8], sources[:8], inputs.sample_rows(len(X), 32, seed=96)]))
+    ref_idx, ref_dist = oracle.knng(X, 64, rows=rows)
+    check_float(X, X, rows, i[rows], d[rows], ref_idx, ref_dist, exclude_self=True)
+    # a duplicate pair is each other's nearest neighbour at distance 0
+    for t, s in zip(targets[:8], sources[:8]):
+        assert i[t, 0] == s and d[t, 0] == 0.0
