@@ -83,7 +83,8 @@ def parse():
     return ap.parse_args()
 
 
-SCHEDULE_NAMES = {0: "fused", 1: "plain-fp32", 2: "fused-no-speculation", 3: "fused-speculation"}
+SCHEDULE_NAMES = {0: "fused", 1: "plain-fp32", 2: "fused-no-speculation", 3: "fused-speculation",
+                  4: "fused-128-no-speculation", 5: "fused-128-speculation"}
 
 
 def autotune_table(path: str) -> dict:

@@ -34,20 +34,40 @@
 
 namespace knn {
 
-// Schedules a problem of a batch can take: the fused tensor-core form with speculative
-// thresholds in its sweep or without them (a choice of the select's work inside the GEMM
-// epilogue), or the plain FP32 form (SIMT GEMM slabs, unfused multi-select).
-// SCHED_FUSED leaves speculation to the size rule (from 16384 points on).
-enum Schedule : int { SCHED_FUSED = 0, SCHED_PLAIN = 1, SCHED_FUSED_NOSPEC = 2, SCHED_FUSED_SPEC = 3 };
-constexpr int TUNE_VERSION = 2;  // bumped when the schedule table or its timing changes
+// Schedules a problem of a batch can take: the fused tensor-core form on 128 x 256 tiles (one
+// CTA an SM) or on 128 x 128 tiles (two CTAs an SM: twice the epilogue warps per SM, for lists
+// of at most 512 keys), each with speculative thresholds in its sweep or without them (a
+// choice of the select's work inside the GEMM epilogue), or the plain FP32 form (SIMT GEMM
+// slabs, unfused multi-select). SCHED_FUSED leaves speculation to the size rule (from 16384
+// points on).
+enum Schedule : int {
+    SCHED_FUSED = 0,
+    SCHED_PLAIN = 1,
+    SCHED_FUSED_NOSPEC = 2,
+    SCHED_FUSED_SPEC = 3,
+    SCHED_FUSED_T128_NOSPEC = 4,
+    SCHED_FUSED_T128_SPEC = 5,
+};
+constexpr int SCHED_LAST = SCHED_FUSED_T128_SPEC;
+constexpr int TUNE_VERSION = 4;  // bumped when the schedule table or its timing changes
 
 bool is_fused(int sched) { return sched != SCHED_PLAIN; }
+// corpus columns of a fused schedule's tiles
+int tile_of(int sched) { return sched == SCHED_FUSED_T128_NOSPEC || sched == SCHED_FUSED_T128_SPEC ? 128 : 256; }
+// speculative thresholds: 1 on, 0 off, -1 by the size rule
+int spec_of(int sched) {
+    if (sched == SCHED_FUSED_SPEC || sched == SCHED_FUSED_T128_SPEC) return 1;
+    if (sched == SCHED_FUSED_NOSPEC || sched == SCHED_FUSED_T128_NOSPEC) return 0;
+    return -1;
+}
 
 const char* schedule_name(int sched) {
     switch (sched) {
         case SCHED_PLAIN: return "plain-fp32";
         case SCHED_FUSED_NOSPEC: return "fused-no-speculation";
         case SCHED_FUSED_SPEC: return "fused-speculation";
+        case SCHED_FUSED_T128_NOSPEC: return "fused-128-no-speculation";
+        case SCHED_FUSED_T128_SPEC: return "fused-128-speculation";
         default: return "fused";
     }
 }
@@ -109,7 +129,7 @@ void tune_load() {
             continue;
         }
         int v;
-        if (std::fscanf(f, " : %d", &v) == 1 && v >= SCHED_FUSED && v <= SCHED_FUSED_SPEC) entries[key] = v;
+        if (std::fscanf(f, " : %d", &v) == 1 && v >= SCHED_FUSED && v <= SCHED_LAST) entries[key] = v;
     }
     std::fclose(f);
     if (device == tune_device_tag()) g_tune = entries;
@@ -168,17 +188,32 @@ __global__ void synth_kernel(float* x, int64_t n, uint64_t seed) {
     }
 }
 
-// Times one schedule on a synthetic problem of p's shape (fewer query rows); ms per row.
+}  // namespace
+int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precision_req, ::knn_stats* stats,
+              cudaStream_t st);
+namespace {
+void drop_batch_graph(const std::vector<Problem>& probs, const std::vector<int>& sched, int prec);
+
+// Times one schedule on a synthetic problem of p's shape (at most 4096 query rows), as a batch
+// of copies of that problem (the path the schedule will run on) with enough row blocks to fill
+// every CTA slot of the GPU, so that schedules that share an SM between CTAs are timed as they
+// run inside a full batch; ms per row.
 int time_schedule(const Problem& p, int sched, float* ms_per_row) {
     const int64_t M = std::min<int64_t>(p.M, 4096);
+    int dev = 0, sms = 1;
+    KNN_CK(cudaGetDevice(&dev));
+    KNN_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t rb = (M + 127) / 128;
+    const int copies = static_cast<int>(std::max<int64_t>(1, (2 * static_cast<int64_t>(sms) + rb - 1) / rb));
     float *Q = nullptr, *C = nullptr, *od = nullptr;
     int32_t* oi = nullptr;
     cudaStream_t st = nullptr;
     KNN_CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const size_t out_elems = static_cast<size_t>(M) * p.k * copies;
     cudaError_t e = cudaMalloc(&Q, static_cast<size_t>(M) * p.d * 4);
     if (e == cudaSuccess) e = cudaMalloc(&C, static_cast<size_t>(p.N) * p.d * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&oi, static_cast<size_t>(M) * p.k * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&od, static_cast<size_t>(M) * p.k * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&oi, out_elems * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&od, out_elems * 4);
     int rc = KNN_OK;
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -192,20 +227,24 @@ int time_schedule(const Problem& p, int sched, float* ms_per_row) {
         q.M = M;
         q.graph = false;
         q.thr = nullptr;
-        q.out_idx = oi;
-        q.out_dist = od;
         q.flags = KNN_FLAG_NO_FALLBACK;
         q.precision = is_fused(sched) ? KNN_BF16 : KNN_FP32;
         q.fused = is_fused(sched) ? 1 : 0;
-        q.spec = sched == SCHED_FUSED_SPEC ? 1 : (sched == SCHED_FUSED_NOSPEC ? 0 : -1);
-        ::knn_stats s{};
+        q.spec = spec_of(sched);
+        q.sched = sched;
+        std::vector<Problem> batch(static_cast<size_t>(copies), q);
+        for (int c = 0; c < copies; ++c) {
+            batch[c].out_idx = oi + static_cast<size_t>(c) * M * p.k;
+            batch[c].out_dist = od + static_cast<size_t>(c) * M * p.k;
+        }
+        std::vector<int> status(batch.size(), KNN_OK);
         float best = 1e30f;
         for (int rep = 0; rep < 3 && rc == KNN_OK; ++rep) {
             cudaEvent_t a, b;
             cudaEventCreate(&a);
             cudaEventCreate(&b);
             cudaEventRecord(a, st);
-            rc = run_problem(q, &s, st);
+            rc = run_batch(batch, status, q.precision, nullptr, st);
             cudaEventRecord(b, st);
             cudaEventSynchronize(b);
             float t = 0.f;
@@ -214,17 +253,9 @@ int time_schedule(const Problem& p, int sched, float* ms_per_row) {
             cudaEventDestroy(a);
             cudaEventDestroy(b);
         }
-        // In a batch the fused kernel's row blocks share every SM with other problems'
-        // work items; alone, a problem of nrb row blocks occupies only nrb SMs. Charge the
-        // fused form for the share of the GPU it actually used.
-        if (is_fused(sched)) {
-            int dev = 0, sms = 1;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const double nrb = static_cast<double>((M + 127) / 128);
-            best *= static_cast<float>(std::min(1.0, nrb / sms));
-        }
-        *ms_per_row = best / static_cast<float>(M);
+        *ms_per_row = best / static_cast<float>(M * copies);
+        std::vector<int> scheds(batch.size(), sched);
+        drop_batch_graph(batch, scheds, P_BF16);
     }
     cudaStreamSynchronize(st);
     cudaFree(Q);
@@ -241,7 +272,17 @@ int choose_schedule(const Problem& p, int precision_req, bool* fused_capable) {
     const int km = static_cast<int>(std::min<int64_t>(p.k + p.m, p.N - (p.graph ? 1 : 0)));
     const int want = precision_req == KNN_FP8_E4M3 ? P_FP8 : P_BF16;
     *fused_capable = fused_available() && fused_stages(fused_cap(p.k, km), want) > 0 && p.fused != 0;
+    const bool t128 = *fused_capable && fused_stages(fused_cap(p.k, km), want, false, 128) > 0;
+    if (p.sched >= 0) {
+        // forced (the autotuner's timing runs): kept where the problem can take it
+        if (!is_fused(p.sched)) return SCHED_PLAIN;
+        if (!*fused_capable) return SCHED_PLAIN;
+        return tile_of(p.sched) == 128 && !t128 ? SCHED_FUSED : p.sched;
+    }
     if (!*fused_capable || precision_req == KNN_FP32) return SCHED_PLAIN;
+    // KNN_BATCH_TILE=128: every problem that can takes the 128-column tiles (tests, tuning)
+    if (const char* te = std::getenv("KNN_BATCH_TILE"); te && std::atoi(te) == 128 && t128)
+        return p.N >= 16384 ? SCHED_FUSED_T128_SPEC : SCHED_FUSED_T128_NOSPEC;
     if (p.fused == 1 || precision_req != KNN_AUTO) return SCHED_FUSED;
     const char* env = std::getenv("KNN_AUTOTUNE");
     if (env && env[0] == '0') return SCHED_FUSED;
@@ -254,8 +295,9 @@ int choose_schedule(const Problem& p, int precision_req, bool* fused_capable) {
     // sweep of a few tiles: below 512 points only the plain sweep is timed)
     int sched = SCHED_FUSED;
     float best = 1e30f;
-    for (int s : {SCHED_FUSED_SPEC, SCHED_FUSED_NOSPEC, SCHED_PLAIN}) {
-        if (s == SCHED_FUSED_SPEC && p.N < 512) continue;
+    for (int s : {SCHED_FUSED_SPEC, SCHED_FUSED_NOSPEC, SCHED_FUSED_T128_SPEC, SCHED_FUSED_T128_NOSPEC, SCHED_PLAIN}) {
+        if (spec_of(s) == 1 && p.N < 512) continue;
+        if (tile_of(s) == 128 && (!t128 || !is_fused(s))) continue;
         float t = 0.f;
         if (time_schedule(p, s, &t) == KNN_OK && t < best) {
             best = t;
@@ -333,9 +375,14 @@ struct BatchLayout {
     std::vector<FusedWork> work;
     int64_t prep_rows = 0, query_rows = 0, plain_prep_rows = 0, plain_query_rows = 0;
     int cap_max = 0, stages = 0, grid = 0;
-    // the fused work runs as two launches: problems whose lists hold at most 512 keys (the
-    // kernel variant with 16 keys a lane and four pipeline stages), then the longer lists
-    int n_short = 0, cap_short = 0, cap_long = 0;
+    // the fused work runs as up to three launches: problems on 128 x 256 tiles whose lists
+    // hold at most 512 keys (the kernel variant with 16 keys a lane and four pipeline stages),
+    // then the longer lists, then the problems on 128 x 128 tiles (two CTAs an SM)
+    struct Part {
+        int first = 0, count = 0, cap = 0, bn = 256;
+    };
+    Part parts[3];
+    int sms = 0;
     // device pointers
     BatchDev* d_dev = nullptr;
     FusedProblem* d_fprob = nullptr;
@@ -456,15 +503,20 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
         L.plain_query_rows += probs[i].M;
     }
     L.fprob.assign(L.fused_ids.size(), FusedProblem{});
-    L.cap_short = L.cap_long = 0;
-    for (int pass = 0; pass < 2; ++pass) {
+    L.sms = sms;
+    for (int pass = 0; pass < 3; ++pass) {
         const size_t first = L.work.size();
+        BatchLayout::Part& part = L.parts[pass];
+        part = BatchLayout::Part{};
+        part.first = static_cast<int>(first);
+        part.bn = pass == 2 ? 128 : 256;
         for (size_t f = 0; f < L.fused_ids.size(); ++f) {
             const int i = L.fused_ids[f];
             const Problem& p = probs[i];
             const int cap = L.dev[i].cap;
-            if ((cap <= 512) != (pass == 0)) continue;
-            (pass == 0 ? L.cap_short : L.cap_long) = std::max(pass == 0 ? L.cap_short : L.cap_long, cap);
+            const int bn = tile_of(sched[i]);
+            if (bn != part.bn || (bn == 256 && (cap <= 512) != (pass == 0))) continue;
+            part.cap = std::max(part.cap, cap);
             const int nrb = static_cast<int>((p.M + 127) / 128);
             for (int rb = 0; rb < nrb; ++rb) L.work.push_back({static_cast<int32_t>(f), rb});
         }
@@ -475,10 +527,17 @@ void layout_batch(const std::vector<Problem>& probs, const std::vector<int>& sch
                              const Problem& pb = probs[L.fused_ids[b.problem]];
                              return (pa.N + 255) / 256 * ((pa.d + 63) / 64) > (pb.N + 255) / 256 * ((pb.d + 63) / 64);
                          });
-        if (pass == 0) L.n_short = static_cast<int>(L.work.size());
+        part.count = static_cast<int>(L.work.size() - first);
     }
-    L.grid = static_cast<int>(std::max<size_t>(1, std::min<size_t>(static_cast<size_t>(sms), L.work.size())));
-    L.stages = L.fused_ids.empty() ? 0 : fused_stages(L.cap_max, prec);
+    // persistent CTAs of the widest launch (sizes the shrink scratch); stages: 0 when a part's
+    // lists do not fit
+    L.grid = 1;
+    L.stages = L.fused_ids.empty() ? 0 : (1 << 20);
+    for (const BatchLayout::Part& part : L.parts) {
+        if (part.count == 0) continue;
+        L.grid = std::max(L.grid, std::min(sms * (part.bn == 128 ? 2 : 1), part.count));
+        L.stages = std::min(L.stages, fused_stages(part.cap, prec, false, part.bn));
+    }
     L.d_dev = ar.take<BatchDev>(static_cast<size_t>(n));
     L.d_fprob = ar.take<FusedProblem>(std::max<size_t>(1, L.fprob.size()));
     L.d_prep_segs = ar.take<BatchSeg>(std::max<size_t>(1, L.prep_segs.size()));
@@ -513,20 +572,18 @@ int enqueue_batch(const std::vector<Problem>& probs, int prec, const BatchLayout
         KNN_CK(launch_bounds_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
                                      prec, st));
         KNN_CK(mark(1));
-        int sms = L.grid;
-        for (int part = 0; part < 2; ++part) {
-            const int first = part == 0 ? 0 : L.n_short;
-            const int count = part == 0 ? L.n_short : static_cast<int>(L.work.size()) - L.n_short;
-            if (count <= 0) continue;
+        for (const BatchLayout::Part& part : L.parts) {
+            if (part.count <= 0) continue;
             FusedParams fp{};
             fp.status = L.status;
             fp.scratch = L.scratch;
-            fp.cap_max = part == 0 ? L.cap_short : L.cap_long;
-            fp.stages = fused_stages(fp.cap_max, prec);
-            fp.n_items = count;
+            fp.cap_max = part.cap;
+            fp.stages = fused_stages(part.cap, prec, false, part.bn);
+            fp.n_items = part.count;
             fp.problems = L.d_fprob;
-            fp.work = L.d_work + first;
-            KNN_CK(launch_fused_batched(fp, prec, std::min(sms, count), st));
+            fp.work = L.d_work + part.first;
+            const int ctas = L.sms * (part.bn == 128 ? 2 : 1);
+            KNN_CK(launch_fused_batched(fp, prec, std::min(ctas, part.count), st, part.bn));
         }
         KNN_CK(mark(2));
         KNN_CK(launch_rerank_batched(L.d_dev, L.d_query_segs, static_cast<int32_t>(L.query_segs.size()), L.query_rows,
@@ -608,6 +665,22 @@ std::string signature(const std::vector<Problem>& probs, const std::vector<int>&
     return s;
 }
 
+
+// Forgets a batch's cached graph (the autotuner's one-problem timing batches, whose buffers are
+// freed right after).
+void drop_batch_graph(const std::vector<Problem>& probs, const std::vector<int>& sched, int prec) {
+    const std::string sig = signature(probs, sched, prec);
+    std::lock_guard<std::mutex> lk(g_bws_mu);
+    auto it = g_graphs.find(sig);
+    if (it == g_graphs.end()) return;
+    if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+    for (auto e : it->second.marks)
+        if (e) cudaEventDestroy(e);
+    g_graphs.erase(it);
+    for (auto& kv : g_uploaded)
+        if (kv.second == sig) kv.second.clear();
+}
+
 }  // namespace
 
 // Runs the batch (device pointers only); per-problem statuses in status[]. Returns the
@@ -678,8 +751,8 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
             q.flags = b.flags;
             // speculation as the autotuner chose it, else from 16384 points on
             const int sc = sched[L.fused_ids[f]];
-            q.spec = sc == SCHED_FUSED_NOSPEC ? 0 : (sc == SCHED_FUSED_SPEC || b.N >= 16384 ? 1 : 0);
-            if (!encode_problem_maps(&q, b.xq, b.xc, prec))
+            q.spec = spec_of(sc) >= 0 ? spec_of(sc) : (b.N >= 16384 ? 1 : 0);
+            if (!encode_problem_maps(&q, b.xq, b.xc, prec, tile_of(sc)))
                 return set_error(KNN_EUNSUPPORTED, "tensor map encoding failed for problem %d", i);
         }
         if (cg.exec) {
@@ -821,7 +894,7 @@ int run_batch(std::vector<Problem>& probs, std::vector<int>& status, int precisi
         for (const Problem& p : probs) flops += 2.0 * double(p.M) * double(p.N) * double(p.d);
         stats->gemm_flops = flops;
         stats->kernel_launches =
-            1 + (L.fused_ids.empty() ? 0 : 2 + (L.n_short > 0) + (static_cast<int>(L.work.size()) > L.n_short) +
+            1 + (L.fused_ids.empty() ? 0 : 2 + (L.parts[0].count > 0) + (L.parts[1].count > 0) + (L.parts[2].count > 0) +
                                                 rerank_launches(L.cap_max)) +
             (L.plain_ids.empty() ? 0 : 2);
         for (int i : L.plain_ids) {

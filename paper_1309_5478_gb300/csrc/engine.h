@@ -71,6 +71,7 @@ struct Problem {
     int32_t fused;        // -1 auto, 0, 1
     int32_t flags;        // KNN_FLAG_*
     int32_t spec = -1;    // speculative thresholds in the fused sweep: -1 by the size rule, 0 off, 1 on
+    int32_t sched = -1;   // batched form: the schedule to take (the autotuner's timing runs), -1: chosen
 };
 
 struct PrepState {

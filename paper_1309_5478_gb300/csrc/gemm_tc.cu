@@ -49,11 +49,26 @@ namespace {
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK_BYTES = 128;  // one 128-byte swizzle row per stage: 64 BF16 or 128 FP8 values
-constexpr int TC_THREADS = 384;  // producer, MMA issuer, 8 epilogue warps, 2 re-rank warps
 constexpr int A_BYTES = TC_BM * TC_BK_BYTES;  // 16 KB
-constexpr int B_BYTES = TC_BN * TC_BK_BYTES;  // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr uint32_t TMEM_COLS = 512;
+
+// Tile configurations (corpus columns per tile BN):
+//   256: 128 x 256 tiles, two 256-column accumulators (all 512 TMEM columns), one CTA of
+//        12 warps an SM (producer, MMA issuer, 8 epilogue warps, 2 re-rank warps);
+//   128: 128 x 128 tiles, two 128-column accumulators (256 TMEM columns), 10 warps a CTA and
+//        two CTAs an SM, so 16 epilogue warps share an SM (batched launches only).
+template <int BN>
+struct Tile {
+    static constexpr int B_BYTES = BN * TC_BK_BYTES;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TMEM_COLS = 2u * BN;
+    static constexpr int THREADS = BN == 256 ? 384 : 320;
+    static constexpr int CTAS_PER_SM = BN == 256 ? 1 : 2;
+};
+constexpr int TC_THREADS = Tile<TC_BN>::THREADS;
+constexpr int STAGE_BYTES = Tile<TC_BN>::STAGE_BYTES;
+// dynamic shared memory a CTA may use: the SM's 228 KB less 1 KB reserved per CTA, shared by
+// the CTAs of an SM
+constexpr size_t smem_budget(int bn) { return bn == 256 ? 232448 : (233472 - 2 * 1024) / 2; }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -120,27 +135,27 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = 256.
-template <int P>
+// Instruction descriptor: FP32 accumulator, K-major A and B, M = 128, N = BN.
+template <int P, int BN>
 __host__ __device__ constexpr uint32_t idesc() {
     // bits 4-5 D format (1 = F32); 7-9 A format, 10-12 B format (kind::f16: 1 = BF16;
     // kind::f8f6f4: 0 = E4M3); 15/16 A/B major (0 = K); 17-22 N >> 3; 24-28 M >> 4.
     return (1u << 4) | ((P == P_BF16 ? 1u : 0u) << 7) | ((P == P_BF16 ? 1u : 0u) << 10) |
-           (static_cast<uint32_t>(TC_BN >> 3) << 17) | (static_cast<uint32_t>(TC_BM >> 4) << 24);
+           (static_cast<uint32_t>(BN >> 3) << 17) | (static_cast<uint32_t>(TC_BM >> 4) << 24);
 }
 
-template <int P>
+template <int P, int BN>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
     if constexpr (P == P_BF16) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc<P>()), "r"(accumulate));
+            "l"(a), "l"(b), "r"(idesc<P, BN>()), "r"(accumulate));
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc<P>()), "r"(accumulate));
+            "l"(a), "l"(b), "r"(idesc<P, BN>()), "r"(accumulate));
     }
 }
 
@@ -216,16 +231,18 @@ __host__ __device__ constexpr size_t epi_warp_bytes(int cap) {
 }
 constexpr size_t ROWSTATE_BYTES = 128 * (4 + 8 + 4 + 4);
 
-__host__ __device__ constexpr size_t cn_bytes(int precision) { return (precision == P_FP8 ? 2 : 1) * 2 * TC_BN * 4; }
+__host__ __device__ constexpr size_t cn_bytes(int precision, int bn = TC_BN) {
+    return static_cast<size_t>(precision == P_FP8 ? 2 : 1) * 2 * bn * 4;
+}
 
 // Re-rank warps' shared memory: a key buffer and an FP64 tie buffer each, and counters.
 constexpr size_t RR_BYTES = RR_WARPS * (static_cast<size_t>(RR_P + TIE_MAX) * 8 + RC_COUNT * 8);
 // mbarriers, TMEM address, abort flag, completion count, and the epilogue pairs' wait results
 constexpr size_t BAR_BYTES = 192;
 
-__host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision, bool rr) {
-    return 1024 /* alignment slack */ + static_cast<size_t>(stages) * STAGE_BYTES + EPI_WARPS * epi_warp_bytes(cap) +
-           cn_bytes(precision) + ROWSTATE_BYTES + BAR_BYTES + (rr ? RR_BYTES : 0);
+__host__ __device__ constexpr size_t tc_smem_bytes(int cap, int stages, int precision, bool rr, int bn = TC_BN) {
+    return 1024 /* alignment slack */ + static_cast<size_t>(stages) * (A_BYTES + bn * TC_BK_BYTES) +
+           EPI_WARPS * epi_warp_bytes(cap) + cn_bytes(precision, bn) + ROWSTATE_BYTES + BAR_BYTES + (rr ? RR_BYTES : 0);
 }
 
 __host__ __device__ constexpr size_t scratch_words_per_warp(int cap) {
@@ -268,7 +285,7 @@ __device__ __forceinline__ int item_rb(const FusedParams& p, int it) {
     return ((w & 1) && (w + 1) * g <= p.n_items) ? w * g + (g - 1 - b) : it;
 }
 
-template <bool BATCHED>
+template <bool BATCHED, int BN>
 __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                          int it) {
     Item im;
@@ -325,7 +342,7 @@ __device__ __forceinline__ Item get_item(const FusedParams& p, const CUtensorMap
         im.spec_d2 = F_INF;
         im.qnorm2 = nullptr;
     }
-    im.nct = static_cast<int>((im.N + TC_BN - 1) / TC_BN);
+    im.nct = static_cast<int>((im.N + BN - 1) / BN);
     im.t0 = (!BATCHED && p.sym) ? im.rb >> 1 : 0;
     im.nsw = im.nct - im.t0;
     return im;
@@ -796,8 +813,8 @@ __device__ __forceinline__ bool wait_epilogue(const volatile int* ep_done, int t
     return ok != 0;
 }
 
-template <int P, bool BATCHED, int KPL>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+template <int P, bool BATCHED, int KPL, int BN>
+__global__ void __launch_bounds__(Tile<BN>::THREADS, Tile<BN>::CTAS_PER_SM)
     fused_gemm_select_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                              const FusedParams params) {
     const FusedParams& p = params;
@@ -806,9 +823,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                                                            ~static_cast<uintptr_t>(1023));
     const int nst = p.stages;
     unsigned char* stage_base = smem;
-    unsigned char* epi_base = smem + nst * STAGE_BYTES;
-    float* cn_smem = reinterpret_cast<float*>(epi_base + EPI_WARPS * epi_warp_bytes(p.cap_max));  // [2][TC_BN] (+ scales)
-    unsigned char* rs_base = reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P);
+    constexpr int STAGE = Tile<BN>::STAGE_BYTES;
+    unsigned char* epi_base = smem + nst * STAGE;
+    float* cn_smem = reinterpret_cast<float*>(epi_base + EPI_WARPS * epi_warp_bytes(p.cap_max));  // [2][BN] (+ scales)
+    unsigned char* rs_base = reinterpret_cast<unsigned char*>(cn_smem) + cn_bytes(P, BN);
     RowState rs;
     rs.tau = reinterpret_cast<uint64_t*>(rs_base);
     rs.cnt = reinterpret_cast<uint16_t*>(rs.tau + 128);
@@ -830,7 +848,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = static_cast<int>(threadIdx.x / 32);
     const uint32_t lane = lane_id();
     const int n_items = p.n_items;
-    constexpr uint32_t CN_TX = static_cast<uint32_t>(cn_bytes(P) / 2);  // bytes staged per tile
+    constexpr uint32_t CN_TX = static_cast<uint32_t>(cn_bytes(P, BN) / 2);  // bytes staged per tile
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -848,7 +866,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                     "r"(TMEM_COLS)
+                     "r"(Tile<BN>::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -865,17 +883,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bool ok = true;
             const int kx = TC_BK_BYTES / (P == P_BF16 ? 2 : 1);
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-                const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
+                const Item im = get_item<BATCHED, BN>(p, &tmA, &tmB, it);
                 for (int ct = 0; ct < im.nsw && ok; ++ct) {
                     for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, wait_limit)) {
                             ok = false;
                             break;
                         }
-                        unsigned char* a = stage_base + s * STAGE_BYTES;
-                        mbar_expect_tx(&full[s], STAGE_BYTES);
+                        unsigned char* a = stage_base + s * STAGE;
+                        mbar_expect_tx(&full[s], STAGE);
                         tma_load_2d(a, im.tmA, &full[s], ks * kx, im.rb * TC_BM);
-                        tma_load_2d(a + A_BYTES, im.tmB, &full[s], ks * kx, tile_at(im, ct) * TC_BN);
+                        tma_load_2d(a + A_BYTES, im.tmB, &full[s], ks * kx, tile_at(im, ct) * BN);
                         if (++s == nst) {
                             s = 0;
                             ph ^= 1u;
@@ -916,7 +934,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t copy_ph = 0;
             const int k_per_mma = 32;  // bytes of K per instruction: 16 BF16 or 32 FP8 values
             for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-                const Item im = get_item<BATCHED>(p, &tmA, &tmB, it);
+                const Item im = get_item<BATCHED, BN>(p, &tmA, &tmB, it);
                 for (int ct = 0; ct < im.nsw && ok; ++ct, ++tile) {
                     const int acc = tile & 1;
                     const uint32_t acc_ph = static_cast<uint32_t>((tile >> 1) & 1);
@@ -929,23 +947,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     mbar_expect_tx(&acc_full[acc], CN_TX);
                     copy_acc = acc;
                     copy_ph = acc_ph;
-                    const int64_t cphys = static_cast<int64_t>(tile_at(im, ct)) * TC_BN;
-                    bulk_copy_g2s(cn_smem + acc * TC_BN, im.cnorm2 + cphys, TC_BN * 4, &acc_full[acc]);
+                    const int64_t cphys = static_cast<int64_t>(tile_at(im, ct)) * BN;
+                    bulk_copy_g2s(cn_smem + acc * BN, im.cnorm2 + cphys, BN * 4, &acc_full[acc]);
                     if constexpr (P == P_FP8)
-                        bulk_copy_g2s(cn_smem + 2 * TC_BN + acc * TC_BN, im.c_inv_scale + cphys, TC_BN * 4,
+                        bulk_copy_g2s(cn_smem + 2 * BN + acc * BN, im.c_inv_scale + cphys, BN * 4,
                                       &acc_full[acc]);
-                    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * TC_BN);
+                    const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
                     for (int ks = 0; ks < im.nk; ++ks) {
                         if (!mbar_wait(&full[s], ph, abort_flag, wait_limit)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t a_addr = smem_u32(stage_base + s * STAGE_BYTES);
+                        const uint32_t a_addr = smem_u32(stage_base + s * STAGE);
                         const uint32_t b_addr = a_addr + A_BYTES;
 #pragma unroll
                         for (int kk = 0; kk < TC_BK_BYTES / k_per_mma; ++kk) {
-                            umma<P>(d_tmem, sdesc(a_addr + kk * k_per_mma), sdesc(b_addr + kk * k_per_mma),
+                            umma<P, BN>(d_tmem, sdesc(a_addr + kk * k_per_mma), sdesc(b_addr + kk * k_per_mma),
                                     (ks | kk) != 0 ? 1u : 0u);
                         }
                         umma_commit(&empty[s]);
@@ -990,7 +1008,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         bool ok = true;
         uint32_t inserted = 0;  // this lane's insertions (its rows)
         for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
-            const Item p = get_item<BATCHED>(params, &tmA, &tmB, it);
+            const Item p = get_item<BATCHED, BN>(params, &tmA, &tmB, it);
             const int rb = p.rb;
             const int nct = p.nsw;
             // room for one half-tile of insertions from both warps: 2 x 64 per row
@@ -1050,26 +1068,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // gives up still takes the tile's first one, where the pair decides together
                 const bool got = mbar_wait_all(&acc_full[acc], acc_ph, abort_flag, wait_limit);
                 if (got) tc_fence_after();
-                const int c0 = half * (TC_BN / 2);  // first column of this warp's half
+                const int c0 = half * (BN / 2);  // first column of this warp's half
                 const uint32_t taddr = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                       static_cast<uint32_t>(acc * TC_BN + c0);
-                const float* cn = cn_smem + acc * TC_BN + c0;
-                const float* cs = cn_smem + 2 * TC_BN + acc * TC_BN + c0;
-                const int64_t jt = static_cast<int64_t>(tile_at(p, ct)) * TC_BN + c0;
+                                       static_cast<uint32_t>(acc * BN + c0);
+                const float* cn = cn_smem + acc * BN + c0;
+                const float* cs = cn_smem + 2 * BN + acc * BN + c0;
+                const int64_t jt = static_cast<int64_t>(tile_at(p, ct)) * BN + c0;
                 sym.on = sym_item && ct > 0;  // past the row block's own super-block
                 uint32_t ra[32], rb2[32];
 #pragma unroll 1
-                for (int hs = 0; hs < 2; ++hs) {
+                // each step covers 64 columns of each warp's half: two steps a 256-column
+                // tile, one a 128-column tile
+                for (int hs = 0; hs < BN / 128; ++hs) {
                     if (got) {
-                        // two chunks of 32 columns, the second load overlapping the first filter
-                        tmem_ld32(taddr + hs * 64, ra);
-                        tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
-                        filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf,
-                                        my_cnt, seg_base, seg_dir, inserted, sym);
-                        tmem_ld_wait();
-                        filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32, self,
-                                        tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted, sym);
-                        if (hs == 1) {
+                        if constexpr (BN == TC_BN) {
+                            // two chunks of 32 columns, the second load overlapping the first filter
+                            tmem_ld32(taddr + hs * 64, ra);
+                            tmem_ld32_issue(taddr + hs * 64 + 32, rb2);
+                            filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf,
+                                            my_cnt, seg_base, seg_dir, inserted, sym);
+                            tmem_ld_wait();
+                            filter_chunk<P>(rb2, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32,
+                                            self, tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted, sym);
+                        } else {
+                            // two CTAs an SM: one chunk's registers at a time (the SM's other
+                            // CTA covers the load latency)
+                            tmem_ld32(taddr + hs * 64, ra);
+                            filter_chunk<P>(ra, cn + hs * 64, cs + hs * 64, qscale, jt + hs * 64, self, tau_f, gbuf,
+                                            my_cnt, seg_base, seg_dir, inserted, sym);
+                            tmem_ld32(taddr + hs * 64 + 32, ra);
+                            filter_chunk<P>(ra, cn + hs * 64 + 32, cs + hs * 64 + 32, qscale, jt + hs * 64 + 32,
+                                            self, tau_f, gbuf, my_cnt, seg_base, seg_dir, inserted, sym);
+                        }
+                        if (hs == BN / 128 - 1) {
                             // accumulator and staged norms of this tile no longer needed by this warp
                             tc_fence_before();
                             __syncwarp();
@@ -1089,7 +1120,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     need &= partner_bit ? 0xaaaaaaaau : 0x55555555u;
                     if (need) {
                         // target ranks: speculative while only part of the corpus has been seen
-                        const int64_t seen = static_cast<int64_t>(ct) * TC_BN + (hs + 1) * (TC_BN / 2);
+                        const int64_t seen = static_cast<int64_t>(ct) * BN + (hs + 1) * 128;
                         const int rk = p.spec ? spec_rank(p.k, seen, p.N) : p.k;
                         const int rkm = p.spec ? spec_rank(p.km, seen, p.N) : p.km;
                         while (need) {
@@ -1215,7 +1246,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(Tile<BN>::TMEM_COLS)
                      : "memory");
     }
     if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, static_cast<int>(KNN_ETIMEOUT));
@@ -1267,10 +1298,11 @@ int fused_cap(int k, int km) {
     return c < 448 ? 448 : c;
 }
 
-int fused_stages(int cap, int precision, bool rr) {
+int fused_stages(int cap, int precision, bool rr, int bn) {
     if (cap > FUSED_CAP_MAX) return 0;  // a list is staged as at most 48 keys per lane
+    if (bn == 128 && cap > 512) return 0;  // the two-CTA tile exists for the 16-keys-a-lane lists only
     for (int st = MAX_STAGES; st >= 2; --st)
-        if (tc_smem_bytes(cap, st, precision, rr) <= 232448) return st;
+        if (tc_smem_bytes(cap, st, precision, rr, bn) <= smem_budget(bn)) return st;
     return 0;
 }
 
@@ -1278,34 +1310,41 @@ size_t fused_scratch_words(int cap, int grid) {
     return scratch_words_per_warp(cap) * EPI_WARPS * static_cast<size_t>(grid);
 }
 
-bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision) {
+bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision, int bn) {
     const int elem = precision == P_BF16 ? 2 : 1;
     return make_map(&prob->tmA, xq, prob->M, prob->k_bytes, TC_BM, elem) &&
-           make_map(&prob->tmB, xc, prob->N, prob->k_bytes, TC_BN, elem);
+           make_map(&prob->tmB, xc, prob->N, prob->k_bytes, bn, elem);
 }
 
 // Kernel instantiation for a precision, a launch form and the list capacity (keys
 // per lane of the register-staged shrink: 16 up to 512 keys, 32 up to 1024, 48 up to 1536).
+// The 128-column tile exists for batched launches with lists of at most 512 keys.
 template <bool BATCHED>
-void (*fused_kernel(int precision, int cap_max))(const CUtensorMap, const CUtensorMap, const FusedParams) {
+void (*fused_kernel(int precision, int cap_max, int bn))(const CUtensorMap, const CUtensorMap, const FusedParams) {
+    if constexpr (BATCHED) {
+        if (bn == 128)
+            return precision == P_BF16 ? fused_gemm_select_kernel<P_BF16, true, 16, 128>
+                                       : fused_gemm_select_kernel<P_FP8, true, 16, 128>;
+    }
     if (precision == P_BF16)
-        return cap_max > 1024 ? fused_gemm_select_kernel<P_BF16, BATCHED, 48>
-               : cap_max > 512 ? fused_gemm_select_kernel<P_BF16, BATCHED, 32>
-                               : fused_gemm_select_kernel<P_BF16, BATCHED, 16>;
-    return cap_max > 1024 ? fused_gemm_select_kernel<P_FP8, BATCHED, 48>
-           : cap_max > 512 ? fused_gemm_select_kernel<P_FP8, BATCHED, 32>
-                           : fused_gemm_select_kernel<P_FP8, BATCHED, 16>;
+        return cap_max > 1024 ? fused_gemm_select_kernel<P_BF16, BATCHED, 48, TC_BN>
+               : cap_max > 512 ? fused_gemm_select_kernel<P_BF16, BATCHED, 32, TC_BN>
+                               : fused_gemm_select_kernel<P_BF16, BATCHED, 16, TC_BN>;
+    return cap_max > 1024 ? fused_gemm_select_kernel<P_FP8, BATCHED, 48, TC_BN>
+           : cap_max > 512 ? fused_gemm_select_kernel<P_FP8, BATCHED, 32, TC_BN>
+                           : fused_gemm_select_kernel<P_FP8, BATCHED, 16, TC_BN>;
 }
 
-cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st) {
+cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st, int bn) {
     if (p.n_items <= 0) return cudaSuccess;
-    if (p.cap_max > FUSED_CAP_MAX) return cudaErrorInvalidValue;
+    if (p.cap_max > FUSED_CAP_MAX || (bn != TC_BN && (bn != 128 || p.cap_max > 512))) return cudaErrorInvalidValue;
     CUtensorMap dummy{};
-    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, false);
-    auto kern = fused_kernel<true>(precision, p.cap_max);
+    const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, false, bn);
+    if (smem > smem_budget(bn)) return cudaErrorInvalidValue;
+    auto kern = fused_kernel<true>(precision, p.cap_max, bn);
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, TC_THREADS, smem, st>>>(dummy, dummy, p);
+    kern<<<grid, bn == 128 ? Tile<128>::THREADS : Tile<TC_BN>::THREADS, smem, st>>>(dummy, dummy, p);
     return cudaGetLastError();
 }
 
@@ -1318,7 +1357,7 @@ cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStre
     if (!make_map(&tb, p.xc, p.N, p.k_bytes, TC_BN, elem)) return cudaErrorInvalidValue;
     const size_t smem = tc_smem_bytes(p.cap_max, p.stages, precision, p.rr_on != 0);
     if (smem > 232448) return cudaErrorInvalidValue;
-    auto kern = fused_kernel<false>(precision, p.cap_max);
+    auto kern = fused_kernel<false>(precision, p.cap_max, TC_BN);
     cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(kern), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, TC_THREADS, smem, st>>>(ta, tb, p);

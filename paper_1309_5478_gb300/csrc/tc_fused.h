@@ -93,14 +93,15 @@ constexpr int FUSED_CAP_WIDE = 1024;
 
 bool fused_available();
 // Pipeline stages that fit with lists of capacity cap (and the re-rank warps' buffers when
-// rr); 0: does not fit.
-int fused_stages(int cap, int precision, bool rr = false);
+// rr) for tiles of bn corpus columns (256: one CTA an SM; 128: two CTAs an SM, batched launches
+// with lists of at most 512 keys); 0: does not fit.
+int fused_stages(int cap, int precision, bool rr = false, int bn = 256);
 size_t fused_scratch_words(int cap, int grid);
 int fused_cap(int k, int km);
 cudaError_t launch_fused(const FusedParams& p, int precision, int grid, cudaStream_t st);
 // Batched launch over p.work (p.problems already holds encoded tensor maps).
-cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st);
+cudaError_t launch_fused_batched(const FusedParams& p, int precision, int grid, cudaStream_t st, int bn = 256);
 // Encodes the two tensor maps of one problem (host).
-bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision);
+bool encode_problem_maps(FusedProblem* prob, const void* xq, const void* xc, int precision, int bn = 256);
 
 }  // namespace knn

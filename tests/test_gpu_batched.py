@@ -62,6 +62,18 @@ def test_mixed_batch_bit_exact():
     check_all(probs, refs)
 
 
+@pytest.mark.parametrize("integer", [True, False])
+def test_128_column_tiles(monkeypatch, integer):
+    # every problem whose lists hold at most 512 keys on 128 x 128 tiles (two CTAs an SM), the
+    # others (k = 512) on 128 x 256 tiles in the same batch
+    monkeypatch.setenv("KNN_BATCH_TILE", "128")
+    probs, refs = make_problems(SHAPES, seed0=460, integer=integer)
+    st = kb.knn_search_batched(probs)
+    assert st == [0] * len(probs)
+    torch.cuda.synchronize()
+    check_all(probs, refs, exact=integer)
+
+
 def test_graph_replay_gives_the_same_answer():
     probs, refs = make_problems(SHAPES[:5], seed0=400)
     kb.knn_search_batched(probs)
@@ -159,14 +171,14 @@ def test_autotuner_cache_is_written_keyed_and_reused(tmp_path):
     assert first["status"] == [0]
     data = json.loads(cache.read_text())
     tag = data.pop("_device")
-    assert " sm" in tag and tag.endswith(" v2"), tag
-    assert data and all(v in (1, 2, 3) for v in data.values()), data  # measured: plain or a fused variant
+    assert " sm" in tag and tag.endswith(" v4"), tag
+    assert data and all(v in (1, 2, 3, 4, 5) for v in data.values()), data  # measured: plain or a fused variant
     # a second process follows the file: every bucket forced to the plain form
     cache.write_text(json.dumps({"_device": tag, **{b: 1 for b in data}}))
     second = run_tuned_batch(cache)
     assert second["status"] == [0] and second["fused_used"] == 0
     # entries of another device are ignored: the bucket is measured again and the file rewritten
-    cache.write_text(json.dumps({"_device": "another GPU sm1 v2", **{b: 1 for b in data}}))
+    cache.write_text(json.dumps({"_device": "another GPU sm1 v4", **{b: 1 for b in data}}))
     third = run_tuned_batch(cache)
     assert third["status"] == [0]
     again = json.loads(cache.read_text())
