@@ -795,9 +795,11 @@ int run_fused(const Problem& pb, int prec, knn_stats* stats, cudaStream_t st) {
     uint32_t* flags = nullptr;
     const int km = static_cast<int>(std::min<int64_t>(pb.k + pb.m, pb.N - (pb.graph ? 1 : 0)));
     int cap = fused_cap(pb.k, km);
-    // a large problem first measures its band on sampled rows and may take a larger list
+    // a large problem first measures its band on sampled rows and may take a larger list; a
+    // search within a bounding threshold (a streamed chunk after the first) starts at the bound
+    // instead, and few of its points lie within it
     const bool probe = static_cast<double>(pb.M) * static_cast<double>(pb.N) >= PROBE_MIN_PAIRS &&
-                       pb.M >= 4 * PROBE_ROWS && fused_stages(FUSED_CAP_WIDE, prec) > 0;
+                       pb.M >= 4 * PROBE_ROWS && fused_stages(FUSED_CAP_WIDE, prec) > 0 && !pb.thr_bound;
     // tuning override: a list capacity between the default for k + m and the maximum
     int cap_env = 0;
     if (const char* e = std::getenv("KNN_FUSED_CAP"))
