@@ -43,6 +43,8 @@ constexpr float TIE_REL = 0x1p-19f;
 // Members of one near-tie group settled in FP64 at most (a larger group is left unordered
 // and its row reported uncertified).
 constexpr int TIE_MAX = 128;
+// Odd-even passes tried on a list in approximate order before it is sorted in full.
+constexpr int SETTLE_PASSES = 32;
 
 // Per-warp (or per-block) counters of the re-rank, in shared memory; flushed into
 // RerankCounters by flush_rerank_counts.
@@ -422,11 +424,16 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
     exact_keys<VEC, G, NC>(p, q, K, kk, stop, qn2, inv_e, err_max, lane);
     count = stop;
 
-    // sort only the power of two that holds the list (P bounds it)
-    const int Pc = pow2_ceil(count > 32 ? count : 32) < P ? pow2_ceil(count > 32 ? count : 32) : P;
-    for (int i = count + static_cast<int>(lane); i < Pc; i += 32) K[i] = KEY_MAX;
-    __syncwarp();
-    warp_bitonic_sort_smem(K, Pc);
+    // sort by exact distance. A list taken in ascending approximate order is off by the
+    // approximation error only, a few positions: odd-even passes settle it. Otherwise (or
+    // when the passes do not settle it) sort only the power of two that holds the list.
+    const bool presorted = sorted || can_stop;
+    if (!presorted || !warp_oddeven_settle(K, count, SETTLE_PASSES)) {
+        const int Pc = pow2_ceil(count > 32 ? count : 32) < P ? pow2_ceil(count > 32 ? count : 32) : P;
+        for (int i = count + static_cast<int>(lane); i < Pc; i += 32) K[i] = KEY_MAX;
+        __syncwarp();
+        warp_bitonic_sort_smem(K, Pc);
+    }
 
     // 2. near ties around the first k positions, settled in FP64 (skipped when the
     //    inputs make FP32 exact: then equal values are true ties, already ordered by index)
@@ -445,15 +452,34 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
         any = __any_sync(0xffffffffu, any);
         if (any) {
             used64 = true;
-            int s = 0;
-            while (s < kk) {
-                // group [s, e]: maximal run with near(s..e-1)
+            // groups: maximal runs [s, e] with near(s..e-1), s < kk, found 32 positions a
+            // ballot. Positions from `next` on still hold their sorted FP32 keys (a placed
+            // group only rewrites its own positions), and next itself starts a run when
+            // near(next) holds, the run before it having ended at next - 1.
+            int next = 0;
+            while (next < kk) {
+                const int i = next + static_cast<int>(lane);
+                const bool st = i < kk && i + 1 < count && near(i) && (i == next || !near(i - 1));
+                const uint32_t sm = __ballot_sync(0xffffffffu, st);
+                if (sm == 0u) {
+                    next += 32;
+                    continue;
+                }
+                const int s = next + __ffs(sm) - 1;
                 int e = s;
-                while (e + 1 < count && near(e)) ++e;
+                for (int b = s;; b += 32) {
+                    const int j = b + static_cast<int>(lane);
+                    const uint32_t em = __ballot_sync(0xffffffffu, !(j + 1 < count && near(j)));
+                    if (em != 0u) {
+                        e = b + __ffs(em) - 1;
+                        break;
+                    }
+                }
+                next = e + 1;
                 const int g = e - s + 1;
                 if (g > TIE_MAX) {
                     giant_tie = true;  // left unordered: the row is reported uncertified
-                } else if (g > 1) {
+                } else {
                     for (int m = s; m <= e; ++m) {
                         const uint32_t j = key_idx(K[m]);
                         const double v = sqdist_fp64(q, p.C + static_cast<int64_t>(j) * d, d);
@@ -482,7 +508,6 @@ __device__ __forceinline__ void rerank_row(const RerankParams& p, int64_t row, i
                     for (int t = 0; t < nm; ++t) K[my_pos[t]] = my_key[t];
                     __syncwarp();
                 }
-                s = e + 1;
             }
         }
     }

@@ -384,25 +384,82 @@ __device__ __forceinline__ CompactResult compact_row(uint64_t* A, uint64_t* B, i
 
 namespace knn {
 
-// Ascending bitonic sort of X[0, P) by one warp (P a power of two).
+// Ascending bitonic sort of X[0, P) by one warp (P a power of two). Two stride levels of a
+// merge step share one pass over shared memory: a lane loads four keys b, b + h, b + 2h,
+// b + 3h, compares them at stride 2h and then h in registers and stores them back. Pair and
+// quad positions come from shifts and masks of the lane's item index.
+template <typename K>
+__device__ __forceinline__ void bitonic_ce(K& a, K& b, bool up) {
+    if ((a > b) == up) {
+        const K t = a;
+        a = b;
+        b = t;
+    }
+}
+
 template <typename K>
 __device__ __forceinline__ void warp_bitonic_sort_smem(K* X, int P) {
-    const uint32_t lane = lane_id();
-    for (int size = 2; size <= P; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = static_cast<int>(lane); i < (P >> 1); i += 32) {
-                const int lo = (i / stride) * 2 * stride + (i % stride);
-                const int hi = lo + stride;
+    const int lane = static_cast<int>(lane_id());
+    for (int lsz = 1; (1 << lsz) <= P; ++lsz) {
+        const int size = 1 << lsz;
+        int ls = lsz - 1;  // stride 2^ls
+        for (; ls >= 1; ls -= 2) {
+            const int h = 1 << (ls - 1);
+            for (int q = lane; q < (P >> 2); q += 32) {
+                const int b = ((q >> (ls - 1)) << (ls + 1)) | (q & (h - 1));
+                const bool up = (b & size) == 0;
+                K x0 = X[b], x1 = X[b + h], x2 = X[b + 2 * h], x3 = X[b + 3 * h];
+                bitonic_ce(x0, x2, up);
+                bitonic_ce(x1, x3, up);
+                bitonic_ce(x0, x1, up);
+                bitonic_ce(x2, x3, up);
+                X[b] = x0;
+                X[b + h] = x1;
+                X[b + 2 * h] = x2;
+                X[b + 3 * h] = x3;
+            }
+            __syncwarp();
+        }
+        if (ls == 0) {
+            for (int i = lane; i < (P >> 1); i += 32) {
+                const int lo = i << 1;
                 const bool up = (lo & size) == 0;
-                const K a = X[lo], b = X[hi];
+                const K a = X[lo], b = X[lo + 1];
                 if ((a > b) == up) {
                     X[lo] = b;
-                    X[hi] = a;
+                    X[lo + 1] = a;
                 }
             }
             __syncwarp();
         }
     }
+}
+
+// Ascending sort of X[0, n) by one warp for a list that is already nearly in order:
+// odd-even transposition passes (each lane compares and swaps pairs i, i + 1 for i of one
+// parity) until an even and an odd pass in a row swap nothing, which leaves every adjacent
+// pair in order. A key displaced by r positions needs about r passes. Returns false when
+// max_pass passes did not settle the list (it is then a permutation of the input, and the
+// caller sorts it in full).
+template <typename K>
+__device__ __forceinline__ bool warp_oddeven_settle(K* X, int n, int max_pass) {
+    const int lane = static_cast<int>(lane_id());
+    int quiet = 0;
+    for (int pass = 0; pass < max_pass; ++pass) {
+        bool swapped = false;
+        for (int i = (pass & 1) + 2 * lane; i + 1 < n; i += 64) {
+            const K a = X[i], b = X[i + 1];
+            if (a > b) {
+                X[i] = b;
+                X[i + 1] = a;
+                swapped = true;
+            }
+        }
+        __syncwarp();
+        quiet = __any_sync(0xffffffffu, swapped) ? 0 : quiet + 1;
+        if (quiet == 2) return true;
+    }
+    return false;
 }
 
 __host__ __device__ __forceinline__ int pow2_ceil(int x) {
