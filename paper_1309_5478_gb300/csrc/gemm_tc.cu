@@ -480,9 +480,12 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
             tr = res.truncated;
             band = res.band;
         } else {
-            // reference list overflow: keep a prefix and give up the bound, so the row
-            // cannot be certified and goes to the exact fallback
+            // reference list overflow: keep the first keys of the list and give up the
+            // bound, so the row cannot be certified and goes to the exact fallback
             nn = n < keep_trunc ? n : keep_trunc;
+#pragma unroll
+            for (int q = 0; q < KPL; ++q)
+                if (q * 32 + lane < nn) gbuf[q * 32 + lane] = key[q];
             nt = 0ull;
             tr = true;
         }
@@ -510,7 +513,9 @@ __device__ __noinline__ void shrink_row_k(const Item& p, const EpiSmem& es, cons
 // over the sorted sample, and the row is marked truncated there (every key dropped is
 // above that value; the re-rank certificate decides). Returns false, with the list and
 // the row state untouched, when no such value exists (keep_trunc = 0 disables truncation);
-// the caller then runs shrink_row_k.
+// the caller then runs shrink_row_k. Only the list's n keys are counted and kept: the
+// padding of the register copy is KEY_MAX, which a threshold still open admits (a list
+// that no sample value reduces and that needs no truncation keeps its n keys).
 template <int KPL>
 __device__ __forceinline__ bool shrink_mid_fast_body(const Item& p, const EpiSmem& es, const RowState& rs, int r,
                                                      int64_t grow, float window, int rk, int rkm, int keep_max,
@@ -561,7 +566,7 @@ __device__ __forceinline__ bool shrink_mid_fast_body(const Item& p, const EpiSme
         nt = band < t ? band : t;
         keep = 0;
 #pragma unroll
-        for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
+        for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
         keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
     }
     if (sel >= 0 && keep > keep_max) {
@@ -578,7 +583,7 @@ __device__ __forceinline__ bool shrink_mid_fast_body(const Item& p, const EpiSme
         nt = band < t ? band : t;
         keep = 0;
 #pragma unroll
-        for (int q = 0; q < KPL; ++q) keep += key[q] <= nt ? 1 : 0;
+        for (int q = 0; q < KPL; ++q) keep += (q * 32 + lane < n && key[q] <= nt) ? 1 : 0;
         keep = static_cast<int>(__reduce_add_sync(0xffffffffu, static_cast<uint32_t>(keep)));
     }
     if (keep > keep_max) {
@@ -602,7 +607,7 @@ __device__ __forceinline__ bool shrink_mid_fast_body(const Item& p, const EpiSme
     int nn = 0;
 #pragma unroll
     for (int q = 0; q < KPL; ++q) {
-        const bool kp = key[q] <= nt;
+        const bool kp = q * 32 + lane < n && key[q] <= nt;
         const uint32_t b = __ballot_sync(0xffffffffu, kp);
         if (kp) gbuf[nn + __popc(b & lt_mask)] = key[q];
         nn += __popc(b);

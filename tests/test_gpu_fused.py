@@ -143,6 +143,25 @@ def test_crowded_band_goes_through_every_fallback():
     check_float(X, X, rows, idx[rows], dist[rows], ref_idx, ref_dist, exclude_self=True)
 
 
+def test_crowded_long_lists_trimmed_before_any_shrink():
+    # a crowded corpus of 690 points and k = 300: the lists (824 keys) never reach their
+    # mid-sweep trigger, so the first shrink of a row is the trim before the re-rank, on a
+    # list whose threshold is still open and whose band no sample value reaches (the error
+    # window dwarfs the distances). The trim must find the ranks exactly and keep only the
+    # row's own keys: no index twice in any row, and the answer exact
+    rng = np.random.default_rng(68)
+    base = rng.standard_normal(64).astype(np.float32) * 30
+    C = (base + 0.05 * rng.standard_normal((690, 64))).astype(np.float32)
+    Q = (base + 0.05 * rng.standard_normal((96, 64))).astype(np.float32)
+    idx, dist, st = kb.knn_search(dev(Q), dev(C), 300, precision="bf16", fused=1, return_stats=True)
+    assert st["fused_used"] == 1
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    assert all(len(set(r.tolist())) == 300 for r in idx)
+    rows = np.arange(0, 96, 8)
+    ref_idx, ref_dist = oracle.knn(Q, C, 300, rows=rows)
+    check_float(Q, C, rows, idx[rows], dist[rows], ref_idx, ref_dist, False)
+
+
 @pytest.fixture
 def speculate(monkeypatch):
     def set_spec(on):
