@@ -144,11 +144,12 @@ typedef enum knn_metric {
 /*
  * k-NN search by a metric of the paper: for KNN_METRIC_EUCLIDEAN exactly knn_search
  * (out_val = squared distances, ascending). For KNN_METRIC_COSINE and
- * KNN_METRIC_PEARSON, out_val holds the similarities (FP32 rounding of the FP64
- * value), each row descending by similarity, ties to the lower index; the answer is
- * exact in FP64 arithmetic: the nearest unit rows found by the engine are re-ranked by
- * their FP64 similarity under a certificate, and rows it does not cover are recomputed
- * over the whole corpus in FP64. A row of zero norm (Pearson: zero norm after
+ * KNN_METRIC_PEARSON, out_val holds the similarities (FP32 rounding of a value within
+ * 2^-38 of the FP64 similarity), each row descending by similarity, ties to the lower
+ * index; the answer is exact: the nearest unit rows found by the engine are re-ranked by
+ * their similarity, its dot product summed from FP32 error-free transformations in FP64
+ * (within 2^-38 of sum |x_t y_t|), under a certificate that covers that error, and rows
+ * it does not cover are recomputed over the whole corpus in FP64. A row of zero norm (Pearson: zero norm after
  * centring) or with a non-finite value returns KNN_EINVAL. opt->row_threshold must be
  * NULL for the similarity metrics. opt->stats: rows_uncertified counts the rows the
  * similarity certificate did not cover; rows_fallback adds those rows to the rows the

@@ -128,3 +128,105 @@ def test_bound_conversion_covers_the_exact_norm(d):
             t = np.float32(exact * rng.uniform(0.5, 3.0))
             e = np.float32(rng.uniform(0.0, 1e-3) * exact)
             assert _bound_to_dprime(t, qn2, e, d) - float(e) >= float(t) - exact
+
+
+# ---------------------------------------------------------------------------------------
+# The similarity re-rank's dot product, replayed with the kernel's operation order and FP32
+# roundings: entries centred into FP32 pairs (centre_pair), products of pairs made exact up
+# to the dropped al bl (DotPairSum.add), TwoSum accumulation folded into an FP64 sum every 8
+# terms per lane, lanes (element t on lane t mod 32) added by an xor-shuffle tree. The stated
+# bound is 2^-38 sum_t |a_t b_t| against the exact dot product of the centred rows.
+
+_f32 = np.float32
+
+
+def _two_sum(a, b):
+    s = _f32(a + b)
+    bb = _f32(s - a)
+    return s, _f32(_f32(a - _f32(s - bb)) + _f32(b - bb))
+
+
+def _fma(a, b, c):
+    # the FP32 product is exact in FP64; one rounding of the sum to FP32 (at worst a double
+    # rounding, far inside the bound checked)
+    return _f32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _centre(a, mh, ml):
+    s, e = _two_sum(a, _f32(-mh))
+    e2, r2 = _two_sum(e, _f32(-ml))
+    h, l = _two_sum(s, e2)
+    return h, _f32(l + r2)
+
+
+def replay_pair_dot(x, y, mx, my, centered, drop=""):
+    mxh = _f32(mx)
+    mxl = _f32(mx - np.float64(mxh))
+    myh = _f32(my)
+    myl = _f32(my - np.float64(myh))
+    lanes = []
+    for lane in range(32):
+        acc, S, E, n = np.float64(0.0), _f32(0.0), _f32(0.0), 0
+        for t in range(lane, len(x), 32):
+            ah, al = _centre(x[t], mxh, mxl) if centered else (x[t], _f32(0.0))
+            bh, bl = _centre(y[t], myh, myl) if centered else (y[t], _f32(0.0))
+            if drop == "lo":
+                al = bl = _f32(0.0)
+            pr = _f32(ah * bh)
+            pe = _fma(ah, bh, _f32(-pr)) if drop != "pe" else _f32(0.0)
+            pe = _fma(ah, bl, _fma(al, bh, pe))
+            S, e2 = _two_sum(S, pr)
+            E = _f32(E + _f32(e2 + pe))
+            n += 1
+            if n == 8:
+                acc = np.float64(acc + (np.float64(S) + np.float64(E)))
+                S, E, n = _f32(0.0), _f32(0.0), 0
+        lanes.append(np.float64(acc + (np.float64(S) + np.float64(E))))
+    o = 16
+    while o > 0:
+        lanes = [np.float64(lanes[i] + lanes[i ^ o]) for i in range(32)]
+        o //= 2
+    return float(lanes[0])
+
+
+def _pair_dot_worst(drop, pairs):
+    from fractions import Fraction
+    worst = 0.0
+    for d, kind, centered in ((3, "gauss", False), (64, "gauss", True), (256, "offset", True),
+                              (1024, "gauss", False), (1024, "offset", True), (128, "wide", True),
+                              (768, "lattice", True), (300, "lattice", False)):
+        rng = np.random.default_rng(95 + d)
+        for _ in range(pairs):
+            if kind == "gauss":
+                X = rng.standard_normal((2, d))
+            elif kind == "offset":  # centring cancels most of each entry
+                X = 1e4 + rng.standard_normal((2, d))
+            elif kind == "wide":
+                X = rng.standard_normal((2, d)) * 10.0 ** rng.uniform(-6, 6, (2, d))
+            else:
+                X = rng.integers(-3, 4, (2, d))
+            x, y = X.astype(np.float32)
+            mx = float(x.astype(np.float64).mean()) if centered else 0.0
+            my = float(y.astype(np.float64).mean()) if centered else 0.0
+            a = [Fraction(float(v)) - Fraction(mx) for v in x]
+            b = [Fraction(float(v)) - Fraction(my) for v in y]
+            exact = sum(p * q for p, q in zip(a, b))
+            scale = sum(abs(p * q) for p, q in zip(a, b))
+            got = Fraction(replay_pair_dot(x, y, mx, my, centered, drop))
+            if scale == 0:
+                continue
+            worst = max(worst, float(abs(got - exact) / scale))
+    return worst
+
+
+def test_similarity_dot_within_2_pow_minus_38():
+    worst = _pair_dot_worst("", 2)
+    assert worst <= 2.0 ** -38, worst
+    assert worst < 2.0 ** -44, worst  # FP64-class in practice
+
+
+@pytest.mark.parametrize("drop", ["pe", "lo"])
+def test_similarity_dot_needs_each_correction(drop):
+    # without the products' rounding errors, or without the centred pairs' low parts, the same
+    # rows leave the bound far behind
+    assert _pair_dot_worst(drop, 1) > 2.0 ** -30
