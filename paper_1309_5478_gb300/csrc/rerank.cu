@@ -124,16 +124,22 @@ namespace {
 cudaError_t launch_rerank_batched_range(const BatchDev* probs, const BatchSeg* segs, int32_t nseg, int64_t rows,
                                         int P, int32_t cmin, int32_t cmax, int tier, RerankCounters* counters,
                                         cudaStream_t st) {
+    // warps a CTA: as many key buffers as a third of the SM's shared memory holds (at most
+    // 8), so that three CTAs share an SM, the most its registers allow at 80 a thread
+    // (24 warps for lists of up to 1024 keys, where a fixed 64 KB share gave 21)
+    int dev = 0, sms = 0, per_sm = 0, smem_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
     const size_t per_warp = static_cast<size_t>(P + TIE_MAX) * 8;
-    int warps = static_cast<int>((64u * 1024u) / per_warp);
+    const size_t share = smem_sm > 3 * 4096 ? static_cast<size_t>(smem_sm) / 3 - 2048 : 64u * 1024u;
+    int warps = static_cast<int>(share / per_warp);
     if (warps > 8) warps = 8;
     if (warps < 1) warps = 1;
     const size_t smem = per_warp * warps;
-    cudaError_t e = raise_smem_limit(reinterpret_cast<const void*>(rerank_batched_kernel), static_cast<int>(smem));
+    e = raise_smem_limit(reinterpret_cast<const void*>(rerank_batched_kernel), static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rerank_batched_kernel, warps * 32,
                                                                            smem);
     if (e != cudaSuccess) return e;
